@@ -1,0 +1,188 @@
+"""Pins of the topographic-map oracle: analytic neuron solution, STDP pair rule,
+Fig. 3's worked example, closed-form formation rates, input statistics."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import philox
+from oracle import topo
+
+
+def test_exponential_euler_is_exact_for_constant_conductance():
+    p = topo.TopoParams(tau_s=float("inf"), V_theta=1e9)
+    N = 3
+    V = np.array([-70.0, -60.0, -20.0])
+    gs = np.array([0.0, 0.35, 2.0])
+    ref = np.zeros(N, np.int64)
+    V0 = V.copy()
+    for t in range(1, 200):
+        V, gs, ref, z = topo.neuron_step(V, gs, ref, np.zeros(N), p)
+        Vinf = (p.V_rest + gs * p.E_exc) / (1 + gs)
+        exact = Vinf + (V0 - Vinf) * np.exp(-t * p.dt * (1 + gs) / p.tau_m)
+        np.testing.assert_allclose(V, exact, rtol=0, atol=1e-12)
+
+
+def test_refractory_hold_and_conductance_decay():
+    p = topo.TopoParams()
+    V, gs, ref = np.array([-55.0]), np.array([0.0]), np.zeros(1, np.int64)
+    V, gs, ref, z = topo.neuron_step(V, gs, ref, np.array([5.0]), p)   # strong kick -> spike
+    assert z[0] and V[0] == p.V_reset and ref[0] == p.n_ref
+    for k in range(p.n_ref):
+        V, gs, ref, z = topo.neuron_step(V, gs, ref, np.zeros(1), p)
+        assert V[0] == p.V_reset and not z[0]
+    np.testing.assert_allclose(gs[0], 5.0 * math.exp(-p.dt / p.tau_s) ** p.n_ref, rtol=1e-12)
+    V, gs, ref, z = topo.neuron_step(V, gs, ref, np.zeros(1), p)
+    assert V[0] > p.V_reset
+
+
+@pytest.mark.parametrize("lag", [1, 3, 10])
+def test_stdp_pair_rule(lag):
+    """One synapse 0 -> 0 starting mid-range: a pre spike then a post spike lag steps
+    later changes g by +A_+ exp(-lag dt / tau_+); post then pre by -A_- exp(-lag dt / tau_-)."""
+    p = topo.TopoParams()
+    for order in ("pre_post", "post_pre"):
+        proj = (np.array([1]), np.array([[0]]), np.array([[0.1]]))
+        x, y = np.zeros(1), np.zeros(1)
+        for t in range(lag + 1):
+            pre = np.array([t == (0 if order == "pre_post" else lag)])
+            post = np.array([t == (lag if order == "pre_post" else 0)])
+            xs, y = topo.stdp_step([proj], [x], y, [pre], post, p)
+            x = xs[0]
+        dg = proj[2][0, 0] - 0.1
+        if order == "pre_post":
+            np.testing.assert_allclose(dg, p.A_plus * math.exp(-lag * p.dt / p.tau_plus), rtol=1e-12)
+        else:
+            np.testing.assert_allclose(dg, -p.A_minus * math.exp(-lag * p.dt / p.tau_minus), rtol=1e-12)
+
+
+def test_fig3_worked_example_as_sets():
+    """Fig. 3: six attempts on s0 (t0, t2), s2 (t2) and s4 (t2, t3, t0).  (s0,t0) is
+    strong and stays, (s0,t2) and (s4,t2) are eliminated, (s4,t3) stays, (s2,t2) is
+    formed and (s4,t0) is not."""
+    P, Q, C = 5, 4, 3
+    row_len = np.array([2, 1, 0, 2, 2], np.int32)
+    ind = np.array([[0, 2, -1], [1, -1, -1], [-1, -1, -1], [3, 1, -1], [2, 3, -1]], np.int32)
+    g_max, g_theta = 0.2, 0.1
+    g = np.array([[0.18, 0.05, 0], [0.15, 0, 0], [0, 0, 0], [0.02, 0.19, 0], [0.03, 0.04, 0]])
+    lo, hi = 0, 2 ** 64 - 1
+    draws = topo.Draws(attempts=np.array([2, 0, 1, 0, 3]),
+                       candidates={0: [0, 2], 2: [2], 4: [2, 3, 0]},
+                       R={(0, 0): hi, (0, 2): lo, (4, 2): lo, (4, 3): hi, (2, 2): lo, (4, 0): hi})
+    thr_form = [philox.threshold(0.5)] * 20
+    out = topo.rewire(row_len, ind, g, C, Q, 4, seed=0, rewire_idx=0, n_att=6,
+                      thr_dep=philox.threshold(0.5), thr_pot=philox.threshold(0.01), g_theta=g_theta,
+                      thr_form=thr_form, g_new=g_max, draws=draws)
+    rows = [set(out["ind"][i, :out["row_len"][i]]) for i in range(P)]
+    assert rows == [{0}, {1}, {2}, {3, 1}, {3}]
+    assert list(out["row_len"]) == [1, 1, 1, 2, 1]
+    assert out["removed"] == 2 and out["formed"] == 1 and out["overflow"] == 0
+    assert out["g"][2, 0] == g_max and out["g"][0, 0] == 0.18
+
+
+def test_formation_rate_on_empty_rows_matches_gaussian_closed_form():
+    L, n_att, calls = 16, 200, 150
+    P = Q = L * L
+    p_form, sigma = 0.16, 2.5
+    thr_form = topo.form_thresholds(p_form, sigma, L)
+    empty = (np.zeros(P, np.int32), np.full((P, 8), -1, np.int32), np.zeros((P, 8)))
+    formed = 0
+    shell = {}
+    for r in range(calls):
+        out = topo.rewire(*empty, 8, Q, L, seed=31, rewire_idx=r, n_att=n_att, thr_dep=0, thr_pot=0,
+                          g_theta=0.1, thr_form=thr_form, g_new=0.2)
+        formed += out["formed"]
+        for d2 in out["formed_d2"]:
+            shell[d2] = shell.get(d2, 0) + 1
+    d2_all = synth.torus_d2(np.zeros(Q, np.int64), np.arange(Q), L)
+    p_bar = np.mean(p_form * np.exp(-d2_all / (2 * sigma ** 2)))
+    n = n_att * calls
+    assert abs(formed - n * p_bar) < 5 * math.sqrt(n * p_bar * (1 - p_bar))
+    # per distance shell: binomial with p = (#targets at d2 / Q) * p_form exp(-d2 / 2 sigma^2)
+    for d2 in (0, 1, 2, 4, 5, 8):
+        ps = np.sum(d2_all == d2) / Q * p_form * math.exp(-d2 / (2 * sigma ** 2))
+        assert abs(shell.get(d2, 0) - n * ps) < 5 * math.sqrt(n * ps * (1 - ps)) + 1
+
+
+def test_depressed_full_rows_lose_every_selected_synapse():
+    P = Q = 9
+    C = Q
+    row_len = np.full(P, Q, np.int32)
+    rng = np.random.default_rng(0)
+    ind = np.array([rng.permutation(Q) for _ in range(P)], np.int32)
+    g = np.full((P, C), 0.05)
+    for r in range(5):
+        out = topo.rewire(row_len, ind, g, C, Q, 3, seed=8, rewire_idx=r, n_att=12,
+                          thr_dep=philox.threshold(2.45e-2 * 50), thr_pot=0, g_theta=0.1,
+                          thr_form=[2 ** 64 - 1] * 10, g_new=0.2)
+        assert out["removed"] == out["attempts"].sum() == 12
+        assert out["formed"] == 0
+        for i in range(P):
+            kept = [j for j in ind[i] if j in set(out["ind"][i, :out["row_len"][i]])]
+            assert list(out["ind"][i, :out["row_len"][i]]) == kept     # stable order
+
+
+def test_full_row_formation_counts_overflow():
+    P = Q = 4
+    C = 1
+    row_len = np.ones(P, np.int32)
+    ind = np.array([[0], [1], [2], [3]], np.int32)
+    g = np.full((P, 1), 0.2)
+    draws = topo.Draws(attempts=np.array([2, 0, 0, 0]), candidates={0: [0, 3]},
+                       R={(0, 0): 2 ** 64 - 1, (0, 3): 0})
+    out = topo.rewire(row_len, ind, g, C, Q, 2, 0, 0, 2, 0, 0, 0.1, [2 ** 64 - 1] * 5, 0.2, draws=draws)
+    assert out["overflow"] == 1 and out["formed"] == 0 and out["removed"] == 0
+
+
+def test_input_rates_and_focus():
+    p = topo.TopoParams(L=16)
+    seed = 5
+    T = 4000
+    inside_cnt = outside_cnt = 0
+    inside_n = outside_n = 0
+    foci = []
+    for t in range(T):
+        s = topo.input_spikes(seed, t, p)
+        fx, fy = topo.focus(seed, t // p.t_stim, p.L)
+        if t % p.t_stim == 0:
+            foci.append(fx + p.L * fy)
+        c = np.arange(p.N)
+        d2 = synth.torus_d2(np.full(p.N, fx + p.L * fy), c, p.L)
+        ins = d2 <= p.radius ** 2
+        inside_cnt += s[ins].sum()
+        outside_cnt += s[~ins].sum()
+        inside_n += ins.sum()
+        outside_n += (~ins).sum()
+    for cnt, n, prob in ((inside_cnt, inside_n, 0.1), (outside_cnt, outside_n, 0.02)):
+        assert abs(cnt - n * prob) < 5 * math.sqrt(n * prob * (1 - prob))
+    assert len(set(foci)) > 100
+
+
+def test_initial_degree_matches_lattice_sum():
+    L, p_form, sigma = 32, 0.16, 2.5
+    rag = synth.topo_initial(3, L, p_form, sigma, 64, 0.2)
+    d2 = synth.torus_d2(np.zeros(L * L, np.int64), np.arange(L * L), L)
+    K = p_form * np.exp(-d2 / (2 * sigma ** 2)).sum()
+    assert abs(K - 2 * math.pi * p_form * sigma ** 2) < 0.01        # the paper's K, read as 2 pi p sigma^2
+    var = (p_form * np.exp(-d2 / (2 * sigma ** 2)) * (1 - p_form * np.exp(-d2 / (2 * sigma ** 2)))).sum()
+    assert abs(rag.row_len.mean() - K) < 5 * math.sqrt(var / (L * L))
+
+
+def test_short_run_invariants():
+    p = topo.TopoParams(L=8, n_att=10)
+    ff = synth.topo_initial(1, p.L, p.p_form_ff, p.sigma_ff, 16, p.g_max)
+    lat = synth.topo_initial(2, p.L, p.p_form_lat, p.sigma_lat, 16, p.g_max)
+    st = topo.initial_state([ff.row_len, ff.ind, ff.w], [lat.row_len, lat.ind, lat.w], p)
+    seeds = {"input": 1, "ff": 2, "lat": 3}
+    spikes = 0
+    for t in range(60):
+        out = topo.step(st, t, p, seeds, 16)
+        spikes += out["z"].sum()
+        for proj in (st.ff, st.lat):
+            assert np.all(proj[0] <= 16)
+            for i in range(p.N):
+                tg = list(proj[1][i, :proj[0][i]])
+                assert len(set(tg)) == len(tg)
+                assert np.all((proj[2][i, :proj[0][i]] >= 0) & (proj[2][i, :proj[0][i]] <= p.g_max))
+    assert spikes > 0
