@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: e-prop + DEEP R training of the sparse recurrent classifier on one GB300.
+
+Workload (one "step" = one training batch through the whole hot path):
+  700 Poisson input channels -> 1024 ALIF (tau_m 20 ms, tau_a 2000 ms, v_thr 0.6,
+  beta 0.0174) -> 20 leaky readouts; 10 % ragged input->hidden and hidden->hidden
+  connectivity (row capacity 288 = roundup32(2 x max initial row length)); 20 classes of
+  log-normal rate templates (0-50 Hz, 10 time bins) with per-trial time warp; 1000 steps
+  of 1 ms; batch 512; e-prop gradient, L1 (1e-5) + Adam (lr 1e-3) and one DEEP R
+  rewiring of both sparse projections per batch.  Synthetic data of the spoken-digit
+  benchmark's shape (the dataset itself is not used).
+
+Per step the GPU runs: every trial's 1000 steps in one launch (input spikes,
+propagation, neurons, readout), the adjoint e-prop gradient, L1 + Adam, DEEP R.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "e-prop+DEEP R training samples/s"
+UNIT = "samples/s"
+WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--sample-steps", type=int, default=600, help="oracle sample: steps of one trial")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------ workload
+
+def make_workload(seed: int, device="cuda"):
+    import numpy as np
+    import synth
+    from paper_2510_19764_gb300 import abi, net
+    W = WORKLOAD
+    task = synth.spoken_digit_task(seed, n_in=W["n_in"], n_classes=W["n_classes"], T=W["T"], n_bins=W["n_bins"])
+    in_rag = synth.random_ragged(seed + 1, W["n_in"], W["N"], W["p"])
+    rec_rag = synth.random_ragged(seed + 2, W["N"], W["N"], W["p"], no_autapse=True)
+    W_out, b = synth.dense_readout(seed + 3, W["K"], W["N"])
+    F32 = abi.SNN_F32
+    d_in = net.DeviceRagged(in_rag.row_len, in_rag.ind, in_rag.w, W["N"], dtype=F32, adam=True, grad=True,
+                            deepr=True, seed=seed + 100, device=device)
+    d_rec = net.DeviceRagged(rec_rag.row_len, rec_rag.ind, rec_rag.w, W["N"], dtype=F32, no_autapse=True, adam=True,
+                             grad=True, deepr=True, seed=seed + 101, device=device)
+    cls = net.DeviceClassifier(W["n_in"], W["N"], W["K"], d_in, d_rec, W_out, b, task.thr, seed + 7,
+                               net.NeuronCfg(tau_m=20.0, v_thr=0.6, beta=0.0174, tau_a=2000.0),
+                               max_B=W["B"], max_T=W["T"], dtype=F32, device=device)
+    return task, in_rag, rec_rag, cls
+
+
+def count_events(batch, cls, device="cuda"):
+    """Synaptic events of one batch: presynaptic spikes x row lengths (measurement only)."""
+    import torch
+    shifts = torch.arange(32, device=device, dtype=torch.int32)
+
+    def per_neuron(rec, n):
+        bits = (rec.unsqueeze(-1) >> shifts) & 1
+        return bits.reshape(rec.shape[0], rec.shape[1], -1)[..., :n].sum(dim=(0, 1)).double()
+
+    xin = per_neuron(batch.x_rec, cls.n_in)
+    zh = per_neuron(batch.z_rec, cls.N)
+    ev = float((xin * cls.w_in.row_len.double()).sum() + (zh * cls.w_rec.row_len.double()).sum())
+    return ev, float(xin.sum() + zh.sum())
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import synth
+    from paper_2510_19764_gb300 import abi, build, net
+    if rank == 0 or world > 1:
+        build.build()
+    abi.load()
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(local)
+    W = WORKLOAD
+    B, T = W["B"], W["T"]
+    task, in_rag, rec_rag, cls = make_workload(args.seed + 1000 * rank, dev)
+    n_total = args.warmup + args.steps
+    batches = [synth.trial_batch(task, args.seed + rank, i, B) for i in range(2 * n_total)]
+    # device copies of every batch's trial descriptors (the device-resident leg)
+    d_desc = [(torch.as_tensor(tb.labels, device=dev), torch.as_tensor(tb.bin_len, device=dev),
+               torch.as_tensor(tb.trial_ids, device=dev)) for tb in batches]
+    # pinned host copies (the end-to-end leg)
+    h_desc = [(torch.as_tensor(tb.labels).pin_memory(), torch.as_tensor(tb.bin_len).pin_memory(),
+               torch.as_tensor(tb.trial_ids).pin_memory()) for tb in batches]
+    batch = net.DeviceBatch(cls, batches[0].labels, batches[0].bin_len, batches[0].trial_ids, T, device=dev)
+    stream = torch.cuda.current_stream()
+    stats = torch.zeros((2, 4), dtype=torch.int64, device=dev)
+    lr, l1 = 1e-3, 1e-5
+    calls = ["snn_step_neurons", "snn_eprop_update(GRAD)", "snn_eprop_update(APPLY)", "snn_rewire_deepr"]
+    ev_pairs = []
+
+    def one_step(i, desc, timed):
+        lab, bl, tid = desc
+        batch.labels.copy_(lab, non_blocking=True)
+        batch.bin_len.copy_(bl, non_blocking=True)
+        batch.trial_ids.copy_(tid, non_blocking=True)
+        for t_ in (batch.v, batch.a, batch.y, batch.ysum, batch.x_bits, batch.z_bits):
+            t_.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if timed else None
+        if ev:
+            ev[0].record(stream)
+        abi.snn_step_neurons(cls.handle, batch.desc, 0, T, stream)
+        if ev:
+            ev[1].record(stream)
+        abi.snn_eprop_update(cls.handle, batch.desc, abi.SNN_EPROP_GRAD, None, stream)
+        if ev:
+            ev[2].record(stream)
+        abi.snn_eprop_update(cls.handle, batch.desc, abi.SNN_EPROP_APPLY, net.adam_params(lr, i + 1, l1=l1), stream)
+        if ev:
+            ev[3].record(stream)
+        abi.snn_rewire_deepr(cls.w_in.handle, i, stats[0], stream)
+        abi.snn_rewire_deepr(cls.w_rec.handle, i, stats[1], stream)
+        if ev:
+            ev[4].record(stream)
+            ev_pairs.append(ev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for i in range(args.warmup):
+        one_step(i, d_desc[i], False)
+    barrier()
+    # ---- device-resident timed region
+    with ClockSampler(local) as clk:
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        start.record(stream)
+        for k in range(args.steps):
+            i = args.warmup + k
+            one_step(i, d_desc[i], True)
+        end.record(stream)
+        barrier()
+    ms = start.elapsed_time(end)
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    per_call = [0.0] * 4
+    for ev in ev_pairs:
+        for c in range(4):
+            per_call[c] += ev[c].elapsed_time(ev[c + 1])
+    per_call = [x / len(ev_pairs) for x in per_call]
+    events, spikes = count_events(batch, cls, dev)
+    # ---- end-to-end leg through the public calls, host buffers each step
+    out_host = torch.empty((B, W["K"]), dtype=torch.float32).pin_memory()
+    stats_host = torch.empty((2, 4), dtype=torch.int64).pin_memory()
+    barrier()
+    e2e_start, e2e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_start.record(stream)
+    t_host0 = time.perf_counter()
+    for k in range(args.steps):
+        i = n_total + k
+        one_step(i, h_desc[i], False)
+        out_host.copy_(batch.ysum, non_blocking=True)
+        stats_host.copy_(stats, non_blocking=True)
+        stream.synchronize()
+    e2e_end.record(stream)
+    barrier()
+    e2e_ms = max(e2e_start.elapsed_time(e2e_end), (time.perf_counter() - t_host0) * 1e3)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = sum(x.numel() * x.element_size() for x in h_desc[0])
+    d2h = out_host.numel() * out_host.element_size() + stats_host.numel() * stats_host.element_size()
+    ok = cls.w_in.status(stream) == abi.SNN_OK and cls.w_rec.status(stream) == abi.SNN_OK
+    if rank != 0:
+        return None
+    value = B * args.steps * world / (ms_max / 1e3)
+    pk = peaks()
+    # dominant call and its algorithmic bytes
+    dom = max(range(4), key=lambda c: per_call[c])
+    N, n_in, K = W["N"], W["n_in"], W["K"]
+    alg = {
+        # forward: 8 B per synaptic event (ind + w) + 4 B per spike-bit list entry + 32 B per
+        # ALIF neuron-step (v, a read/write; psi record)
+        0: events * 8 + spikes * 4 + B * T * N * 32.0,
+        # gradient: psi read + delta write/read + synaptic events gathered (4 B delta + 4 B ind)
+        1: B * T * N * 4.0 * 3 + events * 8,
+        2: 28.0 * (in_rag.P * in_rag.C + rec_rag.P * rec_rag.C),
+        3: 24.0 * (in_rag.P * in_rag.C + rec_rag.P * rec_rag.C),
+    }[dom]
+    achieved = alg / (per_call[dom] / 1e3) / 1e9
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "spoken-digit-shaped sparse ALIF classifier, e-prop + DEEP R training batch",
+                   "n_in": n_in, "hidden": N, "readouts": K, "steps_per_trial": T, "global_batch": B * world,
+                   "connectivity": W["p"], "row_capacity": [in_rag.C, rec_rag.C],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (per-batch records and adjoint > 4 GB rewritten every step)"},
+        "synaptic_events_per_s": round(events * world / (ms_max / 1e3 / args.steps), 1),
+        "per_call_ms": {c: round(x, 4) for c, x in zip(calls, per_call)},
+        "roofline": {"kernel": calls[dom], "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
+                     "traffic": None, "peak_source": pk["source"]},
+        "e2e": {"value": round(B * args.steps * world / (e2e_ms / 1e3), 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 18 * args.steps,
+        "clocks": clocks,
+        "status_ok": bool(ok),
+    }
+    return line
+
+
+def run_reference(args, sample_steps: int, world: int, rank: int):
+    """FP64 CPU oracle on a bounded sample: one trial of `sample_steps` steps of the same
+    network (forward + e-prop traces), scaled to a full 1000-step trial."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import synth
+    from oracle import classifier as oc
+    W = WORKLOAD
+    seed = args.seed
+    task = synth.spoken_digit_task(seed, n_in=W["n_in"], n_classes=W["n_classes"], T=W["T"], n_bins=W["n_bins"])
+    in_rag = synth.random_ragged(seed + 1, W["n_in"], W["N"], W["p"])
+    rec_rag = synth.random_ragged(seed + 2, W["N"], W["N"], W["p"], no_autapse=True)
+    W_out, b = synth.dense_readout(seed + 3, W["K"], W["N"])
+    onet = oc.ClassifierNet(W["n_in"], W["N"], W["K"], in_rag.row_len, in_rag.ind, in_rag.w, rec_rag.row_len,
+                            rec_rag.ind, rec_rag.w, W_out, b, oc.NeuronParams())
+    tb = synth.trial_batch(task, seed, 0, 1)
+    t0 = time.perf_counter()
+    r = oc.forward_trial(onet, task.thr, tb.labels[0], tb.bin_len[0], tb.trial_ids[0], seed + 7, sample_steps)
+    oc.eprop_gradients(onet, r["x"], r["z"], r["psi"], r["d"])
+    dt = time.perf_counter() - t0
+    per_trial = dt * W["T"] / sample_steps
+    return 1.0 / per_trial, per_trial, dt
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        v, per_trial, dt = run_reference(args, args.sample_steps, world, rank)
+        line = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_trial * WORKLOAD["B"] * 1e3, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "spoken-digit-shaped sparse ALIF classifier, e-prop + DEEP R training batch",
+                           "global_batch": WORKLOAD["B"]},
+                "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"1 trial x {args.sample_steps} of 1000 steps (forward + e-prop traces), "
+                                           f"{dt:.1f} s, scaled to a full trial"},
+                "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    line = run_ours(args, world, rank, local)
+    if rank == 0:
+        cv, per_trial, dt = run_reference(args, args.sample_steps, world, rank)
+        line["cpu_baseline"] = {"value": round(cv, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"1 trial x {args.sample_steps} of 1000 steps (forward + e-prop traces), "
+                                          f"{dt:.1f} s, scaled to a full trial"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

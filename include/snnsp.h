@@ -1,0 +1,301 @@
+/*
+ * snnsp.h — C ABI of the GB300 (sm_103a) structural-plasticity library.
+ *
+ * Implements the data-parallel hot path of Knight, Senk & Nowotny, "A flexible framework
+ * for structural plasticity in GPU-accelerated sparse spiking neural networks":
+ * spike propagation through ragged sparse matrices (Sec. 2.1, Fig. 1), the LIF/ALIF
+ * recurrent classifier with e-prop learning and Adam (Sec. 2.2.1), DEEP R rewiring
+ * (Sec. 2.1.2, Fig. 2) and the topographic-map rewiring rule with STDP
+ * (Sec. 2.1.3, Sec. 2.2.2, Fig. 3, Tab. 1-2).
+ *
+ * Conventions that hold for every entry point:
+ *  - Every pointer named "device" is CUDA device memory owned by the CALLER; the library
+ *    never frees it.  Opaque handles (snn_ragged, snn_classifier) and the fixed scratch
+ *    they hold are owned by the library and released by the matching destroy call.
+ *  - Every compute call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream), allocates nothing and never synchronises, unless its comment says
+ *    otherwise (the create calls validate inputs and do synchronise).
+ *  - Argument errors are returned synchronously (SNN_EINVAL, with a message from
+ *    snn_last_error()).  Errors that only the device can see (capacity overflow,
+ *    out-of-range index, a wait that gave up) are recorded in the handle's device
+ *    status word and returned by snn_ragged_status(); no device code traps.
+ *  - Ragged layout (Fig. 1): row i = presynaptic neuron i, slot (i, s) at i*C + s,
+ *    s < row_len[i] are synapses, slots >= row_len[i] are padding for growth.  Rows
+ *    are unsorted and contain no duplicate targets.
+ *  - Bitfields: row i of a P x Q bitfield is ceil(Q/32) uint32 words; bit j of the row
+ *    is bit (j & 31) of word (j >> 5).
+ *  - Random numbers: Philox4x64-10 (Salmon et al., SC'11) keyed by (seed, purpose),
+ *    with purpose-specific counters; Bernoulli(p) is "word < floor(p * 2^64)" and a
+ *    uniform index in [0, n) is the high 64 bits of word * n.
+ *  - Spike accumulators (snn_propagate) are int64 fixed point with 40 fractional bits,
+ *    so their sums do not depend on the order of the atomic additions.
+ */
+#ifndef SNNSP_H
+#define SNNSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t snn_status;
+#define SNN_OK         0
+#define SNN_EINVAL    (-1)   /* bad argument (sizes, NULL, alignment, unsupported dtype) */
+#define SNN_ENOMEM    (-2)   /* library-owned scratch could not be allocated at create time */
+#define SNN_ECAPACITY (-3)   /* a row ran out of padding, or activations were left over */
+#define SNN_ECUDA     (-4)   /* a CUDA runtime call failed (message has the CUDA error) */
+#define SNN_ETIMEOUT  (-5)   /* a bounded device-side wait gave up */
+#define SNN_ESTATE    (-6)   /* device-detected invariant violation (bad index, bad row) */
+
+#define SNN_F32 0
+#define SNN_F64 1
+
+#define SNN_FIXED_FRAC_BITS 40   /* fractional bits of the int64 spike accumulators */
+
+typedef void* snn_stream;        /* cudaStream_t */
+
+/* Message for the most recent failing call on this host thread ("" if none). */
+const char* snn_last_error(void);
+/* ABI version of this header (bumped on any incompatible change). */
+int32_t snn_abi_version(void);
+
+/* ==================================================================================
+ * Ragged sparse matrix (Sec. 2.1, Fig. 1; DEEP R bitfields Sec. 2.1.2, Fig. 2)
+ * ================================================================================== */
+typedef struct {
+    int32_t P;            /* rows = presynaptic neurons */
+    int32_t Q;            /* postsynaptic neurons (targets are 0..Q-1) */
+    int32_t C;            /* capacity = maximum row length, padding included */
+    int32_t dtype;        /* SNN_F32 or SNN_F64: element type of w, m, v, grad */
+    int32_t no_autapse;   /* 1: target j == i is forbidden (recurrent projection) */
+    int32_t reserved;     /* must be 0 */
+    int32_t* row_len;     /* device [P] */
+    int32_t* ind;         /* device [P*C] target indices */
+    void* w;              /* device [P*C] weights / conductances */
+    void* m;              /* device [P*C] Adam first moment, or NULL */
+    void* v;              /* device [P*C] Adam second moment, or NULL */
+    void* grad;           /* device [P*C] gradient (written by snn_eprop_update), or NULL */
+    uint32_t* sign_bits;  /* device [P*ceil(Q/32)] DEEP R fixed signs, or NULL */
+    uint32_t* conn_bits;  /* device [P*ceil(Q/32)] DEEP R connectivity mirror, or NULL */
+    uint64_t seed;        /* Philox seed of this projection's structural plasticity */
+} snn_ragged_desc;
+
+typedef struct snn_ragged snn_ragged;
+
+/* Counts of one rewiring call, written to DEVICE memory by the rewire calls
+ * (accumulated: the caller zeroes it when it wants per-call numbers). */
+typedef struct {
+    int64_t removed;      /* synapses eliminated */
+    int64_t formed;       /* synapses created */
+    int64_t overflow;     /* formations skipped because a row was full / activations left over */
+    int64_t attempts;     /* rewiring attempts processed (topographic rule) */
+} snn_rewire_stats;
+
+/* Validate a ragged matrix and wrap it in a handle.  Checks on the device (and waits
+ * for the result): 0 <= row_len <= C, 0 <= ind < Q for live slots, no duplicate
+ * targets in a row, no self target when no_autapse.  If init_deepr_bitfields != 0,
+ * sign_bits and conn_bits must be given and are initialised as in Fig. 2A: all
+ * connectivity bits cleared, all sign bits drawn from Philox (purpose SIGN, counter
+ * (row, word, 0, 0), low 32 bits of word 0), then for every synapse its connectivity
+ * bit set and its sign bit forced to the sign of its weight (w > 0: set, w < 0: clear,
+ * w == 0: unchanged).  Allocates the handle's fixed scratch (O(P) words).  Returns
+ * SNN_EINVAL for bad sizes/pointers, SNN_ESTATE if the contents are invalid. */
+snn_status snn_create_ragged(const snn_ragged_desc* desc, int32_t init_deepr_bitfields,
+                             snn_stream stream, snn_ragged** out);
+snn_status snn_destroy_ragged(snn_ragged* r);
+/* Wait for `stream`, then return and clear the handle's device status word
+ * (SNN_OK, SNN_ECAPACITY, SNN_ESTATE or SNN_ETIMEOUT). */
+snn_status snn_ragged_status(snn_ragged* r, snn_stream stream);
+
+/* Spike propagation (Fig. 1): for every instance b < B and every row i whose bit is set
+ * in pre_bits[b] (device [B][ceil(P/32)]), add w[i][s] to post_acc[b][ind[i][s]] for
+ * s < row_len[i].  post_acc: device int64 [B][Q], fixed point (SNN_FIXED_FRAC_BITS),
+ * accumulated into (the caller zeroes it).  Weights are shared by all instances. */
+snn_status snn_propagate(const snn_ragged* r, const uint32_t* pre_bits, int32_t B,
+                         int64_t* post_acc, snn_stream stream);
+
+/* DEEP R rewiring after the optimiser step (Sec. 2.1.2, Fig. 2B-C).
+ *  elimination: slot s of row i is removed iff its weight's sign is strictly opposite
+ *    to sign bit (i, ind); rows are compacted stably (survivors keep their order;
+ *    w, m, v move with them); connectivity bits of removed synapses are cleared;
+ *  redistribution: D = sum of removed counts is spread over rows in rounds
+ *    r = 0..63: round r draws its remaining activations' rows (purpose DEEPR_DIST,
+ *    counter (rewire_idx, r, k/4, 0), word k%4, row = mulhi(u, P)); a row takes at most
+ *    min(C - row_len, free targets) in total; rejected activations go to round r+1;
+ *  formation: the k-th activation of row i appends the m-th free target (ascending;
+ *    the self target counts as taken when no_autapse), m = mulhi(u, n_free),
+ *    u = Philox(DEEPR_FORM, (rewire_idx, i, k, 0)) word 0, with w = m = v = 0.
+ * Needs w, m, v, sign_bits, conn_bits.  stats: device pointer or NULL.  Leftover
+ * activations after 64 rounds are counted in stats->overflow and set SNN_ECAPACITY in
+ * the status word. */
+snn_status snn_rewire_deepr(snn_ragged* r, int64_t rewire_idx, snn_rewire_stats* stats,
+                            snn_stream stream);
+
+/* ==================================================================================
+ * Recurrent LIF/ALIF classifier with e-prop (Sec. 2.2.1)
+ * ================================================================================== */
+typedef struct {
+    int32_t n_in, N, K;   /* input channels, hidden ALIF/LIF neurons, readouts (K <= 32) */
+    int32_t dtype;        /* SNN_F32 or SNN_F64 (all real arrays below and in the ragged
+                             handles use it) */
+    double tau_m;         /* membrane / readout / trace time constant (ms) */
+    double v_thr;         /* baseline threshold */
+    double beta;          /* adaptation strength (0 for LIF) */
+    double tau_a;         /* adaptation time constant (ms); <= 0 means LIF (rho = 0) */
+    double dt;            /* step (ms) */
+    int32_t n_classes, n_bins;
+    const uint64_t* in_thr;  /* device [n_classes][n_bins][n_in] Poisson thresholds */
+    uint64_t in_seed;        /* Philox seed of the input spikes (purpose INPUT) */
+    snn_ragged* w_in;        /* P = n_in, Q = N */
+    snn_ragged* w_rec;       /* P = N, Q = N, no_autapse = 1 */
+    void* W_out;             /* device [K][N] readout weights */
+    void* b_out;             /* device [K] readout biases */
+    void* W_out_m; void* W_out_v;   /* device [K][N] Adam moments, or NULL */
+    void* b_m; void* b_v;           /* device [K] Adam moments, or NULL */
+    void* G_out;             /* device [K][N] readout weight gradient (written) */
+    void* G_b;               /* device [K] readout bias gradient (written) */
+    int32_t max_B, max_T;    /* largest batch and trial length the scratch is sized for */
+} snn_classifier_desc;
+
+typedef struct snn_classifier snn_classifier;
+
+/* Per-batch state, records and workspace (all caller-owned device memory).
+ * Win = ceil(n_in/32), Wh = ceil(N/32), Kp = roundup(K, 4). */
+typedef struct {
+    int32_t B, T;              /* trials in the batch, steps per trial */
+    const int32_t* labels;     /* [B] class of each trial */
+    const int32_t* bin_len;    /* [B] steps per template bin (time warp), >= 1 */
+    const int64_t* trial_ids;  /* [B] Philox counter field of each trial's input */
+    void* v; void* a; void* y; /* [B][N], [B][N], [B][K] state (zero before step 0) */
+    uint32_t* x_bits;          /* [B][Win] input spikes of the last simulated step */
+    uint32_t* z_bits;          /* [B][Wh] hidden spikes of the last simulated step */
+    uint32_t* x_rec;           /* [B][T][Win] recorded input spikes */
+    uint32_t* z_rec;           /* [B][T][Wh] recorded hidden spikes */
+    void* psi_rec;             /* [B][T][N] recorded surrogate derivatives */
+    void* d_rec;               /* [B][T][K] recorded softmax(y) - onehot(label) */
+    void* ysum;                /* [B][K] sum over steps of y (prediction = argmax) */
+    void* v_rec; void* a_rec;  /* optional [B][T][N] voltage / adaptation records (NULL = off) */
+    void* y_rec;               /* optional [B][T][K] readout records (NULL = off) */
+    void* delta;               /* workspace [B][T][N] (e-prop adjoint) */
+    void* Dout;                /* workspace [B][T][Kp] (filtered readout error) */
+} snn_batch;
+
+typedef struct {
+    double lr, beta1, beta2, eps;
+    double b1t, b2t;          /* beta1^t, beta2^t of this step (running products) */
+    double l1;                /* DEEP R L1 strength (0: off); needs sign_bits */
+} snn_adam;
+
+#define SNN_EPROP_GRAD  0
+#define SNN_EPROP_APPLY 1
+
+/* Create a classifier handle; validates sizes and allocates fixed scratch for the
+ * e-prop gradient partial sums (sized from max_B, max_T and the two ragged handles). */
+snn_status snn_create_classifier(const snn_classifier_desc* desc, snn_classifier** out);
+snn_status snn_destroy_classifier(snn_classifier* c);
+
+/* Advance every trial of the batch by n_steps steps, t0 .. t0+n_steps-1 (t0 + n_steps
+ * <= T), in ONE launch (one CTA per trial).  Per step t (Sec. 2.2.1 equations with the
+ * one-step synaptic delay):
+ *   x^t    : input spikes, channel c fires iff Philox(INPUT; (trial_id, t, c/4, 0))[c%4]
+ *            < in_thr[label][min(n_bins-1, t / bin_len)][c]
+ *   I^t    : ragged propagation of x^{t-1} through w_in and z^{t-1} through w_rec
+ *   v, a, z, psi : v = alpha (v - z v_thr) + I, a = rho a + z_prev, A = v_thr + beta a,
+ *            z = [v >= A], psi = (0.3/v_thr) max(0, 1 - |v - A|/v_thr)
+ *   y^t    : alpha y + W_out z^{t-1} + b ;  d^t = softmax(y^t) - onehot(label)
+ * and records x, z, psi, d (and v, a, y when those pointers are set).  A label outside
+ * [0, n_classes) or a bin_len < 1 sets SNN_ESTATE in w_in's status word and the trial
+ * runs with the value clamped into range. */
+snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
+                            snn_stream stream);
+
+/* e-prop learning (Sec. 2.2.1 eligibility-trace equations, summed over trials).
+ * SNN_EPROP_GRAD: from the records of a finished batch (all T steps) computes
+ *   G^in, G^rec (into the ragged handles' grad arrays), G_out and G_b with the pairing
+ *   G_ji = sum_t L_j^{t+1} ebar_ji^t.  It evaluates the traces in adjoint form: a
+ *   reverse-time scan per hidden neuron builds delta_j^t such that
+ *   G_ji = sum over presynaptic spikes (b, t) of neuron i of delta_j^{b,t}, which is the
+ *   same sum reordered (equal up to rounding).
+ * SNN_EPROP_APPLY: adds L1 (l1 * (sign bit ? +1 : -1)) to ragged gradients of
+ *   projections with sign bits, then one Adam step on active ragged slots and on
+ *   W_out, b_out (needs the moment arrays). */
+snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase,
+                            const snn_adam* adam, snn_stream stream);
+
+/* ==================================================================================
+ * Topographic map (Sec. 2.1.3, Sec. 2.2.2, Tab. 1-2): conductance LIF target sheet,
+ * correlated Poisson source sheet, STDP and distance-dependent rewiring on a torus
+ * ================================================================================== */
+typedef struct {
+    int32_t L;            /* grid side; N = L*L neurons per sheet */
+    int32_t L_f;          /* stimulus tile side (L for a single focus) */
+    int32_t radius2;      /* squared focus radius (sites^2) */
+    int32_t t_stim;       /* steps between focus re-draws */
+    int32_t n_ref;        /* refractory steps */
+    int32_t reserved;
+    double dt, tau_m, V_rest, E_exc, V_theta, V_reset, tau_s, g_leak;
+    double f_base, f_in;             /* Hz outside / inside the focus */
+    double g_max, tau_plus, tau_minus, A_plus, A_minus;
+} snn_topo_params;
+
+typedef struct {
+    double p_form, sigma;            /* Gaussian formation probability */
+    double p_elim_dep, p_elim_pot;   /* elimination probabilities (clamped to [0,1]) */
+    double g_theta, g_new;           /* depression threshold, weight of new synapses */
+    int32_t L;                       /* torus side used for distances */
+    int32_t n_att;                   /* attempts per call */
+} snn_topo_rewire;
+
+/* Topographic network state (caller-owned device memory), N = L*L, Nw = ceil(N/32). */
+typedef struct {
+    float* V; float* gs; int32_t* ref;       /* [N] target sheet */
+    float* x_src; float* x_tgt;              /* [N] presynaptic STDP traces */
+    float* y; float* ydec;                   /* [N] postsynaptic trace, decayed copy */
+    uint32_t* src_bits; uint32_t* tgt_bits;  /* [2][Nw] spikes, parity t & 1 */
+    int64_t* acc;                            /* [N] conductance input (fixed point) */
+} snn_topo_state;
+
+/* Source sheet spikes of step t into src_bits[t&1] and x_src <- x_src e^{-dt/tau+} + s. */
+snn_status snn_topo_input(const snn_topo_params* p, const snn_topo_state* st, uint64_t seed,
+                          int64_t t, snn_stream stream);
+/* Target sheet step t: g <- g e^{-dt/tau_s} + acc (acc consumed and zeroed); refractory
+ * hold or exponential Euler; spikes into tgt_bits[t&1]; x_tgt, y, ydec traces. */
+snn_status snn_topo_neurons(const snn_topo_params* p, const snn_topo_state* st, int64_t t,
+                            snn_stream stream);
+/* All-to-all STDP for step t on one projection: depression of rows whose pre spiked
+ * (pre_bits) by A_- ydec[post], then potentiation of slots whose target spiked
+ * (post_bits) by A_+ x_pre[row], clamped to [0, g_max]. */
+snn_status snn_stdp_update(snn_ragged* r, const snn_topo_params* p, const uint32_t* pre_bits,
+                           const uint32_t* post_bits, const float* x_pre, const float* ydec,
+                           snn_stream stream);
+/* One rewiring update (Sec. 2.1.3): n_att attempts to rows (purpose TOPO_ATT, counter
+ * (rewire_idx, k/4, 0, 0), word k%4); per row a_r distinct candidates, the k-th being the
+ * m-th unselected target, m = mulhi(Philox(TOPO_CAND; (rewire_idx, i, k, 0)), Q - k);
+ * candidates with a synapse are eliminated iff R < thr(p_elim_dep if g < g_theta else
+ * p_elim_pot), the others formed iff R < thr(p_form exp(-d^2/2 sigma^2)) with g = g_new,
+ * R = Philox(TOPO_DRAW; (rewire_idx, i, j, 0)) word 0; rows compact stably; formations are
+ * appended in ascending target order; a full row counts overflow.  F32 only. */
+snn_status snn_rewire_topo(snn_ragged* r, const snn_topo_rewire* p, int64_t rewire_idx,
+                           snn_rewire_stats* stats, snn_stream stream);
+/* Run steps t0 .. t0+n_steps-1 of the full topographic network: input, propagation of
+ * the previous step's spikes (ff and lateral), neurons, STDP on both projections and,
+ * after every step with (t+1) % rewire_every == 0, snn_rewire_topo on ff then lateral
+ * with rewire index (t+1)/rewire_every - 1.  Kernel launches only; no host sync. */
+snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_ragged* ff,
+                        snn_ragged* lat, const snn_topo_rewire* rw_ff, const snn_topo_rewire* rw_lat,
+                        uint64_t input_seed, int32_t rewire_every, int64_t t0, int32_t n_steps,
+                        snn_rewire_stats* stats_ff, snn_rewire_stats* stats_lat, snn_stream stream);
+
+/* ==================================================================================
+ * Test hook
+ * ================================================================================== */
+/* out[k*4 + q] = word q of Philox4x64-10(key = (seed, purpose), counter = ctr[4k..4k+3])
+ * for k < n; ctr and out are device arrays. */
+snn_status snn_philox(uint64_t seed, uint64_t purpose, const uint64_t* ctr, int64_t n,
+                      uint64_t* out, snn_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNNSP_H */

@@ -132,8 +132,9 @@ class ClassifierNet:
 
 
 def forward_trial(net: ClassifierNet, thr: np.ndarray, label: int, bin_len: int, trial_id: int,
-                  seed: int, T: int, state: dict | None = None) -> dict:
-    """Simulate one trial for T steps; return per-step records.
+                  seed: int, T: int, state: dict | None = None, t0: int = 0) -> dict:
+    """Simulate steps t0 .. t0+T-1 of one trial from `state` (v, a, z, x, y of step
+    t0-1; zeros by default); return per-step records.
 
     records: x [T, n_in] (0/1), z [T, N], v, a, psi [T, N], y, pi, d [T, K],
     ysum [K] and the prediction argmax_k sum_t y_k^t.
@@ -148,7 +149,7 @@ def forward_trial(net: ClassifierNet, thr: np.ndarray, label: int, bin_len: int,
     onehot = np.zeros(net.K)
     onehot[int(label)] = 1.0
     rec = {k: [] for k in ("x", "z", "v", "a", "psi", "y", "pi", "d")}
-    for t in range(T):
+    for t in range(t0, t0 + T):
         x = poisson_input(thr, label, bin_len, trial_id, t, seed).astype(np.float64)
         I = propagate(net.in_len, net.in_ind, net.w_in, x_prev, net.N)
         propagate(net.rec_len, net.rec_ind, net.w_rec, z, net.N, out=I)
@@ -208,6 +209,29 @@ def eprop_gradients(net: ClassifierNet, x: np.ndarray, z: np.ndarray, psi: np.nd
         zbar_hid_prev = alpha * zbar_hid_prev + z[t]
         psi_prev = psi[t]
     return projs[0]["G"], projs[1]["G"], G_out, G_b
+
+
+def eprop_synapse(pre: np.ndarray, psi_post: np.ndarray, L_post: np.ndarray, p: NeuronParams) -> float:
+    """e-prop gradient of ONE synapse i -> j summed over trials, with the same trace
+    recursion as eprop_gradients but vectorised over trials instead of synapses.
+    pre: [B, T] presynaptic spikes, psi_post / L_post: [B, T] of the target neuron."""
+    alpha, rho, beta = p.alpha, p.rho, p.beta
+    B, T = pre.shape
+    zb1 = np.zeros(B)
+    zb2 = np.zeros(B)
+    eps = np.zeros(B)
+    ebar = np.zeros(B)
+    G = np.zeros(B)
+    psi_prev = np.zeros(B)
+    for t in range(T):
+        G += L_post[:, t] * ebar
+        eps = psi_prev * zb2 + (rho - psi_prev * beta) * eps
+        e = psi_post[:, t] * (zb1 - beta * eps)
+        ebar = alpha * ebar + e
+        zb2 = zb1
+        zb1 = alpha * zb1 + pre[:, t]
+        psi_prev = psi_post[:, t]
+    return float(G.sum())
 
 
 # ------------------------------------------------------------------------- optimiser

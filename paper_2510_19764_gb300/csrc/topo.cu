@@ -1,0 +1,434 @@
+// Topographic map (Sec. 2.1.3, Sec. 2.2.2, Tab. 1-2 of the paper): correlated Poisson
+// source sheet, conductance LIF target sheet with exponential Euler, all-to-all STDP
+// without a transpose (rows are scanned against the post-spike bitmask) and the
+// parallel rewiring rule (distance-dependent formation, weight-dependent elimination).
+#include "common.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace snn {
+
+struct TopoK {
+    int L, L_f, radius2, t_stim, n_ref, N, Nw;
+    float ds, dplus, dminus, dt_over_tau_m, V_rest, E_exc, V_theta, V_reset, g_leak, g_max, A_plus, A_minus;
+    uint64_t thr_in, thr_base;
+};
+
+static TopoK topo_consts(const snn_topo_params* p) {
+    TopoK k;
+    k.L = p->L;
+    k.L_f = p->L_f;
+    k.radius2 = p->radius2;
+    k.t_stim = p->t_stim;
+    k.n_ref = p->n_ref;
+    k.N = p->L * p->L;
+    k.Nw = (k.N + 31) / 32;
+    k.ds = (float)std::exp(-p->dt / p->tau_s);
+    k.dplus = (float)std::exp(-p->dt / p->tau_plus);
+    k.dminus = (float)std::exp(-p->dt / p->tau_minus);
+    k.dt_over_tau_m = (float)(p->dt / p->tau_m);
+    k.V_rest = (float)p->V_rest;
+    k.E_exc = (float)p->E_exc;
+    k.V_theta = (float)p->V_theta;
+    k.V_reset = (float)p->V_reset;
+    k.g_leak = (float)p->g_leak;
+    k.g_max = (float)p->g_max;
+    k.A_plus = (float)p->A_plus;
+    k.A_minus = (float)p->A_minus;
+    k.thr_in = prob_threshold(p->f_in * p->dt * 1e-3);
+    k.thr_base = prob_threshold(p->f_base * p->dt * 1e-3);
+    return k;
+}
+
+// Thread = 4 source channels (one Philox block); nibbles of 8 lanes form one word.
+__global__ void k_topo_input(TopoK k, uint64_t seed, long long t, uint32_t* __restrict__ bits,
+                             float* __restrict__ x_src) {
+    __shared__ int focus[2];
+    if (threadIdx.x == 0) {
+        const u64x4 f = philox(seed, PH_TOPO_FOCUS, (uint64_t)(t / k.t_stim), 0, 0, 0);
+        focus[0] = (int)mulhi_index(f.x, (uint64_t)k.L_f);
+        focus[1] = (int)mulhi_index(f.y, (uint64_t)k.L_f);
+    }
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_groups = (k.N + 3) >> 2;
+    uint32_t nib = 0;
+    if (g < n_groups) {
+        const u64x4 u = philox(seed, PH_TOPO_INPUT, (uint64_t)t, (uint64_t)g, 0, 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = 4 * g + q;
+            if (c < k.N) {
+                int dx = abs((c % k.L) % k.L_f - focus[0]);
+                int dy = abs((c / k.L) % k.L_f - focus[1]);
+                dx = min(dx, k.L_f - dx);
+                dy = min(dy, k.L_f - dy);
+                const uint64_t thr = (dx * dx + dy * dy <= k.radius2) ? k.thr_in : k.thr_base;
+                const bool s = u[q] < thr;
+                if (s) nib |= 1u << q;
+                x_src[c] = x_src[c] * k.dplus + (s ? 1.0f : 0.0f);
+            }
+        }
+    }
+    uint32_t word = nib << (4 * (g & 7));
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+    if ((g & 7) == 0 && (g >> 3) < k.Nw) bits[g >> 3] = word;
+}
+
+__global__ void k_topo_neurons(TopoK k, float* __restrict__ V, float* __restrict__ gs, int32_t* __restrict__ ref,
+                               float* __restrict__ x_tgt, float* __restrict__ y, float* __restrict__ ydec,
+                               long long* __restrict__ acc, uint32_t* __restrict__ bits) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    bool z = false;
+    if (j < k.N) {
+        const float I = (float)((double)acc[j] * FIX_INV);
+        acc[j] = 0;
+        const float g = gs[j] * k.ds + I;
+        gs[j] = g;
+        float v = V[j];
+        int r = ref[j];
+        if (r > 0) {
+            v = k.V_reset;
+            ref[j] = r - 1;
+        } else {
+            const float geff = g / k.g_leak;
+            const float vinf = (k.V_rest + geff * k.E_exc) / (1.0f + geff);
+            v = vinf + (v - vinf) * expf(-k.dt_over_tau_m * (1.0f + geff));
+            if (v >= k.V_theta) {
+                z = true;
+                v = k.V_reset;
+                ref[j] = k.n_ref;
+            }
+        }
+        V[j] = v;
+        const float yd = y[j] * k.dminus;
+        ydec[j] = yd;
+        y[j] = yd + (z ? 1.0f : 0.0f);
+        x_tgt[j] = x_tgt[j] * k.dplus + (z ? 1.0f : 0.0f);
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, z);
+    if ((threadIdx.x & 31) == 0 && (j >> 5) < k.Nw) bits[j >> 5] = m;
+}
+
+// Warp per row: depression if the row's neuron spiked, potentiation of slots whose
+// target spiked; per synapse depression comes first, then potentiation.
+__global__ void k_stdp(const int32_t* __restrict__ len, const int32_t* __restrict__ ind, float* __restrict__ w,
+                       int P, int C, const uint32_t* __restrict__ pre_bits, const uint32_t* __restrict__ post_bits,
+                       const float* __restrict__ x_pre, const float* __restrict__ ydec, float A_plus, float A_minus,
+                       float g_max) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= P) return;
+    const bool pre = (pre_bits[i >> 5] >> (i & 31)) & 1u;
+    const int n = len[i];
+    const float xp = x_pre[i];
+    for (int s = lane_id(); s < n; s += 32) {
+        const size_t o = (size_t)i * C + s;
+        const int j = ind[o];
+        const bool post = (post_bits[j >> 5] >> (j & 31)) & 1u;
+        if (!pre && !post) continue;
+        float g = w[o];
+        if (pre) g = fmaxf(0.0f, g - A_minus * ydec[j]);
+        if (post) g = fminf(g_max, g + A_plus * xp);
+        w[o] = g;
+    }
+}
+
+struct RewireK {
+    int P, Q, C, Qw, L, n_att;
+    float g_theta, g_new;
+    uint64_t thr_dep, thr_pot;
+    uint64_t seed, rewire;
+};
+
+__device__ __forceinline__ int torus_d2(int i, int j, int L) {
+    int dx = abs(i % L - j % L), dy = abs(i / L - j / L);
+    dx = min(dx, L - dx);
+    dy = min(dy, L - dy);
+    return dx * dx + dy * dy;
+}
+
+// One CTA.  Histogram of attempt rows, then one warp per row with attempts: candidate
+// selection without replacement in a warp-private shared-memory bitfield, stable
+// elimination by ballot compaction, and formation of the remaining candidates in
+// ascending target order.
+__global__ void __launch_bounds__(1024)
+    k_topo_rewire(RewireK k, int32_t* __restrict__ len, int32_t* __restrict__ ind, float* __restrict__ w,
+                  const uint64_t* __restrict__ thr_form, int32_t* status, snn_rewire_stats* stats) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* att = (int*)smem;                       // [P]
+    int* list = att + k.P;                       // [n_att]
+    int* n_rows = list + k.n_att;                // [1]
+    uint32_t* cand_all = (uint32_t*)(n_rows + 1);   // [warps][Qw]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int i = tid; i < k.P; i += blockDim.x) att[i] = 0;
+    if (tid == 0) *n_rows = 0;
+    __syncthreads();
+    for (int g = tid; g < (k.n_att + 3) / 4; g += blockDim.x) {
+        const u64x4 u = philox(k.seed, PH_TOPO_ATT, k.rewire, (uint64_t)g, 0, 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * g + q < k.n_att) atomicAdd(&att[(int)mulhi_index(u[q], (uint64_t)k.P)], 1);
+    }
+    __syncthreads();
+    for (int i = tid; i < k.P; i += blockDim.x)
+        if (att[i] > 0) list[atomicAdd(n_rows, 1)] = i;
+    __syncthreads();
+    const int nr = *n_rows;
+    uint32_t* cand = cand_all + (size_t)warp * k.Qw;
+    const uint32_t tail_mask = (k.Q & 31) ? ~((1u << (k.Q & 31)) - 1u) : 0u;
+    long long removed = 0, formed = 0, overflow = 0, attempts = 0;
+    for (int li = warp; li < nr; li += nwarps) {
+        const int i = list[li];
+        const int a = min(att[i], k.Q);
+        attempts += a;
+        for (int wi = lane; wi < k.Qw; wi += 32) cand[wi] = 0u;
+        __syncwarp();
+        // candidates without replacement: the kk-th is the m-th unselected target
+        for (int kk = 0; kk < a; ++kk) {
+            const u64x4 u = philox(k.seed, PH_TOPO_CAND, k.rewire, (uint64_t)i, (uint64_t)kk, 0);
+            const int mth = (int)mulhi_index(u.x, (uint64_t)(k.Q - kk));
+            int seen = 0, target = -1;
+            for (int wb = 0; wb < k.Qw && target < 0; wb += 32) {
+                const int wi = wb + lane;
+                uint32_t word = 0xffffffffu;
+                if (wi < k.Qw) {
+                    word = cand[wi];
+                    if (wi == k.Qw - 1) word |= tail_mask;
+                }
+                const int zeros = __popc(~word);
+                const int incl = warp_incl_scan(zeros);
+                const int excl = incl - zeros;
+                const uint32_t hm = __ballot_sync(0xffffffffu, mth >= seen + excl && mth < seen + incl);
+                if (hm) {
+                    const int src = __ffs(hm) - 1;
+                    int tg = -1;
+                    if (lane == src) tg = wi * 32 + nth_set_bit(~word, mth - seen - excl);
+                    target = __shfl_sync(0xffffffffu, tg, src);
+                }
+                seen += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0 && target >= 0) cand[target >> 5] |= 1u << (target & 31);
+            if (target < 0 && lane == 0) atomicOr(status, ST_STATE);
+            __syncwarp();
+        }
+        // elimination of existing synapses on candidates
+        const int n = len[i];
+        const size_t row = (size_t)i * k.C;
+        int wp = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int s = base + lane;
+            const bool valid = s < n;
+            int j = 0;
+            float g = 0.0f;
+            bool is_c = false, rm = false;
+            if (valid) {
+                j = ind[row + s];
+                g = w[row + s];
+                is_c = (cand[j >> 5] >> (j & 31)) & 1u;
+                if (is_c) {
+                    const u64x4 u = philox(k.seed, PH_TOPO_DRAW, k.rewire, (uint64_t)i, (uint64_t)j, 0);
+                    rm = u.x < (g < k.g_theta ? k.thr_dep : k.thr_pot);
+                }
+            }
+            const bool keep = valid && !rm;
+            const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+            removed += rm ? 1 : 0;
+            __syncwarp();
+            if (is_c) atomicAnd(&cand[j >> 5], ~(1u << (j & 31)));
+            if (keep) {
+                const int pos = wp + __popc(mask & lanemask_lt());
+                ind[row + pos] = j;
+                w[row + pos] = g;
+            }
+            wp += __popc(mask);
+            __syncwarp();
+        }
+        // formation of the remaining candidates, ascending target order
+        for (int wb = 0; wb < k.Qw; wb += 32) {
+            const int wi = wb + lane;
+            uint32_t word = (wi < k.Qw) ? cand[wi] : 0u;
+            uint32_t pass = 0;
+            for (uint32_t rest = word; rest; rest &= rest - 1u) {
+                const int bpos = __ffs(rest) - 1;
+                const int j = wi * 32 + bpos;
+                const u64x4 u = philox(k.seed, PH_TOPO_DRAW, k.rewire, (uint64_t)i, (uint64_t)j, 0);
+                if (u.x < thr_form[torus_d2(i, j, k.L)]) pass |= 1u << bpos;
+            }
+            const int cnt = __popc(pass);
+            const int incl = warp_incl_scan(cnt);
+            int rank = incl - cnt;
+            for (uint32_t rest = pass; rest; rest &= rest - 1u, ++rank) {
+                const int j = wi * 32 + __ffs(rest) - 1;
+                const int slot = wp + rank;
+                if (slot < k.C) {
+                    ind[row + slot] = j;
+                    w[row + slot] = k.g_new;
+                    ++formed;
+                } else {
+                    ++overflow;
+                }
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            wp = min(wp + total, k.C);
+            if (wi < k.Qw) cand[wi] = 0u;
+            __syncwarp();
+        }
+        if (lane == 0) len[i] = wp;
+    }
+    removed = warp_sum(removed);
+    formed = warp_sum(formed);
+    overflow = warp_sum(overflow);
+    attempts = lane == 0 ? attempts : 0;
+    attempts = warp_sum(attempts);
+    if (lane == 0 && stats && (removed | formed | overflow | attempts)) {
+        atomicAdd((unsigned long long*)&stats->removed, (unsigned long long)removed);
+        atomicAdd((unsigned long long*)&stats->formed, (unsigned long long)formed);
+        atomicAdd((unsigned long long*)&stats->overflow, (unsigned long long)overflow);
+        atomicAdd((unsigned long long*)&stats->attempts, (unsigned long long)attempts);
+    }
+}
+
+static snn_status check_topo(const snn_topo_params* p) {
+    SNN_REQUIRE(p, "topo: NULL parameters");
+    SNN_REQUIRE(p->L > 0 && p->L_f > 0 && p->L % p->L_f == 0, "topo: need L > 0 and L a multiple of L_f");
+    SNN_REQUIRE(p->t_stim > 0 && p->n_ref >= 0 && p->dt > 0 && p->tau_m > 0 && p->tau_s > 0 && p->g_leak > 0,
+                "topo: bad time constants");
+    return SNN_OK;
+}
+
+static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t rewire_idx, snn_rewire_stats* stats,
+                                cudaStream_t s) {
+    const snn_ragged_desc& d = r->d;
+    SNN_REQUIRE(d.dtype == SNN_F32, "snn_rewire_topo: F32 ragged matrices only");
+    SNN_REQUIRE(p->L > 0 && (long long)p->L * p->L == d.Q && d.P == d.Q,
+                "snn_rewire_topo: the matrix must be L*L x L*L (got P=%d Q=%d L=%d)", d.P, d.Q, p->L);
+    SNN_REQUIRE(p->n_att >= 0 && p->n_att <= 65536, "snn_rewire_topo: n_att must be in [0, 65536]");
+    SNN_REQUIRE(p->sigma > 0, "snn_rewire_topo: sigma must be > 0");
+    const int max_d2 = 2 * (p->L / 2) * (p->L / 2);
+    SNN_REQUIRE(max_d2 + 1 <= r->thr_cap, "snn_rewire_topo: distance table does not fit");
+    if (r->thr_L != p->L || r->thr_p != p->p_form || r->thr_sigma != p->sigma) {
+        // formation thresholds by squared distance, computed once per parameter set on
+        // the host in double precision (the first call with new parameters copies them)
+        std::vector<uint64_t> tab(max_d2 + 1);
+        for (int d2 = 0; d2 <= max_d2; ++d2)
+            tab[d2] = prob_threshold(p->p_form * std::exp(-(double)d2 / (2.0 * p->sigma * p->sigma)));
+        SNN_CUDA(cudaMemcpyAsync(r->thr_form, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+        r->thr_L = p->L;
+        r->thr_p = p->p_form;
+        r->thr_sigma = p->sigma;
+    }
+    RewireK k;
+    k.P = d.P;
+    k.Q = d.Q;
+    k.C = d.C;
+    k.Qw = r->Qw;
+    k.L = p->L;
+    k.n_att = p->n_att;
+    k.g_theta = (float)p->g_theta;
+    k.g_new = (float)p->g_new;
+    k.thr_dep = prob_threshold(p->p_elim_dep);
+    k.thr_pot = prob_threshold(p->p_elim_pot);
+    k.seed = d.seed;
+    k.rewire = (uint64_t)rewire_idx;
+    const int threads = 1024;
+    size_t smem = (size_t)(k.P + k.n_att + 1) * 4 + (size_t)(threads / 32) * k.Qw * 4;
+    SNN_REQUIRE(smem <= 227 * 1024, "snn_rewire_topo: P = %d too large for one CTA", k.P);
+    if (smem > 48 * 1024)
+        SNN_CUDA(cudaFuncSetAttribute(k_topo_rewire, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_topo_rewire<<<1, threads, smem, s>>>(k, d.row_len, d.ind, (float*)d.w, r->thr_form, r->status, stats);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+}  // namespace snn
+
+using namespace snn;
+
+extern "C" {
+
+snn_status snn_topo_input(const snn_topo_params* p, const snn_topo_state* st, uint64_t seed, int64_t t,
+                          snn_stream stream) {
+    clear_error();
+    snn_status e = check_topo(p);
+    if (e != SNN_OK) return e;
+    SNN_REQUIRE(st && st->src_bits && st->x_src && t >= 0, "snn_topo_input: bad argument");
+    TopoK k = topo_consts(p);
+    const int groups = (k.N + 3) / 4;
+    k_topo_input<<<ceil_div(groups, 256), 256, 0, (cudaStream_t)stream>>>(k, seed, t, st->src_bits + (t & 1) * k.Nw,
+                                                                          st->x_src);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+snn_status snn_topo_neurons(const snn_topo_params* p, const snn_topo_state* st, int64_t t, snn_stream stream) {
+    clear_error();
+    snn_status e = check_topo(p);
+    if (e != SNN_OK) return e;
+    SNN_REQUIRE(st && st->V && st->gs && st->ref && st->x_tgt && st->y && st->ydec && st->acc && st->tgt_bits && t >= 0,
+                "snn_topo_neurons: bad argument");
+    TopoK k = topo_consts(p);
+    k_topo_neurons<<<ceil_div(k.N, 256), 256, 0, (cudaStream_t)stream>>>(k, st->V, st->gs, st->ref, st->x_tgt, st->y,
+                                                                        st->ydec, (long long*)st->acc,
+                                                                        st->tgt_bits + (t & 1) * k.Nw);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+snn_status snn_stdp_update(snn_ragged* r, const snn_topo_params* p, const uint32_t* pre_bits, const uint32_t* post_bits,
+                           const float* x_pre, const float* ydec, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(r && p && pre_bits && post_bits && x_pre && ydec, "snn_stdp_update: NULL argument");
+    SNN_REQUIRE(r->d.dtype == SNN_F32, "snn_stdp_update: F32 only");
+    const snn_ragged_desc& d = r->d;
+    k_stdp<<<ceil_div((long long)d.P * 32, 256), 256, 0, (cudaStream_t)stream>>>(
+        d.row_len, d.ind, (float*)d.w, d.P, d.C, pre_bits, post_bits, x_pre, ydec, (float)p->A_plus,
+        (float)p->A_minus, (float)p->g_max);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+snn_status snn_rewire_topo(snn_ragged* r, const snn_topo_rewire* p, int64_t rewire_idx, snn_rewire_stats* stats,
+                           snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(r && p && rewire_idx >= 0, "snn_rewire_topo: bad argument");
+    return rewire_launch(r, p, rewire_idx, stats, (cudaStream_t)stream);
+}
+
+snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_ragged* ff, snn_ragged* lat,
+                        const snn_topo_rewire* rw_ff, const snn_topo_rewire* rw_lat, uint64_t input_seed,
+                        int32_t rewire_every, int64_t t0, int32_t n_steps, snn_rewire_stats* stats_ff,
+                        snn_rewire_stats* stats_lat, snn_stream stream) {
+    clear_error();
+    snn_status e = check_topo(p);
+    if (e != SNN_OK) return e;
+    SNN_REQUIRE(st && ff && lat && rw_ff && rw_lat && rewire_every > 0 && t0 >= 0 && n_steps >= 0,
+                "snn_topo_run: bad argument");
+    const int N = p->L * p->L, Nw = (N + 31) / 32;
+    SNN_REQUIRE(ff->d.P == N && ff->d.Q == N && lat->d.P == N && lat->d.Q == N,
+                "snn_topo_run: projections must be N x N with N = L*L");
+    for (int64_t t = t0; t < t0 + n_steps; ++t) {
+        const int cur = (int)(t & 1), prv = cur ^ 1;
+        if ((e = snn_topo_input(p, st, input_seed, t, stream)) != SNN_OK) return e;
+        if ((e = snn_propagate(ff, st->src_bits + prv * Nw, 1, st->acc, stream)) != SNN_OK) return e;
+        if ((e = snn_propagate(lat, st->tgt_bits + prv * Nw, 1, st->acc, stream)) != SNN_OK) return e;
+        if ((e = snn_topo_neurons(p, st, t, stream)) != SNN_OK) return e;
+        if ((e = snn_stdp_update(ff, p, st->src_bits + cur * Nw, st->tgt_bits + cur * Nw, st->x_src, st->ydec,
+                                 stream)) != SNN_OK)
+            return e;
+        if ((e = snn_stdp_update(lat, p, st->tgt_bits + cur * Nw, st->tgt_bits + cur * Nw, st->x_tgt, st->ydec,
+                                 stream)) != SNN_OK)
+            return e;
+        if ((t + 1) % rewire_every == 0) {
+            const int64_t ridx = (t + 1) / rewire_every - 1;
+            if ((e = snn_rewire_topo(ff, rw_ff, ridx, stats_ff, stream)) != SNN_OK) return e;
+            if ((e = snn_rewire_topo(lat, rw_lat, ridx, stats_lat, stream)) != SNN_OK) return e;
+        }
+    }
+    return SNN_OK;
+}
+
+}  // extern "C"

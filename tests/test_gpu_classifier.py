@@ -1,0 +1,248 @@
+"""GPU parity of the classifier path: forward (raster, voltages, readout), e-prop
+gradient, L1 + Adam, and a full e-prop + DEEP R training run against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import classifier as oc
+from oracle import deepr as od
+from tests import _setups
+
+pytestmark = pytest.mark.gpu
+
+F32, F64 = 0, 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2510_19764_gb300 import abi, build
+    build.build()
+    abi.load()
+
+
+def _run_forward(s, B, T, seed=0, batch_idx=0, record_state=True):
+    from paper_2510_19764_gb300 import abi, net
+    tb = synth.trial_batch(s.task, seed, batch_idx, B)
+    batch = net.DeviceBatch(s.dev, tb.labels, tb.bin_len, tb.trial_ids, T, record_state=record_state)
+    abi.snn_step_neurons(s.dev.handle, batch.desc, 0, T)
+    torch.cuda.synchronize()
+    return tb, batch
+
+
+def _host(batch, s):
+    from paper_2510_19764_gb300 import net
+    n_in, N = s.onet.n_in, s.onet.N
+    out = {"x": net.spikes_from_bits(net.u32_to_numpy(batch.x_rec), n_in).astype(np.float64),
+           "z": net.spikes_from_bits(net.u32_to_numpy(batch.z_rec), N).astype(np.float64),
+           "psi": batch.psi_rec.double().cpu().numpy(), "d": batch.d_rec.double().cpu().numpy(),
+           "ysum": batch.ysum.double().cpu().numpy()}
+    if batch.v_rec is not None:
+        out.update(v=batch.v_rec.double().cpu().numpy(), a=batch.a_rec.double().cpu().numpy(),
+                   y=batch.y_rec.double().cpu().numpy())
+    return out
+
+
+@pytest.mark.parametrize("lif", [True, False])
+def test_forward_f64_raster_exact(lif):
+    """FP64 build: input and hidden rasters identical to the oracle's, continuous
+    records equal up to the fixed-point accumulator quantisation."""
+    T, B = 200, 4
+    s = _setups.classifier(seed=0, dtype=F64, lif=lif, v_thr=1.0 if lif else 0.6, T=T, max_B=B)
+    tb, batch = _run_forward(s, B, T)
+    g = _host(batch, s)
+    total = 0
+    for b in range(B):
+        r = oc.forward_trial(s.onet, s.task.thr, tb.labels[b], tb.bin_len[b], tb.trial_ids[b], s.in_seed, T)
+        np.testing.assert_array_equal(g["x"][b], r["x"])
+        np.testing.assert_array_equal(g["z"][b], r["z"])
+        for k in ("v", "a", "psi", "y", "d"):
+            np.testing.assert_allclose(g[k][b], r[k], rtol=1e-9, atol=1e-9)
+        np.testing.assert_allclose(g["ysum"][b], r["ysum"], rtol=1e-9, atol=1e-9)
+        total += r["z"].sum()
+    assert total > 0
+
+
+@pytest.mark.parametrize("lif", [True, False])
+def test_forward_f32_per_step(lif):
+    """FP32: from the kernel's own state at t-1, one oracle step reproduces step t:
+    input spikes exactly, v, a, y, psi, d within 1e-5 relative, spikes except where the
+    margin to threshold is below the FP32 error."""
+    T, B, n_in, N, K = 80, 3, 100, 128, 8
+    s = _setups.classifier(seed=4, dtype=F32, lif=lif, v_thr=0.6, T=T, max_B=B, n_in=n_in, N=N, K=K,
+                           n_classes=5, n_bins=4, spoken=True, p_in=0.2, p_rec=0.1, w_scale=1.5)
+    tb, batch = _run_forward(s, B, T)
+    g = _host(batch, s)
+    flips = 0
+    for b in range(B):
+        for t in range(1, T):
+            st = {"v": g["v"][b, t - 1], "a": g["a"][b, t - 1], "z": g["z"][b, t - 1], "x": g["x"][b, t - 1],
+                  "y": g["y"][b, t - 1]}
+            r = oc.forward_trial(s.onet, s.task.thr, tb.labels[b], tb.bin_len[b], tb.trial_ids[b], s.in_seed, 1,
+                                 state=st, t0=t)
+            np.testing.assert_array_equal(g["x"][b, t], r["x"][0])
+            for k in ("v", "a", "psi", "y", "d"):
+                np.testing.assert_allclose(g[k][b, t], r[k][0], rtol=1e-5, atol=1e-6)
+            A = s.onet.neuron.v_thr + s.onet.neuron.beta * r["a"][0]
+            differ = g["z"][b, t] != r["z"][0]
+            assert np.all(np.abs(r["v"][0] - A)[differ] < 1e-5)
+            flips += differ.sum()
+    assert flips <= 2
+    assert g["z"].sum() > 50
+
+
+@pytest.mark.parametrize("dtype,lif", [(F64, True), (F64, False), (F32, False)])
+def test_eprop_gradient_matches_trace_form(dtype, lif):
+    """The adjoint/event form on the GPU equals the oracle's forward-trace e-prop
+    gradients computed from the same records, summed over trials."""
+    from paper_2510_19764_gb300 import abi
+    T, B, n_in, N, K = 120, 5, 60, 96, 6
+    s = _setups.classifier(seed=9, dtype=dtype, lif=lif, v_thr=0.6, T=T, max_B=B, n_in=n_in, N=N, K=K,
+                           n_classes=3, n_bins=3, spoken=True, p_in=0.2, p_rec=0.15, w_scale=1.5)
+    tb, batch = _run_forward(s, B, T, record_state=False)
+    abi.snn_eprop_update(s.dev.handle, batch.desc, abi.SNN_EPROP_GRAD, None)
+    torch.cuda.synchronize()
+    g = _host(batch, s)
+    Gi = np.zeros(s.in_rag.w.shape)
+    Gr = np.zeros(s.rec_rag.w.shape)
+    Go = np.zeros((K, N))
+    Gb = np.zeros(K)
+    for b in range(B):
+        a, r_, o, bb = oc.eprop_gradients(s.onet, g["x"][b], g["z"][b], g["psi"][b], g["d"][b])
+        Gi += a
+        Gr += r_
+        Go += o
+        Gb += bb
+    tol = 1e-9 if dtype == F64 else 2e-5
+    for got, ref, rag in ((s.dev.w_in.grad, Gi, s.in_rag), (s.dev.w_rec.grad, Gr, s.rec_rag)):
+        got = got.double().cpu().numpy()
+        mask = np.arange(rag.C)[None] < rag.row_len[:, None]
+        scale = np.abs(ref[mask]).max()
+        assert scale > 0
+        np.testing.assert_allclose(got[mask], ref[mask], rtol=0, atol=tol * scale)
+    np.testing.assert_allclose(s.dev.G_out.double().cpu().numpy(), Go, rtol=0, atol=tol * np.abs(Go).max())
+    np.testing.assert_allclose(s.dev.G_b.double().cpu().numpy(), Gb, rtol=0, atol=tol * max(1.0, np.abs(Gb).max()))
+
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_adam_l1_apply(dtype):
+    from paper_2510_19764_gb300 import abi, net
+    s = _setups.classifier(seed=2, dtype=dtype, lif=False, T=10, max_B=1, n_in=50, N=70, K=5)
+    rng = np.random.default_rng(3)
+    host = {}
+    for name, d, rag in (("in", s.dev.w_in, s.in_rag), ("rec", s.dev.w_rec, s.rec_rag)):
+        G = _setups.as_dtype(rng.normal(0, 1, rag.w.shape), dtype)
+        m0 = _setups.as_dtype(rng.normal(0, 0.1, rag.w.shape), dtype)
+        v0 = _setups.as_dtype(rng.random(rag.w.shape) * 0.01, dtype)
+        d.grad.copy_(torch.as_tensor(G))
+        d.m.copy_(torch.as_tensor(m0))
+        d.v.copy_(torch.as_tensor(v0))
+        host[name] = (G, m0, v0, net.u32_to_numpy(d.sign_bits), rag)
+    Go = _setups.as_dtype(rng.normal(size=(5, 70)), dtype)
+    Gb = _setups.as_dtype(rng.normal(size=5), dtype)
+    s.dev.G_out.copy_(torch.as_tensor(Go))
+    s.dev.G_b.copy_(torch.as_tensor(Gb))
+    W0 = s.dev.W_out.double().cpu().numpy()
+    b0 = s.dev.b_out.double().cpu().numpy()
+    ad = net.adam_params(1e-3, 3, l1=1e-2, b1t=0.9 ** 3, b2t=0.999 ** 3)
+    abi.snn_eprop_update(s.dev.handle, None, abi.SNN_EPROP_APPLY, ad)
+    torch.cuda.synchronize()
+    # FP32: each stored value is within a few float32 ulps of the FP64 update; moments
+    # that cancel towards zero keep the absolute error of their terms (|m|, |v| <~ 1)
+    rtol, atol = (1e-6, 1e-7) if dtype == F32 else (1e-13, 1e-15)
+    for name, d in (("in", s.dev.w_in), ("rec", s.dev.w_rec)):
+        G, m0, v0, sign, rag = host[name]
+        Gl = oc.l1_on_sign(G, rag.row_len, rag.ind, sign, 1e-2)
+        w, m, v = oc.adam_ragged(rag.w, m0, v0, Gl, rag.row_len, 1e-3, 0.9 ** 3, 0.999 ** 3)
+        mask = np.arange(rag.C)[None] < rag.row_len[:, None]
+        for got, ref in ((d.w, w), (d.m, m), (d.v, v)):
+            np.testing.assert_allclose(got.double().cpu().numpy()[mask], ref[mask], rtol=rtol, atol=atol)
+    w, m, v = oc.adam(W0, 0 * W0, 0 * W0, Go, 1e-3, 0.9 ** 3, 0.999 ** 3)
+    np.testing.assert_allclose(s.dev.W_out.double().cpu().numpy(), w, rtol=rtol, atol=atol)
+    w, m, v = oc.adam(b0, 0 * b0, 0 * b0, Gb, 1e-3, 0.9 ** 3, 0.999 ** 3)
+    np.testing.assert_allclose(s.dev.b_out.double().cpu().numpy(), w, rtol=rtol, atol=atol)
+
+
+def _oracle_train(s, batches, lr, l1, T):
+    """Oracle training run: per batch forward all trials, sum gradients, L1 + Adam,
+    DEEP R on both projections (bitfields from the oracle's own init)."""
+    n = s.onet
+    seed_in, seed_rec = s.dev.w_in.desc.seed, s.dev.w_rec.desc.seed
+    sign_in = od.init_bitfields(n.in_len, n.in_ind, n.w_in, n.N, seed_in)[0]
+    sign_rec = od.init_bitfields(n.rec_len, n.rec_ind, n.w_rec, n.N, seed_rec)[0]
+    st = {"in": [n.in_len.copy(), n.in_ind.copy(), n.w_in.copy(), np.zeros_like(n.w_in), np.zeros_like(n.w_in)],
+          "rec": [n.rec_len.copy(), n.rec_ind.copy(), n.w_rec.copy(), np.zeros_like(n.w_rec), np.zeros_like(n.w_rec)]}
+    conn = {"in": od.init_bitfields(n.in_len, n.in_ind, n.w_in, n.N, 0)[1],
+            "rec": od.init_bitfields(n.rec_len, n.rec_ind, n.w_rec, n.N, 0)[1]}
+    sign = {"in": sign_in, "rec": sign_rec}
+    W, b = n.W_out.copy(), n.b_out.copy()
+    mW, vW, mb, vb = np.zeros_like(W), np.zeros_like(W), np.zeros_like(b), np.zeros_like(b)
+    b1t = b2t = 1.0
+    rasters, preds = [], []
+    for bi, tb in enumerate(batches):
+        net_b = oc.ClassifierNet(n.n_in, n.N, n.K, st["in"][0], st["in"][1], st["in"][2], st["rec"][0],
+                                 st["rec"][1], st["rec"][2], W, b, n.neuron)
+        G = {"in": 0, "rec": 0}
+        Go, Gb = 0, 0
+        for k in range(len(tb.labels)):
+            r = oc.forward_trial(net_b, s.task.thr, tb.labels[k], tb.bin_len[k], tb.trial_ids[k], s.in_seed, T)
+            rasters.append(r["z"])
+            preds.append(r["pred"])
+            gi, gr, go, gb = oc.eprop_gradients(net_b, r["x"], r["z"], r["psi"], r["d"])
+            G["in"] = G["in"] + gi
+            G["rec"] = G["rec"] + gr
+            Go, Gb = Go + go, Gb + gb
+        b1t *= 0.9
+        b2t *= 0.999
+        for name in ("in", "rec"):
+            rl, ind, w, m, v = st[name]
+            Gl = oc.l1_on_sign(G[name], rl, ind, sign[name], l1)
+            w, m, v = oc.adam_ragged(w, m, v, Gl, rl, lr, b1t, b2t)
+            out = od.rewire(rl, ind, w, m, v, sign[name], conn[name], w.shape[1], n.N, name == "rec",
+                            seed_in if name == "in" else seed_rec, bi)
+            st[name] = [out["row_len"], out["ind"], out["w"], out["m"], out["v"]]
+            conn[name] = out["conn"]
+        W, mW, vW = oc.adam(W, mW, vW, Go, lr, b1t, b2t)
+        b, mb, vb = oc.adam(b, mb, vb, Gb, lr, b1t, b2t)
+    return st, conn, W, b, rasters, preds
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_training_run_tiny_config(dtype):
+    """32 Poisson inputs -> 64 LIF (v_thr 1) -> 4 readouts, 200 steps, 10 trials of batch
+    1 with e-prop, L1 1e-5, Adam lr 1e-3 and DEEP R after every trial.  FP64: every
+    raster and the final connectivity equal the oracle's exactly; FP32: >= 99.9 % spike
+    agreement and identical predictions."""
+    from paper_2510_19764_gb300 import abi, net
+    T, n_trials, lr, l1 = 200, 10, 1e-3, 1e-5
+    s = _setups.classifier(seed=0, dtype=dtype, lif=True, v_thr=1.0, T=T, max_B=1, w_scale=1.5)
+    batches = [synth.trial_batch(s.task, 0, i, 1) for i in range(n_trials)]
+    g_rasters, g_preds = [], []
+    batch = net.DeviceBatch(s.dev, batches[0].labels, batches[0].bin_len, batches[0].trial_ids, T)
+    for i, tb in enumerate(batches):
+        batch.set_trials(tb.labels, tb.bin_len, tb.trial_ids)
+        net.train_batch(s.dev, batch, net.adam_params(lr, i + 1, l1=l1), i)
+        torch.cuda.synchronize()
+        g_rasters.append(net.spikes_from_bits(net.u32_to_numpy(batch.z_rec[0]), s.onet.N).astype(np.float64))
+        g_preds.append(int(np.argmax(batch.ysum[0].double().cpu().numpy())))
+    assert s.dev.w_in.status() == abi.SNN_OK and s.dev.w_rec.status() == abi.SNN_OK
+    st, conn, W, b, rasters, preds = _oracle_train(s, batches, lr, l1, T)
+    total = sum(r.sum() for r in rasters)
+    assert total > 100
+    if dtype == F64:
+        for gr, r in zip(g_rasters, rasters):
+            np.testing.assert_array_equal(gr, r)
+        for name, d in (("in", s.dev.w_in), ("rec", s.dev.w_rec)):
+            h = d.host()
+            rl = st[name][0]
+            np.testing.assert_array_equal(h["row_len"], rl)
+            mask = np.arange(d.C)[None] < rl[:, None]
+            np.testing.assert_array_equal(h["ind"][mask], st[name][1][mask])
+            np.testing.assert_allclose(h["w"][mask], st[name][2][mask], rtol=1e-9, atol=1e-12)
+            np.testing.assert_array_equal(h["conn_bits"], conn[name])
+        np.testing.assert_allclose(s.dev.W_out.cpu().numpy(), W, rtol=1e-9, atol=1e-12)
+    else:
+        agree = np.mean([np.mean(gr == r) for gr, r in zip(g_rasters, rasters)])
+        assert agree >= 0.999
+    assert abs(np.mean(np.array(g_preds) == np.array([tb.labels[0] for tb in batches]))
+               - np.mean(np.array(preds) == np.array([tb.labels[0] for tb in batches]))) <= 0.005 + 1e-12

@@ -1,0 +1,121 @@
+"""GPU parity of DEEP R rewiring: bit-exact connectivity, moved state and counts."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import deepr as od
+from tests._setups import as_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2510_19764_gb300 import abi, build
+    build.build()
+    abi.load()
+
+
+def _stats():
+    return torch.zeros(4, dtype=torch.int64, device="cuda")
+
+
+def _compare(d, out, stats):
+    from paper_2510_19764_gb300 import abi
+    h = d.host()
+    np.testing.assert_array_equal(h["row_len"], out["row_len"])
+    mask = np.arange(d.C)[None] < out["row_len"][:, None]
+    np.testing.assert_array_equal(h["ind"][mask], out["ind"][mask])
+    for k in ("w", "m", "v"):
+        np.testing.assert_array_equal(h[k][mask], out[k][mask])
+    np.testing.assert_array_equal(h["conn_bits"], out["conn"])
+    st = stats.cpu().numpy()
+    assert st[0] == out["removed"] and st[1] == out["formed"] and st[2] == out["overflow"]
+    assert d.status() == (abi.SNN_OK if out["overflow"] == 0 else abi.SNN_ECAPACITY)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("P,Q,p,no_aut", [(5, 4, 0.5, False), (64, 64, 0.2, True), (700, 1024, 0.1, False),
+                                          (1024, 1024, 0.1, True), (33, 1000, 0.05, False)])
+def test_rewire_bit_exact(dtype, P, Q, p, no_aut):
+    from paper_2510_19764_gb300 import abi, net
+    rag = synth.random_ragged(11, P, Q, p, no_autapse=no_aut)
+    rag.w = as_dtype(rag.w, dtype)
+    rng = np.random.default_rng(5)
+    m0 = as_dtype(rng.normal(size=rag.w.shape), dtype)
+    v0 = as_dtype(rng.random(rag.w.shape), dtype)
+    d = net.DeviceRagged(rag.row_len, rag.ind, rag.w, Q, dtype=dtype, no_autapse=no_aut, adam=True, deepr=True,
+                         seed=99, m=m0, v=v0)
+    sign = net.u32_to_numpy(d.sign_bits).copy()
+    conn = net.u32_to_numpy(d.conn_bits).copy()
+    state = (rag.row_len.copy(), rag.ind.copy(), rag.w.copy(), m0.copy(), v0.copy())
+    for ridx in range(3):
+        # drift weights so that a fraction of them flips sign (some land exactly on 0)
+        rl, ind, w, m, v = state
+        mask = np.arange(rag.C)[None] < rl[:, None]
+        w = as_dtype(np.where(mask, w + rng.normal(0, 0.15, w.shape), w), dtype)
+        w[mask & (rng.random(w.shape) < 0.02)] = 0.0
+        d.w.copy_(torch.as_tensor(w))
+        stats = _stats()
+        abi.snn_rewire_deepr(d.handle, ridx, stats)
+        torch.cuda.synchronize()
+        out = od.rewire(rl, ind, w, m, v, sign, conn, rag.C, Q, no_aut, 99, ridx)
+        assert out["removed"] > 0
+        _compare(d, out, stats)
+        state = (out["row_len"], out["ind"], out["w"], out["m"], out["v"])
+        conn = out["conn"]
+
+
+def test_fig2_shaped_scripted_example():
+    """5 pre x 4 post, out-degree 3 with scripted sign bits (Fig. 2 shape)."""
+    from paper_2510_19764_gb300 import abi, net
+    P, Q, C = 5, 4, 3
+    row_len = np.array([2, 3, 1, 0, 2], np.int32)
+    ind = np.array([[1, 3, -1], [0, 2, 3], [2, -1, -1], [-1, -1, -1], [0, 1, -1]], np.int32)
+    w = np.array([[0.5, -0.2, 0], [-0.1, 0.3, 0.0], [-0.4, 0, 0], [0, 0, 0], [0.2, 0.7, 0]])
+    sign = np.zeros((P, 1), np.uint32)
+    for i, j in {(0, 1), (0, 3), (1, 2), (1, 3), (2, 2), (4, 0)}:
+        sign[i, 0] |= np.uint32(1 << j)
+    d = net.DeviceRagged(row_len, ind, w, Q, dtype=1, adam=True, deepr=True, seed=1, sign_bits=sign)
+    stats = _stats()
+    abi.snn_rewire_deepr(d.handle, 0, stats)
+    torch.cuda.synchronize()
+    conn = np.zeros((P, 1), np.uint32)
+    for i in range(P):
+        for s in range(row_len[i]):
+            conn[i, 0] |= np.uint32(1 << int(ind[i, s]))
+    out = od.rewire(row_len, ind, w, np.zeros_like(w), np.zeros_like(w), sign, conn, C, Q, False, 1, 0)
+    assert out["removed"] == 3
+    _compare(d, out, stats)
+
+
+def test_capacity_overflow_reported():
+    """1000 full rows (every target taken) and one dormant synapse: its activation has
+    to land on the one row with room, which 64 uniform rounds usually miss.  The kernel
+    must agree with the oracle on where (if anywhere) it lands, count the leftover in
+    the stats and report SNN_ECAPACITY in the status word (no device trap)."""
+    from paper_2510_19764_gb300 import abi, net
+    P, Q, C = 1000, 4, 4
+    row_len = np.full(P, 4, np.int32)
+    ind = np.tile(np.arange(4, dtype=np.int32), (P, 1))
+    w = np.ones((P, C))
+    d = net.DeviceRagged(row_len, ind, w, Q, dtype=1, adam=True, deepr=True, seed=3)
+    sign = net.u32_to_numpy(d.sign_bits).copy()
+    conn = net.u32_to_numpy(d.conn_bits).copy()
+    w2 = w.copy()
+    w2[7, 0] = -1.0
+    d.w.copy_(torch.as_tensor(w2))
+    overflowed = 0
+    for ridx in range(4):
+        stats = _stats()
+        d.row_len.copy_(torch.as_tensor(row_len))
+        d.ind.copy_(torch.as_tensor(ind))
+        d.w.copy_(torch.as_tensor(w2))
+        d.conn_bits.copy_(torch.as_tensor(conn.view(np.int32)))
+        abi.snn_rewire_deepr(d.handle, ridx, stats)
+        torch.cuda.synchronize()
+        out = od.rewire(row_len, ind, w2, np.zeros_like(w), np.zeros_like(w), sign, conn, C, Q, False, 3, ridx)
+        _compare(d, out, stats)
+        overflowed += out["overflow"]
+    assert overflowed > 0

@@ -1,0 +1,174 @@
+"""GPU parity of the topographic map: rewiring bit-exact, and each simulation step
+(input, conductance LIF, propagation, STDP) against the oracle from the same state."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import philox as oph
+from oracle import topo as ot
+from tests._setups import as_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2510_19764_gb300 import abi, build
+    build.build()
+    abi.load()
+
+
+def _rewire_args(p, L, name):
+    pf, sg = (p.p_form_ff, p.sigma_ff) if name == "ff" else (p.p_form_lat, p.sigma_lat)
+    return pf, sg
+
+
+@pytest.mark.parametrize("L,C,n_att,name", [(16, 16, 60, "ff"), (16, 16, 60, "lat"), (32, 64, 40, "ff"),
+                                            (32, 64, 40, "lat"), (8, 6, 500, "ff"), (16, 8, 3000, "lat")])
+def test_rewire_bit_exact(L, C, n_att, name):
+    from paper_2510_19764_gb300 import abi, net
+    p = ot.TopoParams(L=L, n_att=n_att)
+    pf, sg = _rewire_args(p, L, name)
+    rag = synth.topo_initial(4, L, pf, sg, C, p.g_max)
+    rng = np.random.default_rng(1)
+    g = as_dtype(np.where(rag.ind >= 0, rng.uniform(0, p.g_max, rag.w.shape), 0.0), 0)
+    d = net.DeviceRagged(rag.row_len, rag.ind, g, L * L, dtype=0, seed=2024)
+    rw = net.topo_rewire(L, pf, sg, n_att, g_max=p.g_max)
+    state = (rag.row_len.copy(), rag.ind.copy(), g.copy())
+    changes = 0
+    for ridx in range(10):
+        stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+        abi.snn_rewire_topo(d.handle, rw, ridx, stats)
+        torch.cuda.synchronize()
+        out = ot.rewire(*state, C, L * L, L, 2024, ridx, n_att, oph.threshold(p.p_elim_dep),
+                        oph.threshold(p.p_elim_pot), float(np.float32(p.g_theta)),
+                        ot.form_thresholds(pf, sg, L), float(np.float32(p.g_max)))
+        h = d.host()
+        np.testing.assert_array_equal(h["row_len"], out["row_len"])
+        mask = np.arange(C)[None] < out["row_len"][:, None]
+        np.testing.assert_array_equal(h["ind"][mask], out["ind"][mask])
+        np.testing.assert_array_equal(h["w"][mask], out["g"][mask])
+        st = stats.cpu().numpy()
+        assert (st[0], st[1], st[2], st[3]) == (out["removed"], out["formed"], out["overflow"],
+                                                int(out["attempts"].sum()))
+        changes += out["removed"] + out["formed"]
+        state = (out["row_len"], out["ind"], out["g"])
+        assert d.status() == abi.SNN_OK
+    assert changes > 0
+
+
+def test_steps_match_oracle_from_same_state():
+    from paper_2510_19764_gb300 import abi, net
+    L, C, T = 16, 32, 60
+    N = L * L
+    p = ot.TopoParams(L=L, n_att=10, f_base=40.0, f_in=200.0)
+    ff = synth.topo_initial(1, L, p.p_form_ff, p.sigma_ff, C, p.g_max)
+    lat = synth.topo_initial(2, L, p.p_form_lat, p.sigma_lat, C, p.g_max)
+    for r in (ff, lat):
+        r.w = as_dtype(r.w, 0)
+    dff = net.DeviceRagged(ff.row_len, ff.ind, ff.w, N, dtype=0, seed=11)
+    dlat = net.DeviceRagged(lat.row_len, lat.ind, lat.w, N, dtype=0, seed=12)
+    tp = net.topo_params(L=L, f_base=40.0, f_in=200.0)
+    rw_ff = net.topo_rewire(L, p.p_form_ff, p.sigma_ff, p.n_att)
+    rw_lat = net.topo_rewire(L, p.p_form_lat, p.sigma_lat, p.n_att)
+    st = net.DeviceTopoState(N, p.V_rest)
+    Nw = net.words(N)
+    seed_in = 5
+    thr_dep, thr_pot = oph.threshold(p.p_elim_dep), oph.threshold(p.p_elim_pot)
+    spikes = 0
+    flips = 0
+    for t in range(T):
+        cur, prv = t & 1, (t & 1) ^ 1
+        # oracle input from the GPU state of step t-1
+        o = {k: getattr(st, k).double().cpu().numpy() for k in ("V", "gs", "x_src", "x_tgt", "y")}
+        o["ref"] = st.ref.cpu().numpy().astype(np.int64)
+        s_prev = net.spikes_from_bits(net.u32_to_numpy(st.src_bits[prv]), N).astype(bool)
+        z_prev = net.spikes_from_bits(net.u32_to_numpy(st.tgt_bits[prv]), N).astype(bool)
+        hff, hlat = dff.host(), dlat.host()
+        # GPU step t without rewiring
+        abi.snn_topo_input(tp, st.desc, seed_in, t)
+        abi.snn_propagate(dff.handle, st.src_bits[prv], 1, st.acc)
+        abi.snn_propagate(dlat.handle, st.tgt_bits[prv], 1, st.acc)
+        abi.snn_topo_neurons(tp, st.desc, t)
+        abi.snn_stdp_update(dff.handle, tp, st.src_bits[cur], st.tgt_bits[cur], st.x_src, st.ydec)
+        abi.snn_stdp_update(dlat.handle, tp, st.tgt_bits[cur], st.tgt_bits[cur], st.x_tgt, st.ydec)
+        torch.cuda.synchronize()
+        # oracle step t
+        s = ot.input_spikes(seed_in, t, p)
+        np.testing.assert_array_equal(net.spikes_from_bits(net.u32_to_numpy(st.src_bits[cur]), N).astype(bool), s)
+        I = ot.propagate_rows((hff["row_len"], hff["ind"], hff["w"]), s_prev, N)
+        I += ot.propagate_rows((hlat["row_len"], hlat["ind"], hlat["w"]), z_prev, N)
+        V, gs, ref, z = ot.neuron_step(o["V"], o["gs"], o["ref"], I, p)
+        zg = net.spikes_from_bits(net.u32_to_numpy(st.tgt_bits[cur]), N).astype(bool)
+        differ = zg != z
+        flips += differ.sum()
+        spikes += z.sum()
+        np.testing.assert_allclose(st.gs.double().cpu().numpy(), gs, rtol=1e-5, atol=1e-6)
+        ok = ~differ
+        np.testing.assert_allclose(st.V.double().cpu().numpy()[ok], V[ok], rtol=1e-5, atol=1e-4)
+        # STDP from the GPU's pre-step weights with the GPU's spikes (decisions fixed)
+        pff = [hff["row_len"], hff["ind"], hff["w"].copy()]
+        plat = [hlat["row_len"], hlat["ind"], hlat["w"].copy()]
+        xs, y = ot.stdp_step([tuple(pff), tuple(plat)], [o["x_src"], o["x_tgt"]], o["y"], [s, zg], zg, p)
+        np.testing.assert_allclose(st.x_src.double().cpu().numpy(), xs[0], rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(st.x_tgt.double().cpu().numpy(), xs[1], rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(st.y.double().cpu().numpy(), y, rtol=1e-6, atol=1e-6)
+        for dev, ref_p in ((dff, pff), (dlat, plat)):
+            mask = np.arange(C)[None] < ref_p[0][:, None]
+            np.testing.assert_allclose(dev.w.double().cpu().numpy()[mask], ref_p[2][mask], rtol=0, atol=2e-7)
+        if (t + 1) % p.rewire_every == 0:
+            ridx = (t + 1) // p.rewire_every - 1
+            for dev, rw, pf, sg, seed in ((dff, rw_ff, p.p_form_ff, p.sigma_ff, 11),
+                                          (dlat, rw_lat, p.p_form_lat, p.sigma_lat, 12)):
+                h = dev.host()
+                abi.snn_rewire_topo(dev.handle, rw, ridx)
+                torch.cuda.synchronize()
+                out = ot.rewire(h["row_len"], h["ind"], h["w"], C, N, L, seed, ridx, p.n_att, thr_dep, thr_pot,
+                                float(np.float32(p.g_theta)), ot.form_thresholds(pf, sg, L),
+                                float(np.float32(p.g_max)))
+                h2 = dev.host()
+                np.testing.assert_array_equal(h2["row_len"], out["row_len"])
+                mask = np.arange(C)[None] < out["row_len"][:, None]
+                np.testing.assert_array_equal(h2["ind"][mask], out["ind"][mask])
+                np.testing.assert_array_equal(h2["w"][mask], out["g"][mask])
+    assert spikes > 20
+    assert flips <= 2
+
+
+def test_topo_run_matches_granular_calls():
+    """snn_topo_run over 40 steps equals the same sequence of granular calls."""
+    from paper_2510_19764_gb300 import abi, net
+    L, C, T = 16, 32, 40
+    N = L * L
+    p = ot.TopoParams(L=L, n_att=10)
+    res = []
+    for mode in ("run", "granular"):
+        ff = synth.topo_initial(1, L, p.p_form_ff, p.sigma_ff, C, p.g_max)
+        lat = synth.topo_initial(2, L, p.p_form_lat, p.sigma_lat, C, p.g_max)
+        dff = net.DeviceRagged(ff.row_len, ff.ind, ff.w, N, dtype=0, seed=11)
+        dlat = net.DeviceRagged(lat.row_len, lat.ind, lat.w, N, dtype=0, seed=12)
+        tp = net.topo_params(L=L)
+        rw_ff = net.topo_rewire(L, p.p_form_ff, p.sigma_ff, p.n_att)
+        rw_lat = net.topo_rewire(L, p.p_form_lat, p.sigma_lat, p.n_att)
+        st = net.DeviceTopoState(N, p.V_rest)
+        if mode == "run":
+            abi.snn_topo_run(tp, st.desc, dff.handle, dlat.handle, rw_ff, rw_lat, 5, 10, 0, T)
+        else:
+            for t in range(T):
+                cur, prv = t & 1, (t & 1) ^ 1
+                abi.snn_topo_input(tp, st.desc, 5, t)
+                abi.snn_propagate(dff.handle, st.src_bits[prv], 1, st.acc)
+                abi.snn_propagate(dlat.handle, st.tgt_bits[prv], 1, st.acc)
+                abi.snn_topo_neurons(tp, st.desc, t)
+                abi.snn_stdp_update(dff.handle, tp, st.src_bits[cur], st.tgt_bits[cur], st.x_src, st.ydec)
+                abi.snn_stdp_update(dlat.handle, tp, st.tgt_bits[cur], st.tgt_bits[cur], st.x_tgt, st.ydec)
+                if (t + 1) % 10 == 0:
+                    abi.snn_rewire_topo(dff.handle, rw_ff, (t + 1) // 10 - 1)
+                    abi.snn_rewire_topo(dlat.handle, rw_lat, (t + 1) // 10 - 1)
+        torch.cuda.synchronize()
+        res.append((dff.host(), dlat.host(), st.V.cpu().numpy().copy()))
+    for a, b in zip(res[0][:2], res[1][:2]):
+        for k in ("row_len", "ind", "w"):
+            np.testing.assert_array_equal(a[k], b[k])
+    np.testing.assert_array_equal(res[0][2], res[1][2])
