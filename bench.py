@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--sample-steps", type=int, default=600, help="oracle sample: steps of one trial")
+    ap.add_argument("--batch", type=int, default=512, help="trials per batch (512 = the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     return ap.parse_args()
 
 
@@ -338,6 +340,7 @@ def run_reference(args, sample_steps: int, world: int, rank: int):
 
 def main():
     args = parse()
+    WORKLOAD["B"] = args.batch
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         if rank != 0:
@@ -356,7 +359,9 @@ def main():
         print(json.dumps(line), flush=True)
         return 0
     line = run_ours(args, world, rank, local)
-    if rank == 0:
+    if rank == 0 and args.no_cpu_baseline:
+        print(json.dumps(line), flush=True)
+    elif rank == 0:
         cv, per_trial, dt = run_reference(args, args.sample_steps, world, rank)
         line["cpu_baseline"] = {"value": round(cv, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"1 trial x {args.sample_steps} of 1000 steps (forward + e-prop traces), "
