@@ -132,6 +132,30 @@ snn_status snn_propagate(const snn_ragged* r, const uint32_t* pre_bits, int32_t 
 snn_status snn_rewire_deepr(snn_ragged* r, int64_t rewire_idx, snn_rewire_stats* stats,
                             snn_stream stream);
 
+/* DEEP R rewiring that allocates nothing (the paper has no counterpart; this entry
+ * exists for callers that cannot allocate device memory).  Some callers cannot call
+ * cudaMalloc: a serving process that reserved its whole device-memory budget at start-up
+ * and must not grow it, a host framework whose own allocator owns every device buffer,
+ * or a latency-critical loop where an allocation could synchronise the device.  They
+ * cannot create an snn_ragged handle either, because that allocates its scratch.
+ *
+ * Same computation, inputs and outputs as snn_rewire_deepr, but on a plain descriptor
+ * (the caller's device arrays; no handle) and with its scratch taken from a fixed array
+ * of 16384 rows inside the library (static device memory that every GPU which loads the
+ * library holds until the process exits).
+ *  - desc->P must be <= 16384; larger matrices get SNN_EINVAL (use the handle API).
+ *  - status: optional device int32 that receives the OR of the error flags
+ *    (1 = leftover activations, 2 = invalid state); NULL discards them.
+ *  - The first call on a device looks up the scratch's device address (once per
+ *    device, with that device current); make that first call before any stream capture.
+ *  - Every call shares the one scratch array and leaves its contents behind; the
+ *    kernels re-initialise what they read.  Calls that overlap on the GPU (different
+ *    streams, or different host threads, without ordering between them) race on it and
+ *    give wrong results: serialise them.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine. */
+snn_status snn_rewire_deepr_noalloc(const snn_ragged_desc* desc, int64_t rewire_idx,
+                                    snn_rewire_stats* stats, int32_t* status, snn_stream stream);
+
 /* ==================================================================================
  * Recurrent LIF/ALIF classifier with e-prop (Sec. 2.2.1)
  * ================================================================================== */

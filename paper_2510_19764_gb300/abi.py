@@ -23,7 +23,7 @@ EXPORTED = [
     "snn_last_error", "snn_abi_version", "snn_create_ragged", "snn_destroy_ragged", "snn_ragged_status",
     "snn_propagate", "snn_rewire_deepr", "snn_create_classifier", "snn_destroy_classifier", "snn_step_neurons",
     "snn_eprop_update", "snn_topo_input", "snn_topo_neurons", "snn_stdp_update", "snn_rewire_topo", "snn_topo_run",
-    "snn_philox",
+    "snn_philox", "snn_rewire_deepr_noalloc",
 ]
 
 
@@ -118,6 +118,7 @@ def load() -> C.CDLL:
         "snn_topo_run": (i32, [P(TopoParams), P(TopoState), vp, vp, P(TopoRewire), P(TopoRewire), u64, i32, i64,
                                i32, vp, vp, vp]),
         "snn_philox": (i32, [u64, u64, vp, i64, vp, vp]),
+        "snn_rewire_deepr_noalloc": (i32, [P(RaggedDesc), i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +176,10 @@ def snn_propagate(h: int, pre_bits, B: int, post_acc, stream=None) -> None:
 
 def snn_rewire_deepr(h: int, rewire_idx: int, stats=None, stream=None) -> None:
     check(load().snn_rewire_deepr(h, rewire_idx, ptr(stats), stream_ptr(stream)))
+
+
+def snn_rewire_deepr_noalloc(desc: RaggedDesc, rewire_idx: int, stats=None, status=None, stream=None) -> None:
+    check(load().snn_rewire_deepr_noalloc(C.byref(desc), rewire_idx, ptr(stats), ptr(status), stream_ptr(stream)))
 
 
 def snn_create_classifier(desc: ClassifierDesc) -> int:

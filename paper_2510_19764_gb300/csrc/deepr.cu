@@ -13,6 +13,8 @@
 //                       connectivity bitfield.
 #include "common.cuh"
 
+#include <mutex>
+
 namespace snn {
 
 template <typename real>
@@ -203,9 +205,84 @@ static snn_status rewire_impl(snn_ragged* r, uint64_t rewire, snn_rewire_stats* 
     return SNN_OK;
 }
 
+// ------------------------------------------------------------------ no-allocation variant
+// Fixed scratch for snn_rewire_deepr_noalloc: four int32 arrays of NOALLOC_MAX_ROWS rows
+// (dormant counts, taken, room, per-round histogram) and one status word.  It lives in
+// every device that loads the library until the process exits.
+constexpr int NOALLOC_MAX_ROWS = 16384;
+static __device__ __align__(256) int32_t g_noalloc_scratch[4 * NOALLOC_MAX_ROWS + 32];
+
+static int32_t* g_noalloc_ptr[256];
+static std::mutex g_noalloc_mu;
+
+// Device address of the static scratch for the current device.  The first call on a
+// device looks it up with cudaGetSymbolAddress (the host-side symbol is only a stand-in
+// for it) and caches it.
+static snn_status noalloc_scratch(int32_t** out) {
+    int dev = -1;
+    SNN_CUDA(cudaGetDevice(&dev));
+    SNN_REQUIRE(dev >= 0 && dev < 256, "snn_rewire_deepr_noalloc: device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("snn_rewire_deepr_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return SNN_ECUDA;
+        }
+        g_noalloc_ptr[dev] = (int32_t*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SNN_OK;
+}
+
+template <typename real>
+static snn_status rewire_noalloc_impl(const snn_ragged_desc& d, int32_t* scratch, int32_t* status, uint64_t rewire,
+                                      snn_rewire_stats* stats, cudaStream_t s) {
+    const int Qw = (d.Q + 31) / 32;
+    int32_t* dormant = scratch;
+    int32_t* taken = scratch + NOALLOC_MAX_ROWS;
+    int32_t* room = scratch + 2 * NOALLOC_MAX_ROWS;
+    int32_t* cnt = scratch + 3 * NOALLOC_MAX_ROWS;
+    if (!status) status = scratch + 4 * NOALLOC_MAX_ROWS;
+    const int blocks = ceil_div((long long)d.P * 32, 256);
+    k_deepr_eliminate<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
+                                                    d.sign_bits, d.conn_bits, dormant, d.P, d.C, Qw);
+    SNN_LAUNCH_CHECK();
+    k_deepr_distribute<<<1, 1024, 0, s>>>(d.row_len, dormant, room, taken, cnt, d.P, d.C, d.Q, d.no_autapse, d.seed,
+                                          rewire, status, stats);
+    SNN_LAUNCH_CHECK();
+    k_deepr_form<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v, d.conn_bits,
+                                               taken, d.P, d.C, d.Q, Qw, d.no_autapse, d.seed, rewire, status, stats);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
 }  // namespace snn
 
 using namespace snn;
+
+extern "C" snn_status snn_rewire_deepr_noalloc(const snn_ragged_desc* d, int64_t rewire_idx, snn_rewire_stats* stats,
+                                               int32_t* status, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(d, "snn_rewire_deepr_noalloc: NULL descriptor");
+    SNN_REQUIRE(rewire_idx >= 0, "snn_rewire_deepr_noalloc: rewire_idx must be >= 0");
+    SNN_REQUIRE(d->P > 0 && d->Q > 0 && d->C > 0, "snn_rewire_deepr_noalloc: P, Q, C must be > 0");
+    SNN_REQUIRE(d->P <= NOALLOC_MAX_ROWS,
+                "snn_rewire_deepr_noalloc: P = %d rows exceeds the fixed scratch of %d rows "
+                "(use snn_create_ragged + snn_rewire_deepr for larger matrices)",
+                d->P, NOALLOC_MAX_ROWS);
+    SNN_REQUIRE((long long)d->P * d->C < (1ll << 31), "snn_rewire_deepr_noalloc: P*C must be < 2^31");
+    SNN_REQUIRE(d->dtype == SNN_F32 || d->dtype == SNN_F64, "snn_rewire_deepr_noalloc: bad dtype");
+    SNN_REQUIRE(d->row_len && d->ind && d->w && d->m && d->v && d->sign_bits && d->conn_bits,
+                "snn_rewire_deepr_noalloc: needs row_len, ind, w, m, v, sign_bits and conn_bits");
+    int32_t* scratch = nullptr;
+    snn_status st = noalloc_scratch(&scratch);
+    if (st != SNN_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return d->dtype == SNN_F32 ? rewire_noalloc_impl<float>(*d, scratch, status, (uint64_t)rewire_idx, stats, s)
+                               : rewire_noalloc_impl<double>(*d, scratch, status, (uint64_t)rewire_idx, stats, s);
+}
 
 extern "C" snn_status snn_rewire_deepr(snn_ragged* r, int64_t rewire_idx, snn_rewire_stats* stats, snn_stream stream) {
     clear_error();
