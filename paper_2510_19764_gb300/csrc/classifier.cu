@@ -26,28 +26,22 @@
 namespace snn {
 
 constexpr int FWD_THREADS = 256;
-constexpr int GATHER_WARPS = 8;
 
 template <typename real>
 struct FwdParams {
-    int n_in, N, K, Win, Wh, T, t0, n_steps;
+    int n_in, N, K, Win, Wh, T, t0, n_steps, n_classes;
     real alpha, rho, beta, v_thr, psi_scale, inv_vthr;
-    const uint64_t* in_thr;
-    int n_bins, n_classes;
-    uint64_t in_seed;
     int32_t* status;
     const int32_t* labels;
-    const int32_t* bin_len;
-    const int64_t* trial_ids;
     const int32_t* in_len;
     const int32_t* in_ind;
-    const real* in_w;
+    const long long* in_pk;    // packed (index | fixed-point weight) shadows of the ragged rows
     int in_C;
     const int32_t* rec_len;
     const int32_t* rec_ind;
-    const real* rec_w;
+    const long long* rec_pk;
     int rec_C;
-    const real* W_out;
+    const long long* out_wf;   // [K][N]
     const real* b_out;
     real* v;
     real* a;
@@ -55,216 +49,297 @@ struct FwdParams {
     real* ysum;
     uint32_t* x_bits;
     uint32_t* z_bits;
-    uint32_t* x_rec;
+    const uint32_t* x_rec;
     uint32_t* z_rec;
     real* psi_rec;
     real* d_rec;
     real* v_rec;
     real* a_rec;
     real* y_rec;
+    int record_state;
+};
+
+struct InputParams {
+    int n_in, Win, T, t0, n_steps, n_bins, n_classes, B;
+    const uint64_t* in_thr;
+    uint64_t seed;
+    const int32_t* labels;
+    const int32_t* bin_len;
+    const int64_t* trial_ids;
+    uint32_t* x_rec;
+    int32_t* status;
 };
 
 __device__ __forceinline__ float exp_real(float x) { return expf(x); }
 __device__ __forceinline__ double exp_real(double x) { return exp(x); }
 
-template <typename real>
-__device__ __forceinline__ void propagate_word(uint32_t word, int row0, const int32_t* __restrict__ len,
-                                               const int32_t* __restrict__ ind, const real* __restrict__ w, int C,
-                                               unsigned long long* acc) {
-    while (word) {
-        int i = row0 + __ffs(word) - 1;
-        word &= word - 1u;
-        int n = len[i];
-        const int32_t* ri = ind + (size_t)i * C;
-        const real* rw = w + (size_t)i * C;
-        int s = lane_id();
-        // four independent loads in flight per lane before the atomics
-        for (; s + 96 < n; s += 128) {
-            int j0 = ri[s], j1 = ri[s + 32], j2 = ri[s + 64], j3 = ri[s + 96];
-            real w0 = rw[s], w1 = rw[s + 32], w2 = rw[s + 64], w3 = rw[s + 96];
-            atomicAdd(acc + j0, (unsigned long long)to_fixed(w0));
-            atomicAdd(acc + j1, (unsigned long long)to_fixed(w1));
-            atomicAdd(acc + j2, (unsigned long long)to_fixed(w2));
-            atomicAdd(acc + j3, (unsigned long long)to_fixed(w3));
+// Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
+// only, so they are drawn ahead of the sequential simulation.  Thread = 4 channels (one
+// Philox block); the nibbles of 8 consecutive threads form one 32-channel word.
+__global__ void k_input(InputParams p) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int G = p.Win * 8;
+    const long long total = (long long)p.B * p.n_steps * G;
+    uint32_t nib = 0;
+    int gi = (int)(g % G);
+    long long bt = g / G;
+    if (g < total) {
+        const int b = (int)(bt / p.n_steps);
+        const int t = p.t0 + (int)(bt % p.n_steps);
+        int label = p.labels[b], bin_len = p.bin_len[b];
+        if (label < 0 || label >= p.n_classes || bin_len < 1) {
+            if (gi == 0) atomicOr(p.status, ST_STATE);
+            label = min(max(label, 0), p.n_classes - 1);
+            bin_len = max(bin_len, 1);
         }
-        for (; s < n; s += 32) atomicAdd(acc + ri[s], (unsigned long long)to_fixed(rw[s]));
+        if (4 * gi < p.n_in) {
+            const int bin = min(p.n_bins - 1, t / bin_len);
+            const uint64_t* thr = p.in_thr + ((size_t)label * p.n_bins + bin) * p.n_in;
+            const u64x4 r = philox(p.seed, PH_INPUT, (uint64_t)p.trial_ids[b], (uint64_t)t, (uint64_t)gi, 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 4 * gi + q;
+                if (c < p.n_in && r[q] < thr[c]) nib |= 1u << q;
+            }
+        }
+    }
+    uint32_t word = nib << (4 * (gi & 7));
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+    if (g < total && (gi & 7) == 0) {
+        const int b = (int)(bt / p.n_steps);
+        const int t = p.t0 + (int)(bt % p.n_steps);
+        p.x_rec[((size_t)b * p.T + t) * p.Win + (gi >> 3)] = word;
     }
 }
 
-template <typename real>
-__global__ void __launch_bounds__(FWD_THREADS) k_forward(FwdParams<real> p) {
+// One CTA = one trial, all requested steps.  Spiking rows are kept as explicit lists
+// (global row ids: input rows 0..n_in-1, hidden rows n_in + j), double-buffered by step
+// parity and built where the spikes appear: hidden spikes are appended with one
+// warp-aggregated shared-memory atomic per warp during the neuron update, the input
+// spikes of step t (drawn ahead of time by k_input) are listed by warp 0.  Per step t:
+//  (A) warps take every nwarps-th row of the lists of step t-1, two rows at a time; each
+//      slot is one packed 64-bit load (target index | fixed-point weight) and one
+//      branch-free shared-memory atomic (invalid lanes add 0 to their own spare
+//      accumulator); hidden rows also add their readout column.  The last warp
+//      meanwhile finishes the readout of step t-1 (leak, softmax, d record).
+//  (B) each thread updates its NPT neurons (state in registers) and writes psi.
+template <typename real, int NPT>
+__global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh;
-    long long* Iacc = (long long*)smem;
-    real* vs = (real*)(Iacc + N);
-    real* as = vs + N;
-    real* yacc = as + N;                        // [32]
-    uint32_t* xb = (uint32_t*)(yacc + 32);      // [2][Win]
-    uint32_t* zb = xb + 2 * Win;                // [2][Wh]
+    const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh, n_in = p.n_in;
+    const int R = n_in + N;
+    long long* Iacc = (long long*)smem;           // [N + 32] (slots N.. are per-lane spares)
+    long long* yfix = Iacc + N + 32;              // [2][32] readout accumulators
+    int* lens = (int*)(yfix + 64);                // [R]
+    int* list = lens + R;                         // [2][R] spiking rows by step parity
+    int* lcnt = list + 2 * R;                     // [2]
+    uint32_t* xw = (uint32_t*)(lcnt + 2);         // [Win] input spike words of the current step
+    uint32_t* zb = xw + Win;                      // [2][Wh]
 
     const int b = blockIdx.x;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int warp = tid >> 5, nwarps = nthr >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int nwarps = FWD_THREADS / 32;
+    constexpr int RO_WARP = nwarps - 1;
     int label = p.labels[b];
-    int bin_len = p.bin_len[b];
-    if (label < 0 || label >= p.n_classes || bin_len < 1) {
-        // invalid per-trial input: report it and simulate a valid stand-in instead of
-        // reading outside the threshold table
-        if (tid == 0) atomicOr(p.status, ST_STATE);
-        label = min(max(label, 0), p.n_classes - 1);
-        bin_len = max(bin_len, 1);
-    }
-    const uint64_t trial = (uint64_t)p.trial_ids[b];
-    const int t0 = p.t0;
+    label = min(max(label, 0), p.n_classes - 1);  // validity is reported by k_input
+    const int t0 = p.t0, t_end = p.t0 + p.n_steps;
+    real vr[NPT], ar[NPT];
     {
-        const int prv = (t0 - 1) & 1, cur = t0 & 1;
-        for (int j = tid; j < N; j += nthr) {
-            Iacc[j] = 0;
-            vs[j] = p.v[(size_t)b * N + j];
-            as[j] = p.a[(size_t)b * N + j];
+        const int prv = (t0 - 1) & 1;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            const int j = tid + q * FWD_THREADS;
+            vr[q] = j < N ? p.v[(size_t)b * N + j] : real(0);
+            ar[q] = j < N ? p.a[(size_t)b * N + j] : real(0);
         }
-        for (int w = tid; w < Win; w += nthr) {
-            xb[prv * Win + w] = p.x_bits[(size_t)b * Win + w];
-            xb[cur * Win + w] = 0u;
-        }
-        for (int w = tid; w < Wh; w += nthr) {
-            zb[prv * Wh + w] = p.z_bits[(size_t)b * Wh + w];
-            zb[cur * Wh + w] = 0u;
+        for (int j = tid; j < N + 32; j += FWD_THREADS) Iacc[j] = 0;
+        for (int j = tid; j < N; j += FWD_THREADS) lens[n_in + j] = p.rec_len[j];
+        for (int i = tid; i < n_in; i += FWD_THREADS) lens[i] = p.in_len[i];
+        if (tid < 64) yfix[tid] = 0;
+        for (int w = tid; w < Wh; w += FWD_THREADS) zb[prv * Wh + w] = p.z_bits[(size_t)b * Wh + w];
+        if (warp == 0) {
+            // lists of step t0-1 from the state's spike words
+            if (lane == 0) lcnt[prv] = 0;
+            __syncwarp();
+            for (int w = lane; w < Win + Wh; w += 32) {
+                uint32_t word = w < Win ? p.x_bits[(size_t)b * Win + w] : p.z_bits[(size_t)b * Wh + (w - Win)];
+                const int base = w < Win ? w * 32 : n_in + (w - Win) * 32;
+                const int pos = atomicAdd(&lcnt[prv], __popc(word));
+                for (int k = 0; word; ++k, word &= word - 1u) list[prv * R + pos + k] = base + __ffs(word) - 1;
+            }
         }
     }
     real yk = 0, ysk = 0, bk = 0;
-    if (warp == 0 && lane < K) {
+    if (warp == RO_WARP && lane < K) {
         yk = p.y[(size_t)b * K + lane];
         ysk = p.ysum[(size_t)b * K + lane];
         bk = p.b_out[lane];
     }
+    const uint32_t* xrec_b = p.x_rec + (size_t)b * p.T * Win;
+    uint32_t* zrec_b = p.z_rec + (size_t)b * p.T * Wh;
+    real* psi_b = p.psi_rec + (size_t)b * p.T * N;
+    real* d_b = p.d_rec + (size_t)b * p.T * K;
+    uint32_t xnext = (warp == 0 && lane < Win) ? xrec_b[(size_t)t0 * Win + lane] : 0u;
     __syncthreads();
     unsigned long long* acc = (unsigned long long*)Iacc;
-    const int n_groups = (p.n_in + 3) >> 2;
-    for (int t = t0; t < t0 + p.n_steps; ++t) {
+
+    auto readout = [&](int s) {
+        long long* yb = yfix + 32 * (s & 1);
+        real ynew = 0, ex = 0;
+        if (lane < K) {
+            yk = p.alpha * yk + from_fixed<real>(yb[lane]) + bk;
+            yb[lane] = 0;
+            ynew = yk;
+            ysk += yk;
+        }
+        const real mx = warp_max(lane < K ? ynew : -INFINITY);
+        if (lane < K) ex = exp_real(ynew - mx);
+        const real ssum = warp_sum(ex);
+        if (lane < K) {
+            d_b[(size_t)s * K + lane] = ex / ssum - (lane == label ? real(1) : real(0));
+            if (p.y_rec) p.y_rec[((size_t)b * p.T + s) * K + lane] = ynew;
+        }
+    };
+
+    for (int t = t0; t < t_end; ++t) {
         const int cur = t & 1, prv = cur ^ 1;
-        uint32_t* xprv = xb + prv * Win;
-        uint32_t* xcur = xb + cur * Win;
-        uint32_t* zprv = zb + prv * Wh;
+        const uint32_t* zprv = zb + prv * Wh;
         uint32_t* zcur = zb + cur * Wh;
-        // ---------------- phase A: propagate step t-1, readout sum, input of step t
-        for (int wi = warp; wi < Win + Wh; wi += nwarps) {
-            if (wi < Win)
-                propagate_word<real>(xprv[wi], wi * 32, p.in_len, p.in_ind, p.in_w, p.in_C, acc);
-            else
-                propagate_word<real>(zprv[wi - Win], (wi - Win) * 32, p.rec_len, p.rec_ind, p.rec_w, p.rec_C, acc);
+        unsigned long long* yacc = (unsigned long long*)(yfix + 32 * cur);
+        const int* lprv = list + prv * R;
+        int* lcur = list + cur * R;
+        // ---------------- phase A
+        const int n_rows = lcnt[prv];
+        if (tid >= 64 && tid - 64 < Wh) {
+            const int w = tid - 64;
+            if (t > t0) zrec_b[(size_t)(t - 1) * Wh + w] = zprv[w];
+            zcur[w] = 0u;
         }
-        for (int k = warp; k < K; k += nwarps) {
-            real part = 0;
-            for (int wi = lane; wi < Wh; wi += 32) {
-                uint32_t word = zprv[wi];
-                while (word) {
-                    int j = wi * 32 + __ffs(word) - 1;
-                    word &= word - 1u;
-                    part += p.W_out[(size_t)k * N + j];
-                }
-            }
-            part = warp_sum(part);
-            if (lane == 0) yacc[k] = part;
-        }
-        {
-            const int bin = min(p.n_bins - 1, t / bin_len);
-            const uint64_t* thr = p.in_thr + ((size_t)label * p.n_bins + bin) * p.n_in;
-            for (int g = tid; g < n_groups; g += nthr) {
-                u64x4 r = philox(p.in_seed, PH_INPUT, trial, (uint64_t)t, (uint64_t)g, 0);
-                uint32_t nib = 0;
+        if (tid == 32) lcnt[cur] = 0;
+        if (warp == RO_WARP && t > t0) readout(t - 1);
+        for (int k = warp; k < n_rows; k += 2 * nwarps) {
+            const int rA = lprv[k];
+            const int rB = (k + nwarps < n_rows) ? lprv[k + nwarps] : -1;
+            const bool hA = rA >= n_in, hB = rB >= n_in;
+            const int iA = hA ? rA - n_in : rA, iB = hB ? rB - n_in : (rB < 0 ? 0 : rB);
+            const int nA = lens[rA], nB = rB >= 0 ? lens[rB] : 0;
+            const long long* pkA = hA ? p.rec_pk + (size_t)iA * p.rec_C : p.in_pk + (size_t)iA * p.in_C;
+            const long long* pkB = hB ? p.rec_pk + (size_t)iB * p.rec_C : p.in_pk + (size_t)iB * p.in_C;
+            const bool roA = hA && lane < K, roB = hB && lane < K;
+            const long long oA = roA ? p.out_wf[(size_t)lane * N + iA] : 0ll;
+            const long long oB = roB ? p.out_wf[(size_t)lane * N + iB] : 0ll;
+            const int nmax = nA > nB ? nA : nB;
+            for (int s0 = 0; s0 < nmax; s0 += 128) {
+                long long wA[4], wB[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    int c = 4 * g + q;
-                    if (c < p.n_in && r[q] < thr[c]) nib |= 1u << q;
+                    const int sl = s0 + q * 32 + lane;
+                    wA[q] = pkA[sl < nA ? sl : 0];
+                    wB[q] = pkB[sl < nB ? sl : 0];
                 }
-                if (nib) atomicOr(&xcur[(4 * g) >> 5], nib << ((4 * g) & 31));
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int sl = s0 + q * 32 + lane;
+                    const bool okA = sl < nA, okB = sl < nB;
+                    atomicAdd(acc + (okA ? (int)((unsigned long long)wA[q] >> 52) : N + lane),
+                              okA ? (unsigned long long)((wA[q] << 12) >> 12) : 0ull);
+                    atomicAdd(acc + (okB ? (int)((unsigned long long)wB[q] >> 52) : N + lane),
+                              okB ? (unsigned long long)((wB[q] << 12) >> 12) : 0ull);
+                }
             }
+            if (roA) atomicAdd(yacc + lane, (unsigned long long)oA);
+            if (roB) atomicAdd(yacc + lane, (unsigned long long)oB);
         }
-        for (int w = tid; w < Wh; w += nthr) zcur[w] = 0u;
-        if (t > t0)
-            for (int w = tid; w < Wh; w += nthr) p.z_rec[((size_t)b * p.T + (t - 1)) * Wh + w] = zprv[w];
         __syncthreads();
-        // ---------------- phase B: neurons, readout softmax, records
-        const size_t rec_off = ((size_t)b * p.T + t) * N;
-        for (int j = tid; j < N; j += nthr) {
-            real I = from_fixed<real>(Iacc[j]);
-            Iacc[j] = 0;
-            const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
-            real v = p.alpha * (zp ? vs[j] - p.v_thr : vs[j]) + I;
-            real aa = p.rho * as[j] + (zp ? real(1) : real(0));
-            real A = p.v_thr + p.beta * aa;
-            bool z = v >= A;
-            real u = real(1) - fabs((v - A) * p.inv_vthr);
-            real psi = p.psi_scale * (u > real(0) ? u : real(0));
-            vs[j] = v;
-            as[j] = aa;
-            p.psi_rec[rec_off + j] = psi;
-            if (p.v_rec) p.v_rec[rec_off + j] = v;
-            if (p.a_rec) p.a_rec[rec_off + j] = aa;
-            if (z) atomicOr(&zcur[j >> 5], 1u << (j & 31));
+        // ---------------- phase B: neurons; spike lists of step t
+        if (warp == 0 && lane < Win) {
+            uint32_t word = xnext;                 // x^t
+            if (t + 1 < t_end) xnext = xrec_b[(size_t)(t + 1) * Win + lane];
+            const int pos = atomicAdd(&lcnt[cur], __popc(word));
+            for (int k = 0; word; ++k, word &= word - 1u) lcur[pos + k] = lane * 32 + __ffs(word) - 1;
+            xw[lane] = 0u;
         }
-        if (warp == 0) {
-            real ynew = 0, e = 0;
-            if (lane < K) {
-                yk = p.alpha * yk + yacc[lane] + bk;
-                ynew = yk;
-                ysk += yk;
+        real* psi_t = psi_b + (size_t)t * N;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            const int j = tid + q * FWD_THREADS;
+            if (j < N) {
+                const real I = from_fixed<real>(Iacc[j]);
+                Iacc[j] = 0;
+                const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
+                const real v = p.alpha * (zp ? vr[q] - p.v_thr : vr[q]) + I;
+                const real aa = p.rho * ar[q] + (zp ? real(1) : real(0));
+                const real A = p.v_thr + p.beta * aa;
+                const real u = real(1) - fabs((v - A) * p.inv_vthr);
+                psi_t[j] = p.psi_scale * (u > real(0) ? u : real(0));
+                vr[q] = v;
+                ar[q] = aa;
+                if (p.record_state) {
+                    p.v_rec[(size_t)b * p.T * N + (size_t)t * N + j] = v;
+                    p.a_rec[(size_t)b * p.T * N + (size_t)t * N + j] = aa;
+                }
+                const unsigned am = __activemask();
+                const unsigned zm = __ballot_sync(am, v >= A);
+                if (zm) {
+                    const int leader = __ffs(am) - 1;
+                    int pos = 0;
+                    if (lane == leader) {
+                        zcur[j >> 5] = zm;
+                        pos = atomicAdd(&lcnt[cur], __popc(zm));
+                    }
+                    pos = __shfl_sync(am, pos, leader);
+                    if (v >= A) lcur[pos + __popc(zm & lanemask_lt())] = n_in + j;
+                }
             }
-            real mx = warp_max(lane < K ? ynew : -INFINITY);
-            if (lane < K) e = exp_real(ynew - mx);
-            real ssum = warp_sum(e);
-            if (lane < K) {
-                real pi = e / ssum;
-                p.d_rec[((size_t)b * p.T + t) * K + lane] = pi - (lane == label ? real(1) : real(0));
-                if (p.y_rec) p.y_rec[((size_t)b * p.T + t) * K + lane] = ynew;
-            }
-        }
-        for (int w = tid; w < Win; w += nthr) {
-            p.x_rec[((size_t)b * p.T + t) * Win + w] = xcur[w];
-            xprv[w] = 0u;
         }
         __syncthreads();
     }
-    const int last = t0 + p.n_steps - 1;
+    const int last = t_end - 1;
     const int cl = last & 1;
-    for (int w = tid; w < Wh; w += nthr) {
-        p.z_rec[((size_t)b * p.T + last) * Wh + w] = zb[cl * Wh + w];
+    if (warp == RO_WARP) readout(last);
+    for (int w = tid; w < Wh; w += FWD_THREADS) {
+        zrec_b[(size_t)last * Wh + w] = zb[cl * Wh + w];
         p.z_bits[(size_t)b * Wh + w] = zb[cl * Wh + w];
     }
-    for (int w = tid; w < Win; w += nthr) p.x_bits[(size_t)b * Win + w] = xb[cl * Win + w];
-    for (int j = tid; j < N; j += nthr) {
-        p.v[(size_t)b * N + j] = vs[j];
-        p.a[(size_t)b * N + j] = as[j];
+    for (int w = tid; w < Win; w += FWD_THREADS) p.x_bits[(size_t)b * Win + w] = xrec_b[(size_t)last * Win + w];
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        const int j = tid + q * FWD_THREADS;
+        if (j < N) {
+            p.v[(size_t)b * N + j] = vr[q];
+            p.a[(size_t)b * N + j] = ar[q];
+        }
     }
-    if (warp == 0 && lane < K) {
+    if (warp == RO_WARP && lane < K) {
         p.y[(size_t)b * K + lane] = yk;
         p.ysum[(size_t)b * K + lane] = ysk;
     }
 }
 
-// ------------------------------------------------------------------ backward
-// One thread per (trial, readout): D^{T-1} = 0, D^t = d^{t+1} + alpha D^{t+1};
-// gb_part[b][k] = sum_t d^t.
+// Packed forward shadow of a ragged matrix: bits 63..52 target index, bits 51..0 the
+// weight in fixed point (40 fractional bits, two's complement), one 64-bit load per slot.
 template <typename real>
-__global__ void k_readout_backward(const real* __restrict__ d, real* __restrict__ D, real* __restrict__ gb_part,
-                                   int B, int T, int K, int Kp, real alpha) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= B * Kp) return;
-    int b = idx / Kp, k = idx % Kp;
-    real Dk = 0, gsum = 0;
-    for (int t = T - 1; t >= 0; --t) {
-        real dnext = 0;
-        if (k < K) {
-            if (t + 1 < T) dnext = d[((size_t)b * T + t + 1) * K + k];
-            gsum += d[((size_t)b * T + t) * K + k];
-        }
-        Dk = (t == T - 1) ? real(0) : dnext + alpha * Dk;
-        D[((size_t)b * T + t) * Kp + k] = (k < K) ? Dk : real(0);
-    }
-    if (k < K) gb_part[(size_t)b * K + k] = gsum;
+__global__ void k_pack(const real* __restrict__ w, const int32_t* __restrict__ ind, const int32_t* __restrict__ len,
+                       int C, long long* __restrict__ pk, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int row = (int)(i / C), s = (int)(i % C);
+    if (s >= len[row]) return;
+    const long long f = to_fixed(w[i]) & ((1ll << 52) - 1);
+    pk[i] = (long long)(((unsigned long long)(unsigned)ind[i] << 52) | (unsigned long long)f);
 }
 
+// Fixed-point shadow of a dense weight array (40 fractional bits).
+template <typename real>
+__global__ void k_to_fixed(const real* __restrict__ w, long long* __restrict__ wf, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) wf[i] = to_fixed(w[i]);
+}
+
+// ------------------------------------------------------------------ backward
 template <typename real>
 __global__ void k_reduce_gb(const real* __restrict__ gb_part, real* __restrict__ G_b, int B, int K) {
     int k = threadIdx.x;
@@ -274,96 +349,159 @@ __global__ void k_reduce_gb(const real* __restrict__ gb_part, real* __restrict__
     G_b[k] = s;
 }
 
-// One thread per (trial, hidden neuron): the reverse-time adjoint scan.
-template <typename real>
-__global__ void k_neuron_backward(const real* __restrict__ psi, const real* __restrict__ D,
-                                  const real* __restrict__ W_out, real* __restrict__ delta, int B, int T, int N,
-                                  int K, int Kp, real alpha, real rho, real beta) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int b = blockIdx.y;
-    if (j >= N) return;
-    real wc[32];
+// The reverse-time scans.  CTA = (trial, 128 hidden neurons); steps are walked
+// backwards in chunks of BWD_TCH.  Per chunk the psi tile [BWD_TCH][128] and the
+// readout error d are staged in shared memory; warp 0 extends the filtered readout error
+//   D_k^t = d_k^{t+1} + alpha D_k^{t+1}   (D^{T-1} = 0)
+// through the chunk (the x == 0 CTA of each trial also stores D and sum_t d_k^t for the
+// readout gradients), then every thread runs its neuron's adjoint recurrences
+//   lam = sum_k W_out[k][j] D_k, mu, h, delta   over the chunk from shared memory.
+constexpr int BWD_THREADS = 128;
+constexpr int BWD_TCH = 32;
+
+template <typename real, int KV>
+__global__ void __launch_bounds__(BWD_THREADS)
+    k_backward(const real* __restrict__ psi, const real* __restrict__ d, const real* __restrict__ W_out,
+               real* __restrict__ delta, real* __restrict__ Dout, real* __restrict__ gb_part, int T, int N, int K,
+               real alpha, real rho, real beta) {
+    constexpr int KP = 4 * KV;
+    __shared__ real ps_s[BWD_TCH][BWD_THREADS];
+    __shared__ __align__(16) real D_s[BWD_TCH][KP];
+    __shared__ real d_s[BWD_TCH + 1][KP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j0 = blockIdx.x * BWD_THREADS;
+    const int j = j0 + tid;
+    const int b = blockIdx.y;
+    const bool writer = blockIdx.x == 0;
+    real wc[KP];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) wc[k] = (k < K) ? W_out[(size_t)k * N + j] : real(0);
+    for (int k = 0; k < KP; ++k) wc[k] = (k < K && j < N) ? W_out[(size_t)k * N + j] : real(0);
     real lam_next = 0, psi_next = 0, mu = 0, h_next = 0, dl = 0;
-    for (int t = T - 1; t >= 0; --t) {
-        const size_t o = (size_t)b * T + t;
-        real ps = psi[o * N + j];
-        const real* Dt = D + o * Kp;
-        real lam = 0;
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (k < K) lam += wc[k] * Dt[k];
-        if (t == T - 1) {
-            mu = 0;
-            dl = 0;
-        } else {
-            mu = beta * lam_next * psi_next + (rho - beta * psi_next) * mu;
-            dl = h_next + alpha * dl;
+    real Dk = 0, gsum = 0;
+    const int n_chunks = (T + BWD_TCH - 1) / BWD_TCH;
+    for (int ch = n_chunks - 1; ch >= 0; --ch) {
+        const int tb = ch * BWD_TCH;
+        const int nt = min(BWD_TCH, T - tb);
+        __syncthreads();
+        for (int idx = tid; idx < nt * BWD_THREADS; idx += BWD_THREADS) {
+            const int r = idx / BWD_THREADS, c = idx % BWD_THREADS;
+            ps_s[r][c] = (j0 + c < N) ? psi[((size_t)b * T + tb + r) * N + j0 + c] : real(0);
         }
-        real h = ps * (lam - mu);
-        delta[o * N + j] = dl;
-        h_next = h;
-        lam_next = lam;
-        psi_next = ps;
+        // d rows tb .. tb + nt (one past the chunk, for d^{t+1})
+        for (int idx = tid; idx < (nt + 1) * KP; idx += BWD_THREADS) {
+            const int r = idx / KP, k = idx % KP;
+            const int t = tb + r;
+            d_s[r][k] = (k < K && t < T) ? d[((size_t)b * T + t) * K + k] : real(0);
+        }
+        __syncthreads();
+        if (warp == 0 && lane < KP) {
+            for (int r = nt - 1; r >= 0; --r) {
+                const int t = tb + r;
+                Dk = (t == T - 1 || lane >= K) ? real(0) : d_s[r + 1][lane] + alpha * Dk;
+                D_s[r][lane] = Dk;
+                gsum += d_s[r][lane];
+                if (writer) Dout[((size_t)b * T + t) * KP + lane] = Dk;
+            }
+        }
+        __syncthreads();
+        for (int r = nt - 1; r >= 0; --r) {
+            const int t = tb + r;
+            const real ps = ps_s[r][tid];
+            real lam = 0;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) lam += wc[k] * D_s[r][k];
+            if (t == T - 1) {
+                mu = 0;
+                dl = 0;
+            } else {
+                mu = beta * lam_next * psi_next + (rho - beta * psi_next) * mu;
+                dl = h_next + alpha * dl;
+            }
+            const real h = ps * (lam - mu);
+            if (j < N) delta[((size_t)b * T + t) * N + j] = dl;
+            h_next = h;
+            lam_next = lam;
+            psi_next = ps;
+        }
     }
+    if (writer && warp == 0 && lane < K) gb_part[(size_t)b * K + lane] = gsum;
 }
 
-// Gather: grid (row blocks, KS).  Warp = one presynaptic row (input rows first, then
-// hidden rows); it scans its K-range of (trial, step) for its spike bit, and for every
-// spike sums delta at its targets (and, for hidden rows, D into the readout gradient).
+// Gather: grid (spike-word columns, KS).  CTA = the 32 presynaptic rows of one bit word
+// (input words first, then hidden words), one warp per row.  The CTA stages the words of
+// its whole (trial, step) range in shared memory, then each warp ballots its bit over
+// them and, two spikes at a time, sums delta at its row's targets (hidden rows also sum
+// D into the readout gradient).
+constexpr int GATHER_THREADS = 1024;
+constexpr int GATHER_SPAN = 8192;
+
 template <typename real, int MAXCH>
-__global__ void __launch_bounds__(GATHER_WARPS * 32)
+__global__ void __launch_bounds__(GATHER_THREADS)
     k_gather(const uint32_t* __restrict__ x_rec, const uint32_t* __restrict__ z_rec, int Win, int Wh,
              const int32_t* __restrict__ in_len, const int32_t* __restrict__ in_ind, int in_C, int n_in,
              const int32_t* __restrict__ rec_len, const int32_t* __restrict__ rec_ind, int rec_C, int N,
              const real* __restrict__ delta, const real* __restrict__ D, int K, int Kp, long long BT,
              long long bt_per, real* __restrict__ part_in, real* __restrict__ part_rec,
              real* __restrict__ part_out) {
-    const int lane = lane_id();
-    const int r = blockIdx.x * GATHER_WARPS + (threadIdx.x >> 5);
+    __shared__ uint32_t words[GATHER_SPAN];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int col = blockIdx.x;
     const int ks = blockIdx.y;
-    if (r >= n_in + N) return;
-    const bool is_in = r < n_in;
-    const int i = is_in ? r : r - n_in;
+    const bool is_in = col < Win;
+    const int wi = is_in ? col : col - Win;
+    const int i = wi * 32 + warp;
+    const int P = is_in ? n_in : N;
+    const bool row_ok = i < P;
     const uint32_t* bits = is_in ? x_rec : z_rec;
     const int W = is_in ? Win : Wh;
     const int C = is_in ? in_C : rec_C;
-    const int len = is_in ? in_len[i] : rec_len[i];
-    const int32_t* ri = (is_in ? in_ind : rec_ind) + (size_t)i * C;
+    const long long bt0 = (long long)ks * bt_per;
+    const long long bt1 = min(BT, bt0 + bt_per);
+    for (int k = threadIdx.x; k < GATHER_SPAN; k += GATHER_THREADS) {
+        const long long my = bt0 + k;
+        words[k] = (my < bt1) ? bits[my * W + wi] : 0u;
+    }
+    const int len = row_ok ? (is_in ? in_len[i] : rec_len[i]) : 0;
+    const int32_t* ri = (is_in ? in_ind : rec_ind) + (size_t)(row_ok ? i : 0) * C;
     int tgt[MAXCH];
     real acc[MAXCH];
 #pragma unroll
     for (int c = 0; c < MAXCH; ++c) {
-        int s = c * 32 + lane;
+        const int s = c * 32 + lane;
         tgt[c] = (s < len) ? ri[s] : -1;
         acc[c] = 0;
     }
     real acc_o = 0;
-    const bool do_out = !is_in && lane < K;
-    const int wi = i >> 5;
-    const uint32_t bit = 1u << (i & 31);
-    const long long bt0 = (long long)ks * bt_per;
-    const long long bt1 = min(BT, bt0 + bt_per);
-    for (long long base = bt0; base < bt1; base += 32) {
-        long long my = base + lane;
-        uint32_t word = (my < bt1) ? bits[my * W + wi] : 0u;
-        uint32_t spk = __ballot_sync(0xffffffffu, (word & bit) != 0u);
+    const bool do_out = !is_in && row_ok && lane < K;
+    const uint32_t bit = 1u << warp;
+    __syncthreads();
+    if (!row_ok) return;
+    const int span = bt1 > bt0 ? (int)(bt1 - bt0) : 0;
+    for (int sub = 0; sub < span; sub += 32) {
+        uint32_t spk = __ballot_sync(0xffffffffu, (words[sub + lane] & bit) != 0u);
         while (spk) {
-            long long e = base + __ffs(spk) - 1;
+            const long long e0 = bt0 + sub + __ffs(spk) - 1;
             spk &= spk - 1u;
-            const real* dl = delta + e * N;
+            const bool two = spk != 0u;
+            const long long e1 = two ? bt0 + sub + __ffs(spk) - 1 : e0;
+            if (two) spk &= spk - 1u;
+            const real* d0 = delta + e0 * N;
+            const real* d1 = delta + e1 * N;
+            real v0[MAXCH], v1[MAXCH];
 #pragma unroll
-            for (int c = 0; c < MAXCH; ++c)
-                if (tgt[c] >= 0) acc[c] += dl[tgt[c]];
-            if (do_out) acc_o += D[e * Kp + lane];
+            for (int c = 0; c < MAXCH; ++c) {
+                v0[c] = tgt[c] >= 0 ? d0[tgt[c]] : real(0);
+                v1[c] = (two && tgt[c] >= 0) ? d1[tgt[c]] : real(0);
+            }
+#pragma unroll
+            for (int c = 0; c < MAXCH; ++c) acc[c] += v0[c] + v1[c];
+            if (do_out) acc_o += D[e0 * Kp + lane] + (two ? D[e1 * Kp + lane] : real(0));
         }
     }
     real* part = is_in ? part_in : part_rec;
-    const size_t P = is_in ? (size_t)n_in : (size_t)N;
 #pragma unroll
     for (int c = 0; c < MAXCH; ++c) {
-        int s = c * 32 + lane;
+        const int s = c * 32 + lane;
         if (s < len) part[((size_t)ks * P + i) * C + s] = acc[c];
     }
     if (do_out) part_out[((size_t)ks * N + i) * K + lane] = acc_o;
@@ -440,45 +578,86 @@ __global__ void k_adam_dense(real* __restrict__ w, real* __restrict__ m, real* _
 }
 
 // ------------------------------------------------------------------ host side
-static size_t fwd_smem(int N, int Win, int Wh, size_t rsz) {
-    return (size_t)N * 8 + 2 * (size_t)N * rsz + 32 * rsz + (size_t)(2 * Win + 2 * Wh) * 4;
+static size_t fwd_smem(int n_in, int N, int Win, int Wh) {
+    return (size_t)(N + 32) * 8 + 64 * 8 + (size_t)(n_in + N) * 4 * 3 + 8 + (size_t)(Win + 2 * Wh) * 4;
+}
+
+template <typename real, int NPT>
+static snn_status launch_forward(const FwdParams<real>& p, int B, size_t smem, cudaStream_t s) {
+    if (smem > 48 * 1024)
+        SNN_CUDA(cudaFuncSetAttribute(k_forward<real, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_forward<real, NPT><<<B, FWD_THREADS, smem, s>>>(p);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+template <typename real>
+static snn_status refresh_fixed(snn_classifier* c, cudaStream_t s) {
+    const snn_classifier_desc& d = c->d;
+    const long long n_in = (long long)d.w_in->d.P * d.w_in->d.C, n_rec = (long long)d.w_rec->d.P * d.w_rec->d.C,
+                    n_out = (long long)d.K * d.N;
+    k_pack<real><<<ceil_div(n_in, 256), 256, 0, s>>>((const real*)d.w_in->d.w, d.w_in->d.ind, d.w_in->d.row_len,
+                                                      d.w_in->d.C, (long long*)c->wf_in, n_in);
+    SNN_LAUNCH_CHECK();
+    k_pack<real><<<ceil_div(n_rec, 256), 256, 0, s>>>((const real*)d.w_rec->d.w, d.w_rec->d.ind, d.w_rec->d.row_len,
+                                                       d.w_rec->d.C, (long long*)c->wf_rec, n_rec);
+    SNN_LAUNCH_CHECK();
+    k_to_fixed<real><<<ceil_div(n_out, 256), 256, 0, s>>>((const real*)d.W_out, (long long*)c->wf_out, n_out);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
 }
 
 template <typename real>
 static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int n_steps, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
+    const int Win = (d.n_in + 31) / 32, Wh = (d.N + 31) / 32;
+    InputParams ip;
+    ip.n_in = d.n_in;
+    ip.Win = Win;
+    ip.T = bt->T;
+    ip.t0 = t0;
+    ip.n_steps = n_steps;
+    ip.n_bins = d.n_bins;
+    ip.n_classes = d.n_classes;
+    ip.B = bt->B;
+    ip.in_thr = d.in_thr;
+    ip.seed = d.in_seed;
+    ip.labels = bt->labels;
+    ip.bin_len = bt->bin_len;
+    ip.trial_ids = bt->trial_ids;
+    ip.x_rec = bt->x_rec;
+    ip.status = d.w_in->status;
+    const long long groups = (long long)bt->B * n_steps * Win * 8;
+    k_input<<<ceil_div(groups, 256), 256, 0, s>>>(ip);
+    SNN_LAUNCH_CHECK();
+
     FwdParams<real> p;
     p.n_in = d.n_in;
     p.N = d.N;
     p.K = d.K;
-    p.Win = (d.n_in + 31) / 32;
-    p.Wh = (d.N + 31) / 32;
+    p.Win = Win;
+    p.Wh = Wh;
     p.T = bt->T;
     p.t0 = t0;
     p.n_steps = n_steps;
+    p.n_classes = d.n_classes;
     p.alpha = (real)c->alpha;
     p.rho = (real)c->rho;
     p.beta = (real)d.beta;
     p.v_thr = (real)d.v_thr;
     p.psi_scale = (real)(0.3 / d.v_thr);
     p.inv_vthr = (real)(1.0 / d.v_thr);
-    p.in_thr = d.in_thr;
-    p.n_bins = d.n_bins;
-    p.n_classes = d.n_classes;
-    p.in_seed = d.in_seed;
     p.status = d.w_in->status;
     p.labels = bt->labels;
-    p.bin_len = bt->bin_len;
-    p.trial_ids = bt->trial_ids;
     p.in_len = d.w_in->d.row_len;
     p.in_ind = d.w_in->d.ind;
-    p.in_w = (const real*)d.w_in->d.w;
+    p.in_pk = (const long long*)c->wf_in;
     p.in_C = d.w_in->d.C;
     p.rec_len = d.w_rec->d.row_len;
     p.rec_ind = d.w_rec->d.ind;
-    p.rec_w = (const real*)d.w_rec->d.w;
+    p.rec_pk = (const long long*)c->wf_rec;
     p.rec_C = d.w_rec->d.C;
-    p.W_out = (const real*)d.W_out;
+    p.out_wf = (const long long*)c->wf_out;
     p.b_out = (const real*)d.b_out;
     p.v = (real*)bt->v;
     p.a = (real*)bt->a;
@@ -493,14 +672,26 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.v_rec = (real*)bt->v_rec;
     p.a_rec = (real*)bt->a_rec;
     p.y_rec = (real*)bt->y_rec;
-    size_t smem = fwd_smem(d.N, p.Win, p.Wh, sizeof(real));
-    SNN_REQUIRE(smem <= 227 * 1024, "snn_step_neurons: N = %d needs %zu bytes of shared memory (max 227 KB)", d.N,
-                smem);
-    if (smem > 48 * 1024)
-        SNN_CUDA(cudaFuncSetAttribute(k_forward<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_forward<real><<<bt->B, FWD_THREADS, smem, s>>>(p);
-    SNN_LAUNCH_CHECK();
-    return SNN_OK;
+    p.record_state = (bt->v_rec && bt->a_rec) ? 1 : 0;
+    const size_t smem = fwd_smem(d.n_in, d.N, Win, Wh);
+    snn_status st = refresh_fixed<real>(c, s);
+    if (st != SNN_OK) return st;
+    SNN_REQUIRE(smem <= 227 * 1024, "snn_step_neurons: n_in = %d, N = %d need %zu bytes of shared memory (max 227 KB)",
+                d.n_in, d.N, smem);
+    const int npt = (d.N + FWD_THREADS - 1) / FWD_THREADS;
+    if (npt <= 1) return launch_forward<real, 1>(p, bt->B, smem, s);
+    if (npt <= 2) return launch_forward<real, 2>(p, bt->B, smem, s);
+    if (npt <= 4) return launch_forward<real, 4>(p, bt->B, smem, s);
+    return launch_forward<real, 8>(p, bt->B, smem, s);
+}
+
+template <typename real, int KV>
+static void launch_backward(const snn_classifier* c, const snn_batch* bt, real* gb_part, cudaStream_t s) {
+    const snn_classifier_desc& d = c->d;
+    dim3 g(ceil_div(d.N, BWD_THREADS), bt->B);
+    k_backward<real, KV><<<g, BWD_THREADS, 0, s>>>((const real*)bt->psi_rec, (const real*)bt->d_rec,
+                                                   (const real*)d.W_out, (real*)bt->delta, (real*)bt->Dout, gb_part,
+                                                   bt->T, d.N, d.K, (real)c->alpha, (real)c->rho, (real)d.beta);
 }
 
 template <typename real>
@@ -508,27 +699,30 @@ static snn_status grad_impl(snn_classifier* c, const snn_batch* bt, cudaStream_t
     const snn_classifier_desc& d = c->d;
     const int B = bt->B, T = bt->T, N = d.N, K = d.K, Kp = (K + 3) & ~3;
     const int Win = (d.n_in + 31) / 32, Wh = (N + 31) / 32;
-    const real alpha = (real)c->alpha, rho = (real)c->rho, beta = (real)d.beta;
     real* gb_part = (real*)c->part_out + (size_t)c->KS * N * K;
-    k_readout_backward<real><<<ceil_div((long long)B * Kp, 128), 128, 0, s>>>(
-        (const real*)bt->d_rec, (real*)bt->Dout, gb_part, B, T, K, Kp, alpha);
+    switch (Kp / 4) {
+        case 1: launch_backward<real, 1>(c, bt, gb_part, s); break;
+        case 2: launch_backward<real, 2>(c, bt, gb_part, s); break;
+        case 3: launch_backward<real, 3>(c, bt, gb_part, s); break;
+        case 4: launch_backward<real, 4>(c, bt, gb_part, s); break;
+        case 5: launch_backward<real, 5>(c, bt, gb_part, s); break;
+        case 6: launch_backward<real, 6>(c, bt, gb_part, s); break;
+        case 7: launch_backward<real, 7>(c, bt, gb_part, s); break;
+        default: launch_backward<real, 8>(c, bt, gb_part, s); break;
+    }
     SNN_LAUNCH_CHECK();
     k_reduce_gb<real><<<1, 32, 0, s>>>(gb_part, (real*)d.G_b, B, K);
     SNN_LAUNCH_CHECK();
-    dim3 gb(ceil_div(N, 128), B);
-    k_neuron_backward<real><<<gb, 128, 0, s>>>((const real*)bt->psi_rec, (const real*)bt->Dout,
-                                               (const real*)d.W_out, (real*)bt->delta, B, T, N, K, Kp, alpha, rho,
-                                               beta);
-    SNN_LAUNCH_CHECK();
     const long long BT = (long long)B * T;
     const int KS = c->KS;
-    long long bt_per = ((BT + KS - 1) / KS + 31) / 32 * 32;
-    dim3 gg(ceil_div(d.n_in + N, GATHER_WARPS), KS);
+    const long long bt_per = ((BT + KS - 1) / KS + 31) / 32 * 32;
+    SNN_REQUIRE(bt_per <= GATHER_SPAN, "snn_eprop_update: internal K-split too small");
+    dim3 gg(Win + Wh, KS);
     const snn_ragged_desc& ri = d.w_in->d;
     const snn_ragged_desc& rr = d.w_rec->d;
     int Cmax = ri.C > rr.C ? ri.C : rr.C;
 #define SNN_GATHER(MC)                                                                                        \
-    k_gather<real, MC><<<gg, GATHER_WARPS * 32, 0, s>>>(                                                       \
+    k_gather<real, MC><<<gg, GATHER_THREADS, 0, s>>>(                                                          \
         bt->x_rec, bt->z_rec, Win, Wh, ri.row_len, ri.ind, ri.C, d.n_in, rr.row_len, rr.ind, rr.C, N,          \
         (const real*)bt->delta, (const real*)bt->Dout, K, Kp, BT, bt_per, (real*)c->part_in, (real*)c->part_rec, \
         (real*)c->part_out)
@@ -596,6 +790,9 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     SNN_REQUIRE(d->tau_m > 0 && d->dt > 0 && d->v_thr > 0, "snn_create_classifier: tau_m, dt, v_thr must be > 0");
     SNN_REQUIRE(d->max_B > 0 && d->max_T > 0, "snn_create_classifier: max_B, max_T must be > 0");
     SNN_REQUIRE(d->w_in->d.C <= 2048 && d->w_rec->d.C <= 2048, "snn_create_classifier: row capacity must be <= 2048");
+    SNN_REQUIRE(d->N <= 8 * 256, "snn_create_classifier: N must be <= 2048");
+    SNN_REQUIRE(d->N < 4096, "snn_create_classifier: N must fit the 12-bit packed target index");
+    SNN_REQUIRE(d->n_in <= 1024, "snn_create_classifier: n_in must be <= 1024");
     snn_classifier* c = (snn_classifier*)calloc(1, sizeof(snn_classifier));
     if (!c) {
         set_error("snn_create_classifier: out of host memory");
@@ -605,7 +802,8 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     c->alpha = std::exp(-d->dt / d->tau_m);
     c->rho = d->tau_a > 0 ? std::exp(-d->dt / d->tau_a) : 0.0;
     long long BT = (long long)d->max_B * d->max_T;
-    c->KS = BT >= 65536 ? 16 : (BT >= 4096 ? 4 : 1);
+    // K-splits of the gather: each CTA stages at most 8192 (trial, step) spike words
+    c->KS = (int)((BT + 8191) / 8192);
     size_t rsz = d->dtype == SNN_F32 ? 4 : 8;
     size_t n_in_part = (size_t)c->KS * d->w_in->d.P * d->w_in->d.C * rsz;
     size_t n_rec_part = (size_t)c->KS * d->w_rec->d.P * d->w_rec->d.C * rsz;
@@ -613,6 +811,9 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     cudaError_t e = cudaMalloc(&c->part_in, n_in_part);
     if (e == cudaSuccess) e = cudaMalloc(&c->part_rec, n_rec_part);
     if (e == cudaSuccess) e = cudaMalloc(&c->part_out, n_out_part);
+    if (e == cudaSuccess) e = cudaMalloc(&c->wf_in, (size_t)d->w_in->d.P * d->w_in->d.C * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->wf_rec, (size_t)d->w_rec->d.P * d->w_rec->d.C * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->wf_out, (size_t)d->K * d->N * 8);
     if (e != cudaSuccess) {
         snn_destroy_classifier(c);
         set_error("snn_create_classifier: cudaMalloc failed: %s", cudaGetErrorString(e));
@@ -627,6 +828,9 @@ snn_status snn_destroy_classifier(snn_classifier* c) {
     cudaFree(c->part_in);
     cudaFree(c->part_rec);
     cudaFree(c->part_out);
+    cudaFree(c->wf_in);
+    cudaFree(c->wf_rec);
+    cudaFree(c->wf_out);
     free(c);
     return SNN_OK;
 }

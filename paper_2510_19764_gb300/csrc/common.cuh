@@ -111,11 +111,34 @@ inline uint64_t prob_threshold(double p) {
 constexpr double FIX_SCALE = 1099511627776.0;       // 2^40
 constexpr double FIX_INV = 1.0 / 1099511627776.0;
 
-__device__ __forceinline__ long long to_fixed(float w) { return __float2ll_rn(w * 1099511627776.0f); }
+// float -> int64 with 40 fractional bits using 32-bit integer operations only (GB300's
+// FP64 pipe is narrow, so the FP32 path avoids 64-bit float and 64-bit conversions).
+// Exact for |w| >= 2^-17; smaller magnitudes round half up; |w| must be < 2^23.
+__device__ __forceinline__ long long to_fixed(float w) {
+    const unsigned u = __float_as_uint(w);
+    const int e = (int)((u >> 23) & 0xffu);
+    const unsigned m = (u & 0x7fffffu) | 0x800000u;
+    const int sh = e - 110;                 // w * 2^40 = m * 2^(e - 110)
+    unsigned long long r = 0;
+    if (e != 0) {
+        if (sh >= 0) r = (unsigned long long)m << (sh < 39 ? sh : 39);
+        else if (sh > -25) r = ((unsigned long long)m + (1ull << (-sh - 1))) >> (-sh);
+    }
+    return (u >> 31) ? -(long long)r : (long long)r;
+}
 __device__ __forceinline__ long long to_fixed(double w) { return __double2ll_rn(w * FIX_SCALE); }
 template <typename real>
-__device__ __forceinline__ real from_fixed(long long a) {
-    return (real)((double)a * FIX_INV);
+__device__ __forceinline__ real from_fixed(long long a);
+template <>
+__device__ __forceinline__ double from_fixed<double>(long long a) {
+    return (double)a * FIX_INV;
+}
+// int64 (40 fractional bits) -> float from its two 32-bit halves, FP32 operations only
+template <>
+__device__ __forceinline__ float from_fixed<float>(long long a) {
+    const int hi = (int)(a >> 32);
+    const unsigned lo = (unsigned)(a & 0xffffffffll);
+    return __fmaf_rn((float)hi, 0.00390625f, (float)lo * 9.094947017729282e-13f);
 }
 
 // ------------------------------------------------------------------ warp helpers
@@ -181,4 +204,7 @@ struct snn_classifier {
     void* part_in;           // [KS][P_in*C_in] partial gradients
     void* part_rec;          // [KS][N*C_rec]
     void* part_out;          // [KS][N][K]
+    void* wf_in;             // [P_in*C_in] int64 fixed-point shadow of w_in (refreshed per forward call)
+    void* wf_rec;            // [N*C_rec]
+    void* wf_out;            // [K*N]
 };

@@ -84,7 +84,7 @@ __global__ void k_topo_neurons(TopoK k, float* __restrict__ V, float* __restrict
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     bool z = false;
     if (j < k.N) {
-        const float I = (float)((double)acc[j] * FIX_INV);
+        const float I = from_fixed<float>(acc[j]);
         acc[j] = 0;
         const float g = gs[j] * k.ds + I;
         gs[j] = g;
