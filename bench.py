@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--sample-steps", type=int, default=600, help="oracle sample: steps of one trial")
     ap.add_argument("--batch", type=int, default=512, help="trials per batch (512 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--workload", default="classifier", choices=["classifier", "batched", "serve", "topo"],
+                    help="classifier (default, the benchmark line); batched: 64 uneven instances, plain vs "
+                         "graph-batched; serve: request loop latency; topo: topographic map steps/s")
+    ap.add_argument("--scale", type=int, default=2, help="topo: grid side 16*scale")
+    ap.add_argument("--topo-steps", type=int, default=10000)
     return ap.parse_args()
 
 
@@ -338,8 +343,137 @@ def run_reference(args, sample_steps: int, world: int, rank: int):
     return 1.0 / per_trial, per_trial, dt
 
 
+# ------------------------------------------------------------------ other workloads
+
+def run_batched(args):
+    """64 independent classifier instances of uneven size and trial length: plain
+    one-at-a-time execution with per-step launches vs one CUDA-graph replay per
+    iteration over 16 streams with autotuned row schedules."""
+    import torch
+    import synth
+    from paper_2510_19764_gb300 import abi, build, sched
+    build.build()
+    abi.load()
+    specs = sched.batched_specs(64, args.seed)
+    task = synth.spoken_digit_task(args.seed, n_in=sched.N_IN, n_classes=sched.N_CLASSES, T=1000,
+                                   n_bins=sched.N_BINS)
+    insts = [sched.Instance(s, task) for s in specs]
+    tuner = sched.Autotuner()
+    table = tuner.tune(insts)
+    br = sched.BatchedRunner(insts, n_streams=16)
+    for inst in insts:          # first calls outside capture
+        inst.enqueue(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    br.capture()
+    for _ in range(max(1, args.warmup)):
+        br.iterate()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        br.iterate()
+    b.record()
+    b.synchronize()
+    t_batched = a.elapsed_time(b) / 1e3 / args.steps
+    pr = sched.PlainRunner(insts)
+    pr.iterate()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pr.iterate()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    n = len(insts)
+    return {"workload": "batched", "metric": "training samples/s (64 uneven instances, one trial each)",
+            "instances": n, "steps_total": int(sum(s.T for s in specs)),
+            "batched_samples_per_s": round(n / t_batched, 2), "plain_samples_per_s": round(n / t_plain, 2),
+            "speedup": round(t_plain / t_batched, 2), "batched_ms_per_iteration": round(t_batched * 1e3, 3),
+            "plain_ms_per_iteration": round(t_plain * 1e3, 1),
+            "autotune_table": {str(k): v for k, v in table.items()},
+            "autotune_ms": {str(k): {w: round(t, 4) for w, t in v.items()} for k, v in tuner.timings.items()}}
+
+
+def run_serve(args):
+    """Request loop over 4 resident classifiers (hidden 256..2048, 10 %), requests of
+    100-1000 steps, 10 % fine-tuning jobs, Poisson arrivals at 200 / 1000 / 5000 req/s:
+    continuous batching vs one request at a time."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2510_19764_gb300 import abi, build, serve
+    build.build()
+    abi.load()
+    task = synth.spoken_digit_task(args.seed, n_in=serve.N_IN, n_classes=serve.N_CLASSES, T=serve.T_MAX,
+                                   n_bins=serve.N_BINS)
+    models = [serve.Model(i, N, task, max_batch=64) for i, N in enumerate((256, 512, 1024, 2048))]
+    eng = serve.Engine(models, max_batch=64, slots_per_model=3, n_streams=16)
+    warm = serve.poisson_requests(64, 1e6, len(models), seed=99)
+    eng.run(warm, realtime=False)
+    eng.run_plain(warm[:8], realtime=False)
+    out = {"workload": "serve", "metric": "served requests/s with p50/p99 latency", "rates": {}}
+    for rate in (200.0, 1000.0, 5000.0):
+        n = int(min(4000, rate * 2.0))
+        reqs = serve.poisson_requests(n, rate, len(models), seed=int(rate))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = eng.run(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        s_b = serve.latency_summary(res, wall)
+        t0 = time.perf_counter()
+        res_p = eng.run_plain(reqs, realtime=True)
+        wall_p = time.perf_counter() - t0
+        s_p = serve.latency_summary(res_p, wall_p)
+        same = all(np.array_equal(x.ysum, y.ysum) for x, y in zip(res, res_p))
+        out["rates"][str(int(rate))] = {"batched": s_b, "plain": s_p, "results_identical": bool(same)}
+    out["engine_stats"] = eng.stats
+    return out
+
+
+def run_topo(args):
+    """Topographic map (two L x L sheets, L = 16 * scale): steps/s of the full step
+    sequence (input, propagation, conductance LIF, STDP on both projections, rewiring
+    every 10 steps with 10 s^2 attempts per projection)."""
+    import torch
+    import synth
+    from paper_2510_19764_gb300 import abi, build, net
+    build.build()
+    abi.load()
+    L = 16 * args.scale
+    N = L * L
+    C = 64
+    ff = synth.topo_initial(args.seed + 1, L, 0.16, 2.5, C, 0.2)
+    lat = synth.topo_initial(args.seed + 2, L, 1.0, 1.0, C, 0.2)
+    dff = net.DeviceRagged(ff.row_len, ff.ind, ff.w, N, seed=11)
+    dlat = net.DeviceRagged(lat.row_len, lat.ind, lat.w, N, seed=12)
+    tp = net.topo_params(L=L, L_f=16 if args.scale > 2 else L)
+    n_att = 10 * args.scale * args.scale
+    rw_ff = net.topo_rewire(L, 0.16, 2.5, n_att)
+    rw_lat = net.topo_rewire(L, 1.0, 1.0, n_att)
+    st = net.DeviceTopoState(N, -70.0)
+    s_ff = torch.zeros(4, dtype=torch.int64, device="cuda")
+    s_lat = torch.zeros(4, dtype=torch.int64, device="cuda")
+    abi.snn_topo_run(tp, st.desc, dff.handle, dlat.handle, rw_ff, rw_lat, 5, 10, 0, 200, s_ff, s_lat)
+    torch.cuda.synchronize()
+    n = args.topo_steps
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    abi.snn_topo_run(tp, st.desc, dff.handle, dlat.handle, rw_ff, rw_lat, 5, 10, 200, n, s_ff, s_lat)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    stats_ff, stats_lat = s_ff.cpu().tolist(), s_lat.cpu().tolist()
+    return {"workload": "topo", "metric": "simulated steps/s (1 ms steps)", "L": L, "neurons_per_sheet": N,
+            "steps": n, "steps_per_s": round(n / (ms / 1e3), 1), "realtime_factor": round(n / (ms / 1e3) / 1000.0, 2),
+            "ms_per_1000_steps": round(ms / n * 1000, 3), "launches_per_step": 7 + 0.2,
+            "rewire_ff": dict(zip(["removed", "formed", "overflow", "attempts"], stats_ff)),
+            "rewire_lat": dict(zip(["removed", "formed", "overflow", "attempts"], stats_lat))}
+
+
 def main():
     args = parse()
+    if args.workload != "classifier":
+        fn = {"batched": run_batched, "serve": run_serve, "topo": run_topo}[args.workload]
+        print(json.dumps(fn(args)), flush=True)
+        return 0
     WORKLOAD["B"] = args.batch
     world, rank, local = dist_init(args)
     if args.impl == "reference":

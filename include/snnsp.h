@@ -58,7 +58,7 @@ typedef void* snn_stream;        /* cudaStream_t */
 /* Message for the most recent failing call on this host thread ("" if none). */
 const char* snn_last_error(void);
 /* ABI version of this header (bumped on any incompatible change). */
-int32_t snn_abi_version(void);
+int32_t snn_abi_version(void);   /* 3 */
 
 /* ==================================================================================
  * Ragged sparse matrix (Sec. 2.1, Fig. 1; DEEP R bitfields Sec. 2.1.2, Fig. 2)
@@ -131,6 +131,10 @@ snn_status snn_propagate(const snn_ragged* r, const uint32_t* pre_bits, int32_t 
  * the status word. */
 snn_status snn_rewire_deepr(snn_ragged* r, int64_t rewire_idx, snn_rewire_stats* stats,
                             snn_stream stream);
+/* Same as snn_rewire_deepr with the rewiring index read from device memory when the
+ * kernels run (rewire_idx_dev: device int64), so a captured CUDA graph can advance it. */
+snn_status snn_rewire_deepr_dev(snn_ragged* r, const int64_t* rewire_idx_dev, snn_rewire_stats* stats,
+                                snn_stream stream);
 
 /* DEEP R rewiring that allocates nothing (the paper has no counterpart; this entry
  * exists for callers that cannot allocate device memory).  Some callers cannot call
@@ -196,19 +200,24 @@ typedef struct {
     uint32_t* z_bits;          /* [B][Wh] hidden spikes of the last simulated step */
     uint32_t* x_rec;           /* [B][T][Win] recorded input spikes */
     uint32_t* z_rec;           /* [B][T][Wh] recorded hidden spikes */
-    void* psi_rec;             /* [B][T][N] recorded surrogate derivatives */
-    void* d_rec;               /* [B][T][K] recorded softmax(y) - onehot(label) */
+    void* psi_rec;             /* [B][T][N] recorded surrogate derivatives, or NULL (inference) */
+    void* d_rec;               /* [B][T][K] recorded softmax(y) - onehot(label), or NULL */
     void* ysum;                /* [B][K] sum over steps of y (prediction = argmax) */
     void* v_rec; void* a_rec;  /* optional [B][T][N] voltage / adaptation records (NULL = off) */
     void* y_rec;               /* optional [B][T][K] readout records (NULL = off) */
     void* delta;               /* workspace [B][T][N] (e-prop adjoint) */
     void* Dout;                /* workspace [B][T][Kp] (filtered readout error) */
+    const int32_t* trial_T;    /* [B] per-trial lengths (<= T) or NULL (all run T steps);
+                                  forward only: trials stop at their own length */
 } snn_batch;
 
 typedef struct {
     double lr, beta1, beta2, eps;
     double b1t, b2t;          /* beta1^t, beta2^t of this step (running products) */
     double l1;                /* DEEP R L1 strength (0: off); needs sign_bits */
+    const double* bias_dev;   /* optional device {beta1^t, beta2^t}: read by the kernels
+                                 instead of b1t, b2t (lets a captured CUDA graph advance
+                                 the step count on the device); NULL: use b1t, b2t */
 } snn_adam;
 
 #define SNN_EPROP_GRAD  0
@@ -217,6 +226,10 @@ typedef struct {
 /* Create a classifier handle; validates sizes and allocates fixed scratch for the
  * e-prop gradient partial sums (sized from max_B, max_T and the two ragged handles). */
 snn_status snn_create_classifier(const snn_classifier_desc* desc, snn_classifier** out);
+/* Row schedule of snn_step_neurons: how many warps (4, 8 or 16) share one trial's
+ * spiking rows and neurons (default 8).  Results do not depend on it (integer
+ * accumulation); an autotuner picks it per (N, row length, spike rate). */
+snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_trial);
 snn_status snn_destroy_classifier(snn_classifier* c);
 
 /* Advance every trial of the batch by n_steps steps, t0 .. t0+n_steps-1 (t0 + n_steps

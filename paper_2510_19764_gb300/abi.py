@@ -23,7 +23,7 @@ EXPORTED = [
     "snn_last_error", "snn_abi_version", "snn_create_ragged", "snn_destroy_ragged", "snn_ragged_status",
     "snn_propagate", "snn_rewire_deepr", "snn_create_classifier", "snn_destroy_classifier", "snn_step_neurons",
     "snn_eprop_update", "snn_topo_input", "snn_topo_neurons", "snn_stdp_update", "snn_rewire_topo", "snn_topo_run",
-    "snn_philox", "snn_rewire_deepr_noalloc",
+    "snn_philox", "snn_rewire_deepr_noalloc", "snn_classifier_set_schedule", "snn_rewire_deepr_dev",
 ]
 
 
@@ -62,11 +62,12 @@ class Batch(C.Structure):
     _fields_ = [("B", i32), ("T", i32), ("labels", vp), ("bin_len", vp), ("trial_ids", vp),
                 ("v", vp), ("a", vp), ("y", vp), ("x_bits", vp), ("z_bits", vp), ("x_rec", vp), ("z_rec", vp),
                 ("psi_rec", vp), ("d_rec", vp), ("ysum", vp), ("v_rec", vp), ("a_rec", vp), ("y_rec", vp),
-                ("delta", vp), ("Dout", vp)]
+                ("delta", vp), ("Dout", vp), ("trial_T", vp)]
 
 
 class Adam(C.Structure):
-    _fields_ = [("lr", f64), ("beta1", f64), ("beta2", f64), ("eps", f64), ("b1t", f64), ("b2t", f64), ("l1", f64)]
+    _fields_ = [("lr", f64), ("beta1", f64), ("beta2", f64), ("eps", f64), ("b1t", f64), ("b2t", f64), ("l1", f64),
+                ("bias_dev", vp)]
 
 
 class TopoParams(C.Structure):
@@ -119,6 +120,8 @@ def load() -> C.CDLL:
                                i32, vp, vp, vp]),
         "snn_philox": (i32, [u64, u64, vp, i64, vp, vp]),
         "snn_rewire_deepr_noalloc": (i32, [P(RaggedDesc), i64, vp, vp, vp]),
+        "snn_classifier_set_schedule": (i32, [vp, i32]),
+        "snn_rewire_deepr_dev": (i32, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -182,10 +185,18 @@ def snn_rewire_deepr_noalloc(desc: RaggedDesc, rewire_idx: int, stats=None, stat
     check(load().snn_rewire_deepr_noalloc(C.byref(desc), rewire_idx, ptr(stats), ptr(status), stream_ptr(stream)))
 
 
+def snn_rewire_deepr_dev(h: int, rewire_idx_dev, stats=None, stream=None) -> None:
+    check(load().snn_rewire_deepr_dev(h, ptr(rewire_idx_dev), ptr(stats), stream_ptr(stream)))
+
+
 def snn_create_classifier(desc: ClassifierDesc) -> int:
     h = vp()
     check(load().snn_create_classifier(C.byref(desc), C.byref(h)))
     return h.value
+
+
+def snn_classifier_set_schedule(h: int, warps_per_trial: int) -> None:
+    check(load().snn_classifier_set_schedule(h, warps_per_trial))
 
 
 def snn_destroy_classifier(h: int) -> None:

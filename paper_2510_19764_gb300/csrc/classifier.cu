@@ -25,7 +25,6 @@
 
 namespace snn {
 
-constexpr int FWD_THREADS = 256;
 
 template <typename real>
 struct FwdParams {
@@ -57,10 +56,12 @@ struct FwdParams {
     real* a_rec;
     real* y_rec;
     int record_state;
+    const int32_t* trial_T;   // per-trial lengths or NULL
 };
 
 struct InputParams {
     int n_in, Win, T, t0, n_steps, n_bins, n_classes, B;
+    const int32_t* trial_T;
     const uint64_t* in_thr;
     uint64_t seed;
     const int32_t* labels;
@@ -92,7 +93,7 @@ __global__ void k_input(InputParams p) {
             label = min(max(label, 0), p.n_classes - 1);
             bin_len = max(bin_len, 1);
         }
-        if (4 * gi < p.n_in) {
+        if (4 * gi < p.n_in && (!p.trial_T || t < p.trial_T[b])) {
             const int bin = min(p.n_bins - 1, t / bin_len);
             const uint64_t* thr = p.in_thr + ((size_t)label * p.n_bins + bin) * p.n_in;
             const u64x4 r = philox(p.seed, PH_INPUT, (uint64_t)p.trial_ids[b], (uint64_t)t, (uint64_t)gi, 0);
@@ -125,8 +126,8 @@ __global__ void k_input(InputParams p) {
 //      accumulator); hidden rows also add their readout column.  The last warp
 //      meanwhile finishes the readout of step t-1 (leak, softmax, d record).
 //  (B) each thread updates its NPT neurons (state in registers) and writes psi.
-template <typename real, int NPT>
-__global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
+template <typename real, int NPT, int TH>
+__global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh, n_in = p.n_in;
     const int R = n_in + N;
@@ -141,25 +142,26 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
     const int b = blockIdx.x;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    constexpr int nwarps = FWD_THREADS / 32;
+    constexpr int nwarps = TH / 32;
     constexpr int RO_WARP = nwarps - 1;
     int label = p.labels[b];
     label = min(max(label, 0), p.n_classes - 1);  // validity is reported by k_input
-    const int t0 = p.t0, t_end = p.t0 + p.n_steps;
+    const int t0 = p.t0;
+    const int t_end = p.trial_T ? min(p.t0 + p.n_steps, max(p.trial_T[b], p.t0)) : p.t0 + p.n_steps;
     real vr[NPT], ar[NPT];
     {
         const int prv = (t0 - 1) & 1;
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
-            const int j = tid + q * FWD_THREADS;
+            const int j = tid + q * TH;
             vr[q] = j < N ? p.v[(size_t)b * N + j] : real(0);
             ar[q] = j < N ? p.a[(size_t)b * N + j] : real(0);
         }
-        for (int j = tid; j < N + 32; j += FWD_THREADS) Iacc[j] = 0;
-        for (int j = tid; j < N; j += FWD_THREADS) lens[n_in + j] = p.rec_len[j];
-        for (int i = tid; i < n_in; i += FWD_THREADS) lens[i] = p.in_len[i];
+        for (int j = tid; j < N + 32; j += TH) Iacc[j] = 0;
+        for (int j = tid; j < N; j += TH) lens[n_in + j] = p.rec_len[j];
+        for (int i = tid; i < n_in; i += TH) lens[i] = p.in_len[i];
         if (tid < 64) yfix[tid] = 0;
-        for (int w = tid; w < Wh; w += FWD_THREADS) zb[prv * Wh + w] = p.z_bits[(size_t)b * Wh + w];
+        for (int w = tid; w < Wh; w += TH) zb[prv * Wh + w] = p.z_bits[(size_t)b * Wh + w];
         if (warp == 0) {
             // lists of step t0-1 from the state's spike words
             if (lane == 0) lcnt[prv] = 0;
@@ -180,9 +182,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
     }
     const uint32_t* xrec_b = p.x_rec + (size_t)b * p.T * Win;
     uint32_t* zrec_b = p.z_rec + (size_t)b * p.T * Wh;
-    real* psi_b = p.psi_rec + (size_t)b * p.T * N;
-    real* d_b = p.d_rec + (size_t)b * p.T * K;
-    uint32_t xnext = (warp == 0 && lane < Win) ? xrec_b[(size_t)t0 * Win + lane] : 0u;
+    real* psi_b = p.psi_rec ? p.psi_rec + (size_t)b * p.T * N : nullptr;   // NULL: inference, no records
+    real* d_b = p.d_rec ? p.d_rec + (size_t)b * p.T * K : nullptr;
+    uint32_t xnext = (warp == 0 && lane < Win && t0 < t_end) ? xrec_b[(size_t)t0 * Win + lane] : 0u;
     __syncthreads();
     unsigned long long* acc = (unsigned long long*)Iacc;
 
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
         if (lane < K) ex = exp_real(ynew - mx);
         const real ssum = warp_sum(ex);
         if (lane < K) {
-            d_b[(size_t)s * K + lane] = ex / ssum - (lane == label ? real(1) : real(0));
+            if (d_b) d_b[(size_t)s * K + lane] = ex / ssum - (lane == label ? real(1) : real(0));
             if (p.y_rec) p.y_rec[((size_t)b * p.T + s) * K + lane] = ynew;
         }
     };
@@ -262,10 +264,10 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
             for (int k = 0; word; ++k, word &= word - 1u) lcur[pos + k] = lane * 32 + __ffs(word) - 1;
             xw[lane] = 0u;
         }
-        real* psi_t = psi_b + (size_t)t * N;
+        real* psi_t = psi_b ? psi_b + (size_t)t * N : nullptr;
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
-            const int j = tid + q * FWD_THREADS;
+            const int j = tid + q * TH;
             if (j < N) {
                 const real I = from_fixed<real>(Iacc[j]);
                 Iacc[j] = 0;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
                 const real aa = p.rho * ar[q] + (zp ? real(1) : real(0));
                 const real A = p.v_thr + p.beta * aa;
                 const real u = real(1) - fabs((v - A) * p.inv_vthr);
-                psi_t[j] = p.psi_scale * (u > real(0) ? u : real(0));
+                if (psi_t) psi_t[j] = p.psi_scale * (u > real(0) ? u : real(0));
                 vr[q] = v;
                 ar[q] = aa;
                 if (p.record_state) {
@@ -297,17 +299,19 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_forward(FwdParams<real> p) {
         }
         __syncthreads();
     }
-    const int last = t_end - 1;
-    const int cl = last & 1;
-    if (warp == RO_WARP) readout(last);
-    for (int w = tid; w < Wh; w += FWD_THREADS) {
-        zrec_b[(size_t)last * Wh + w] = zb[cl * Wh + w];
-        p.z_bits[(size_t)b * Wh + w] = zb[cl * Wh + w];
+    if (t_end > t0) {
+        const int last = t_end - 1;
+        const int cl = last & 1;
+        if (warp == RO_WARP) readout(last);
+        for (int w = tid; w < Wh; w += TH) {
+            zrec_b[(size_t)last * Wh + w] = zb[cl * Wh + w];
+            p.z_bits[(size_t)b * Wh + w] = zb[cl * Wh + w];
+        }
+        for (int w = tid; w < Win; w += TH) p.x_bits[(size_t)b * Win + w] = xrec_b[(size_t)last * Win + w];
     }
-    for (int w = tid; w < Win; w += FWD_THREADS) p.x_bits[(size_t)b * Win + w] = xrec_b[(size_t)last * Win + w];
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
-        const int j = tid + q * FWD_THREADS;
+        const int j = tid + q * TH;
         if (j < N) {
             p.v[(size_t)b * N + j] = vr[q];
             p.a[(size_t)b * N + j] = ar[q];
@@ -542,13 +546,24 @@ __device__ __forceinline__ void adam_update(real& w, real& m, real& v, real g, r
     w = w - lr * mh / (sqrt(vh) + eps);
 }
 
+// bias_dev (optional): device {beta1^t, beta2^t}; replaces bc1 = 1 - beta1^t, bc2 = 1 - beta2^t
+template <typename real>
+__device__ __forceinline__ void bias_from_device(const double* bias_dev, real& bc1, real& bc2) {
+    if (bias_dev) {
+        bc1 = (real)(1.0 - bias_dev[0]);
+        bc2 = (real)(1.0 - bias_dev[1]);
+    }
+}
+
 template <typename real>
 __global__ void k_adam_ragged(const int32_t* __restrict__ len, const int32_t* __restrict__ ind, int P, int C, int Qw,
                               real* __restrict__ w, real* __restrict__ m, real* __restrict__ v,
                               const real* __restrict__ grad, const uint32_t* __restrict__ sign, real l1, real lr,
-                              real b1, real b2, real omb1, real omb2, real eps, real bc1, real bc2) {
+                              real b1, real b2, real omb1, real omb2, real eps, real bc1, real bc2,
+                              const double* __restrict__ bias_dev) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)P * C) return;
+    bias_from_device(bias_dev, bc1, bc2);
     int i = (int)(idx / C), s = (int)(idx % C);
     if (s >= len[i]) return;
     real g = grad[idx];
@@ -567,9 +582,10 @@ __global__ void k_adam_ragged(const int32_t* __restrict__ len, const int32_t* __
 template <typename real>
 __global__ void k_adam_dense(real* __restrict__ w, real* __restrict__ m, real* __restrict__ v,
                              const real* __restrict__ grad, int n, real lr, real b1, real b2, real omb1,
-                             real omb2, real eps, real bc1, real bc2) {
+                             real omb2, real eps, real bc1, real bc2, const double* __restrict__ bias_dev) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
+    bias_from_device(bias_dev, bc1, bc2);
     real ww = w[idx], mm = m[idx], vv = v[idx];
     adam_update(ww, mm, vv, grad[idx], lr, b1, b2, omb1, omb2, eps, bc1, bc2);
     w[idx] = ww;
@@ -582,13 +598,31 @@ static size_t fwd_smem(int n_in, int N, int Win, int Wh) {
     return (size_t)(N + 32) * 8 + 64 * 8 + (size_t)(n_in + N) * 4 * 3 + 8 + (size_t)(Win + 2 * Wh) * 4;
 }
 
-template <typename real, int NPT>
+template <typename real, int NPT, int TH>
 static snn_status launch_forward(const FwdParams<real>& p, int B, size_t smem, cudaStream_t s) {
-    if (smem > 48 * 1024)
-        SNN_CUDA(cudaFuncSetAttribute(k_forward<real, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_forward<real, NPT><<<B, FWD_THREADS, smem, s>>>(p);
+    // raise the dynamic shared-memory limit once per device and size (not inside graph capture)
+    static int set_for[64] = {0};
+    int dev = 0;
+    SNN_CUDA(cudaGetDevice(&dev));
+    if (smem > 48 * 1024 && dev < 64 && set_for[dev] < (int)smem) {
+        SNN_CUDA(cudaFuncSetAttribute(k_forward<real, NPT, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        set_for[dev] = (int)smem;
+    }
+    k_forward<real, NPT, TH><<<B, TH, smem, s>>>(p);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
+}
+
+// Row schedule: TH threads (TH / 32 warps) share one trial's spiking rows.
+template <typename real, int TH>
+static snn_status launch_forward_th(const FwdParams<real>& p, int B, size_t smem, cudaStream_t s) {
+    const int npt = (p.N + TH - 1) / TH;
+    if (npt <= 1) return launch_forward<real, 1, TH>(p, B, smem, s);
+    if (npt <= 2) return launch_forward<real, 2, TH>(p, B, smem, s);
+    if (npt <= 4) return launch_forward<real, 4, TH>(p, B, smem, s);
+    if (npt <= 8) return launch_forward<real, 8, TH>(p, B, smem, s);
+    SNN_REQUIRE(false, "snn_step_neurons: N = %d too large for %d threads per trial", p.N, TH);
 }
 
 template <typename real>
@@ -627,6 +661,7 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     ip.trial_ids = bt->trial_ids;
     ip.x_rec = bt->x_rec;
     ip.status = d.w_in->status;
+    ip.trial_T = bt->trial_T;
     const long long groups = (long long)bt->B * n_steps * Win * 8;
     k_input<<<ceil_div(groups, 256), 256, 0, s>>>(ip);
     SNN_LAUNCH_CHECK();
@@ -673,16 +708,17 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.a_rec = (real*)bt->a_rec;
     p.y_rec = (real*)bt->y_rec;
     p.record_state = (bt->v_rec && bt->a_rec) ? 1 : 0;
+    p.trial_T = bt->trial_T;
     const size_t smem = fwd_smem(d.n_in, d.N, Win, Wh);
     snn_status st = refresh_fixed<real>(c, s);
     if (st != SNN_OK) return st;
     SNN_REQUIRE(smem <= 227 * 1024, "snn_step_neurons: n_in = %d, N = %d need %zu bytes of shared memory (max 227 KB)",
                 d.n_in, d.N, smem);
-    const int npt = (d.N + FWD_THREADS - 1) / FWD_THREADS;
-    if (npt <= 1) return launch_forward<real, 1>(p, bt->B, smem, s);
-    if (npt <= 2) return launch_forward<real, 2>(p, bt->B, smem, s);
-    if (npt <= 4) return launch_forward<real, 4>(p, bt->B, smem, s);
-    return launch_forward<real, 8>(p, bt->B, smem, s);
+    switch (c->fwd_threads) {
+        case 128: return launch_forward_th<real, 128>(p, bt->B, smem, s);
+        case 512: return launch_forward_th<real, 512>(p, bt->B, smem, s);
+        default: return launch_forward_th<real, 256>(p, bt->B, smem, s);
+    }
 }
 
 template <typename real, int KV>
@@ -755,15 +791,15 @@ static snn_status apply_impl(snn_classifier* c, const snn_adam* ad, cudaStream_t
         const uint32_t* sign = (ad->l1 != 0.0) ? rd.sign_bits : nullptr;
         k_adam_ragged<real><<<ceil_div((long long)rd.P * rd.C, 256), 256, 0, s>>>(
             rd.row_len, rd.ind, rd.P, rd.C, r->Qw, (real*)rd.w, (real*)rd.m, (real*)rd.v, (const real*)rd.grad, sign,
-            (real)ad->l1, lr, b1, b2, omb1, omb2, eps, bc1, bc2);
+            (real)ad->l1, lr, b1, b2, omb1, omb2, eps, bc1, bc2, ad->bias_dev);
         SNN_LAUNCH_CHECK();
     }
     k_adam_dense<real><<<ceil_div(d.K * d.N, 256), 256, 0, s>>>((real*)d.W_out, (real*)d.W_out_m, (real*)d.W_out_v,
                                                                 (const real*)d.G_out, d.K * d.N, lr, b1, b2, omb1,
-                                                                omb2, eps, bc1, bc2);
+                                                                omb2, eps, bc1, bc2, ad->bias_dev);
     SNN_LAUNCH_CHECK();
     k_adam_dense<real><<<1, 32, 0, s>>>((real*)d.b_out, (real*)d.b_m, (real*)d.b_v, (const real*)d.G_b, d.K, lr, b1,
-                                        b2, omb1, omb2, eps, bc1, bc2);
+                                        b2, omb1, omb2, eps, bc1, bc2, ad->bias_dev);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -799,6 +835,7 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
         return SNN_ENOMEM;
     }
     c->d = *d;
+    c->fwd_threads = 256;
     c->alpha = std::exp(-d->dt / d->tau_m);
     c->rho = d->tau_a > 0 ? std::exp(-d->dt / d->tau_a) : 0.0;
     long long BT = (long long)d->max_B * d->max_T;
@@ -823,6 +860,16 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     return SNN_OK;
 }
 
+snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_trial) {
+    clear_error();
+    SNN_REQUIRE(c, "snn_classifier_set_schedule: NULL classifier");
+    SNN_REQUIRE(warps_per_trial == 4 || warps_per_trial == 8 || warps_per_trial == 16,
+                "snn_classifier_set_schedule: warps_per_trial must be 4, 8 or 16");
+    SNN_REQUIRE(c->d.N <= 8 * 32 * warps_per_trial, "snn_classifier_set_schedule: N = %d needs more warps", c->d.N);
+    c->fwd_threads = 32 * warps_per_trial;
+    return SNN_OK;
+}
+
 snn_status snn_destroy_classifier(snn_classifier* c) {
     if (!c) return SNN_OK;
     cudaFree(c->part_in);
@@ -841,7 +888,7 @@ static snn_status check_batch(const snn_classifier* c, const snn_batch* b) {
     SNN_REQUIRE(b->B <= c->d.max_B && b->T <= c->d.max_T, "batch (B=%d, T=%d) exceeds the classifier's max (%d, %d)",
                 b->B, b->T, c->d.max_B, c->d.max_T);
     SNN_REQUIRE(b->labels && b->bin_len && b->trial_ids && b->v && b->a && b->y && b->ysum && b->x_bits &&
-                    b->z_bits && b->x_rec && b->z_rec && b->psi_rec && b->d_rec,
+                    b->z_bits && b->x_rec && b->z_rec,
                 "batch has a NULL required array");
     return SNN_OK;
 }
@@ -866,7 +913,9 @@ snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase
     if (phase == SNN_EPROP_GRAD) {
         snn_status st = check_batch(c, b);
         if (st != SNN_OK) return st;
-        SNN_REQUIRE(b->delta && b->Dout, "snn_eprop_update: batch workspace delta/Dout missing");
+        SNN_REQUIRE(b->delta && b->Dout && b->psi_rec && b->d_rec,
+                    "snn_eprop_update: GRAD needs the psi/d records and the delta/Dout workspace");
+        SNN_REQUIRE(!b->trial_T, "snn_eprop_update: GRAD needs every trial to run all T steps (trial_T must be NULL)");
         SNN_REQUIRE(c->d.w_in->d.grad && c->d.w_rec->d.grad, "snn_eprop_update: ragged grad arrays missing");
         return c->d.dtype == SNN_F32 ? grad_impl<float>(c, b, s) : grad_impl<double>(c, b, s);
     }
@@ -875,7 +924,8 @@ snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase
         for (snn_ragged* r : {c->d.w_in, c->d.w_rec})
             SNN_REQUIRE(r->d.m && r->d.v && r->d.grad, "snn_eprop_update: ragged m, v, grad required for APPLY");
         SNN_REQUIRE(c->d.W_out_m && c->d.W_out_v && c->d.b_m && c->d.b_v, "snn_eprop_update: readout moments missing");
-        SNN_REQUIRE(adam->b1t < 1.0 && adam->b2t < 1.0, "snn_eprop_update: b1t, b2t must be beta^t with t >= 1");
+        SNN_REQUIRE(adam->bias_dev || (adam->b1t < 1.0 && adam->b2t < 1.0),
+                    "snn_eprop_update: b1t, b2t must be beta^t with t >= 1");
         return c->d.dtype == SNN_F32 ? apply_impl<float>(c, adam, s) : apply_impl<double>(c, adam, s);
     }
     SNN_REQUIRE(false, "snn_eprop_update: unknown phase %d", phase);

@@ -199,6 +199,7 @@ struct snn_ragged {
 
 struct snn_classifier {
     snn_classifier_desc d;
+    int32_t fwd_threads;     // row schedule of the forward: threads sharing one trial
     double alpha, rho;
     int32_t KS;              // K-splits of the e-prop gather
     void* part_in;           // [KS][P_in*C_in] partial gradients

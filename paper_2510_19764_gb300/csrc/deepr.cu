@@ -75,8 +75,10 @@ __device__ __forceinline__ long long block_sum_ll(long long x, long long* red) {
 __global__ void __launch_bounds__(1024)
     k_deepr_distribute(const int32_t* __restrict__ len, const int32_t* __restrict__ dormant, int32_t* __restrict__ room,
                        int32_t* __restrict__ taken, int32_t* __restrict__ cnt, int P, int C, int Q, int no_autapse,
-                       uint64_t seed, uint64_t rewire, int32_t* status, snn_rewire_stats* stats) {
+                       uint64_t seed, uint64_t rewire, const long long* ridx_dev, int32_t* status,
+                       snn_rewire_stats* stats) {
     __shared__ long long red[32];
+    if (ridx_dev) rewire = (uint64_t)*ridx_dev;
     long long dsum = 0;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int forb = (no_autapse && i < Q) ? 1 : 0;
@@ -125,8 +127,10 @@ template <typename real>
 __global__ void k_deepr_form(int32_t* __restrict__ len, int32_t* __restrict__ ind, real* __restrict__ w,
                              real* __restrict__ m, real* __restrict__ v, uint32_t* __restrict__ conn,
                              const int32_t* __restrict__ taken, int P, int C, int Q, int Qw, int no_autapse,
-                             uint64_t seed, uint64_t rewire, int32_t* status, snn_rewire_stats* stats) {
+                             uint64_t seed, uint64_t rewire, const long long* ridx_dev, int32_t* status,
+                             snn_rewire_stats* stats) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (ridx_dev) rewire = (uint64_t)*ridx_dev;
     if (i >= P) return;
     const int nt = taken[i];
     if (nt == 0) return;
@@ -189,18 +193,19 @@ __global__ void k_deepr_form(int32_t* __restrict__ len, int32_t* __restrict__ in
 }
 
 template <typename real>
-static snn_status rewire_impl(snn_ragged* r, uint64_t rewire, snn_rewire_stats* stats, cudaStream_t s) {
+static snn_status rewire_impl(snn_ragged* r, uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
+                              cudaStream_t s) {
     const snn_ragged_desc& d = r->d;
     const int blocks = ceil_div((long long)d.P * 32, 256);
     k_deepr_eliminate<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
                                                     d.sign_bits, d.conn_bits, r->dormant, d.P, d.C, r->Qw);
     SNN_LAUNCH_CHECK();
     k_deepr_distribute<<<1, 1024, 0, s>>>(d.row_len, r->dormant, r->room, r->taken, r->cnt, d.P, d.C, d.Q,
-                                          d.no_autapse, d.seed, rewire, r->status, stats);
+                                          d.no_autapse, d.seed, rewire, ridx_dev, r->status, stats);
     SNN_LAUNCH_CHECK();
     k_deepr_form<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v, d.conn_bits,
                                                r->taken, d.P, d.C, d.Q, r->Qw, d.no_autapse, d.seed, rewire,
-                                               r->status, stats);
+                                               ridx_dev, r->status, stats);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -250,10 +255,11 @@ static snn_status rewire_noalloc_impl(const snn_ragged_desc& d, int32_t* scratch
                                                     d.sign_bits, d.conn_bits, dormant, d.P, d.C, Qw);
     SNN_LAUNCH_CHECK();
     k_deepr_distribute<<<1, 1024, 0, s>>>(d.row_len, dormant, room, taken, cnt, d.P, d.C, d.Q, d.no_autapse, d.seed,
-                                          rewire, status, stats);
+                                          rewire, nullptr, status, stats);
     SNN_LAUNCH_CHECK();
     k_deepr_form<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v, d.conn_bits,
-                                               taken, d.P, d.C, d.Q, Qw, d.no_autapse, d.seed, rewire, status, stats);
+                                               taken, d.P, d.C, d.Q, Qw, d.no_autapse, d.seed, rewire, nullptr, status,
+                                               stats);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -292,6 +298,18 @@ extern "C" snn_status snn_rewire_deepr(snn_ragged* r, int64_t rewire_idx, snn_re
     SNN_REQUIRE(d.m && d.v && d.sign_bits && d.conn_bits,
                 "snn_rewire_deepr: needs Adam moments m, v and the sign / connectivity bitfields");
     cudaStream_t s = (cudaStream_t)stream;
-    return d.dtype == SNN_F32 ? rewire_impl<float>(r, (uint64_t)rewire_idx, stats, s)
-                              : rewire_impl<double>(r, (uint64_t)rewire_idx, stats, s);
+    return d.dtype == SNN_F32 ? rewire_impl<float>(r, (uint64_t)rewire_idx, nullptr, stats, s)
+                              : rewire_impl<double>(r, (uint64_t)rewire_idx, nullptr, stats, s);
+}
+
+extern "C" snn_status snn_rewire_deepr_dev(snn_ragged* r, const int64_t* rewire_idx_dev, snn_rewire_stats* stats,
+                                           snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(r && rewire_idx_dev, "snn_rewire_deepr_dev: NULL argument");
+    const snn_ragged_desc& d = r->d;
+    SNN_REQUIRE(d.m && d.v && d.sign_bits && d.conn_bits,
+                "snn_rewire_deepr_dev: needs Adam moments m, v and the sign / connectivity bitfields");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long* ridx = (const long long*)rewire_idx_dev;
+    return d.dtype == SNN_F32 ? rewire_impl<float>(r, 0, ridx, stats, s) : rewire_impl<double>(r, 0, ridx, stats, s);
 }

@@ -160,7 +160,7 @@ class DeviceBatch:
     """State, records and workspace of one batch of trials."""
 
     def __init__(self, cls: DeviceClassifier, labels, bin_len, trial_ids, T: int, record_state: bool = False,
-                 device="cuda", workspace: bool = True):
+                 device="cuda", workspace: bool = True, records: bool = True, trial_T=None):
         B = len(labels)
         N, K, n_in = cls.N, cls.K, cls.n_in
         td = _tdtype(cls.dtype)
@@ -175,8 +175,9 @@ class DeviceBatch:
         self.z_bits = z(B, words(N), dt=torch.int32)
         self.x_rec = z(B, T, words(n_in), dt=torch.int32)
         self.z_rec = z(B, T, words(N), dt=torch.int32)
-        self.psi_rec = torch.empty((B, T, N), dtype=td, device=device)
-        self.d_rec = torch.empty((B, T, K), dtype=td, device=device)
+        self.psi_rec = torch.empty((B, T, N), dtype=td, device=device) if records else None
+        self.d_rec = torch.empty((B, T, K), dtype=td, device=device) if records else None
+        self.trial_T = None if trial_T is None else torch.as_tensor(np.asarray(trial_T, np.int32), device=device)
         self.v_rec = self.a_rec = self.y_rec = None
         if record_state:
             self.v_rec = torch.empty((B, T, N), dtype=td, device=device)
@@ -187,7 +188,7 @@ class DeviceBatch:
         b = abi.Batch()
         b.B, b.T = B, T
         for name in ("labels", "bin_len", "trial_ids", "v", "a", "y", "x_bits", "z_bits", "x_rec", "z_rec",
-                     "psi_rec", "d_rec", "ysum", "v_rec", "a_rec", "y_rec", "delta", "Dout"):
+                     "psi_rec", "d_rec", "ysum", "v_rec", "a_rec", "y_rec", "delta", "Dout", "trial_T"):
             setattr(b, name, abi.ptr(getattr(self, name)))
         self.desc = b
 
@@ -211,11 +212,14 @@ def spikes_from_bits(bits: np.ndarray, n: int) -> np.ndarray:
 
 
 def adam_params(lr: float, step: int, l1: float = 0.0, beta1: float = 0.9, beta2: float = 0.999,
-                eps: float = 1e-8, b1t: float | None = None, b2t: float | None = None) -> abi.Adam:
+                eps: float = 1e-8, b1t: float | None = None, b2t: float | None = None, bias_dev=None) -> abi.Adam:
+    """Adam hyper-parameters; bias_dev (device float64 {beta1^t, beta2^t}) makes the
+    kernels read the bias corrections from device memory."""
     a = abi.Adam()
     a.lr, a.beta1, a.beta2, a.eps, a.l1 = lr, beta1, beta2, eps, l1
     a.b1t = beta1 ** step if b1t is None else b1t
     a.b2t = beta2 ** step if b2t is None else b2t
+    a.bias_dev = abi.ptr(bias_dev)
     return a
 
 

@@ -1,0 +1,208 @@
+"""Batched execution of many independent e-prop + DEEP R classifier instances.
+
+Each instance is its own sparse ALIF classifier (700 inputs -> N hidden -> 20 readouts,
+its own ragged matrices, connectivity and Philox seeds) training with one trial per
+iteration and DEEP R after every trial.  Instances differ in hidden size and trial
+length, so no two share a kernel launch; two execution forms use the same kernels:
+
+* plain:   one instance after another on one stream, one `snn_step_neurons` launch per
+           simulated step, then the gradient, Adam and DEEP R calls; no graph.
+* batched: the whole iteration of every instance — state reset, the full trial in one
+           forward launch, gradient, Adam, DEEP R — captured once in a CUDA graph over
+           several streams and replayed.  Everything that changes between iterations
+           (trial id, label, Adam's beta powers, the DEEP R rewiring index) lives in
+           device memory and is advanced by the graph itself.
+
+Results are identical in both forms (integer spike accumulation; same kernels and
+order per instance), which tests/test_gpu_sched.py checks bit for bit.
+
+The row schedule of the forward (warps sharing one trial's spiking rows) is picked per
+(hidden size, mean row length, spike rate) class by `Autotuner`, which times the
+candidate schedules on a sample trial of a representative instance.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import abi, net
+
+N_IN, K_OUT, N_CLASSES, N_BINS = 700, 20, 20, 10
+
+
+@dataclass
+class InstanceSpec:
+    N: int
+    T: int
+    p: float
+    seed: int
+
+
+def batched_specs(n: int = 64, seed: int = 0) -> list[InstanceSpec]:
+    """Hidden sizes uniform over {256, 512, 1024, 2048}, trial lengths uniform in
+    [200, 1000], connectivity uniform in [5 %, 20 %]."""
+    rng = np.random.default_rng([seed, 0x5C4E])
+    out = []
+    for i in range(n):
+        out.append(InstanceSpec(int(rng.choice([256, 512, 1024, 2048])), int(rng.integers(200, 1001)),
+                                float(rng.uniform(0.05, 0.20)), seed * 1000 + i))
+    return out
+
+
+class Instance:
+    """One classifier with its training state and device-resident iteration counters."""
+
+    def __init__(self, spec: InstanceSpec, task, device="cuda", lr: float = 1e-3, l1: float = 1e-5):
+        import synth
+        self.spec = spec
+        N, T, p, sd = spec.N, spec.T, spec.p, spec.seed
+        in_rag = synth.random_ragged(sd * 7 + 1, N_IN, N, p)
+        rec_rag = synth.random_ragged(sd * 7 + 2, N, N, p, no_autapse=True)
+        W_out, b = synth.dense_readout(sd * 7 + 3, K_OUT, N)
+        F32 = abi.SNN_F32
+        self.d_in = net.DeviceRagged(in_rag.row_len, in_rag.ind, in_rag.w, N, dtype=F32, adam=True, grad=True,
+                                     deepr=True, seed=sd * 7 + 4, device=device)
+        self.d_rec = net.DeviceRagged(rec_rag.row_len, rec_rag.ind, rec_rag.w, N, dtype=F32, no_autapse=True,
+                                      adam=True, grad=True, deepr=True, seed=sd * 7 + 5, device=device)
+        self.cls = net.DeviceClassifier(N_IN, N, K_OUT, self.d_in, self.d_rec, W_out, b, task.thr, sd * 7 + 6,
+                                        net.NeuronCfg(), max_B=1, max_T=T, dtype=F32, device=device)
+        rng = np.random.default_rng([sd, 0xB1])
+        self.bin_table = torch.as_tensor(
+            np.maximum(1, np.rint(rng.uniform(0.8, 1.2, 64) * T / N_BINS)).astype(np.int32), device=device)
+        self.batch = net.DeviceBatch(self.cls, [0], [int(self.bin_table[0])], [0], T, device=device)
+        self.step = torch.zeros(1, dtype=torch.int64, device=device)          # iterations done
+        self.betas = torch.tensor([0.9, 0.999], dtype=torch.float64, device=device)
+        self.bias = torch.ones(2, dtype=torch.float64, device=device)         # beta^t after the update
+        self.stats = torch.zeros((2, 4), dtype=torch.int64, device=device)
+        self.adam = net.adam_params(lr, 1, l1=l1, bias_dev=self.bias)
+        self.lr, self.l1 = lr, l1
+        self.events = 0
+
+    def _prologue(self):
+        """Device-side bookkeeping of one iteration: trial id = iteration index, label and
+        time warp from it, Adam's beta powers advanced, state reset."""
+        bt = self.batch
+        bt.trial_ids.copy_(self.step)
+        bt.labels.copy_((self.step % N_CLASSES).to(torch.int32))
+        bt.bin_len.copy_(self.bin_table.index_select(0, self.step % self.bin_table.numel()))
+        self.bias.mul_(self.betas)
+        for t in (bt.v, bt.a, bt.y, bt.ysum, bt.x_bits, bt.z_bits):
+            t.zero_()
+
+    def enqueue(self, stream, per_step: bool = False):
+        """Launch one training iteration on `stream` (torch stream)."""
+        with torch.cuda.stream(stream):
+            self._prologue()
+        h, bt = self.cls.handle, self.batch.desc
+        if per_step:
+            for t in range(self.spec.T):
+                abi.snn_step_neurons(h, bt, t, 1, stream)
+        else:
+            abi.snn_step_neurons(h, bt, 0, self.spec.T, stream)
+        abi.snn_eprop_update(h, bt, abi.SNN_EPROP_GRAD, None, stream)
+        abi.snn_eprop_update(h, bt, abi.SNN_EPROP_APPLY, self.adam, stream)
+        abi.snn_rewire_deepr_dev(self.d_in.handle, self.step, self.stats[0], stream)
+        abi.snn_rewire_deepr_dev(self.d_rec.handle, self.step, self.stats[1], stream)
+        with torch.cuda.stream(stream):
+            self.step.add_(1)
+
+    def snapshot(self) -> dict:
+        out = {}
+        for name, d in (("in", self.d_in), ("rec", self.d_rec)):
+            h = d.host()
+            out[name] = {k: h[k] for k in ("row_len", "ind", "w", "conn_bits")}
+        out["W_out"] = self.cls.W_out.cpu().numpy()
+        out["ysum"] = self.batch.ysum.cpu().numpy()
+        return out
+
+
+class PlainRunner:
+    """One instance at a time, per-step launches, one stream, no graph."""
+
+    def __init__(self, instances, stream=None):
+        self.instances = instances
+        self.stream = stream or torch.cuda.current_stream()
+
+    def iterate(self):
+        for inst in self.instances:
+            inst.enqueue(self.stream, per_step=True)
+
+
+class BatchedRunner:
+    """All instances' iterations captured in one CUDA graph over `n_streams` streams."""
+
+    def __init__(self, instances, n_streams: int = 16):
+        self.instances = instances
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.graph = None
+
+    def capture(self):
+        main = torch.cuda.Stream()
+        # warm-up outside capture: first calls set kernel attributes and build tables
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=main):
+            for s in self.streams:
+                s.wait_stream(main)
+            for i, inst in enumerate(self.instances):
+                inst.enqueue(self.streams[i % len(self.streams)])
+            for s in self.streams:
+                main.wait_stream(s)
+        self.graph = g
+
+    def iterate(self):
+        self.graph.replay()
+
+
+class Autotuner:
+    """Row-schedule table keyed on (hidden size, mean row length, spike rate): for each
+    class, time the forward of a representative instance's trial with every admissible
+    warps-per-trial choice and keep the fastest."""
+
+    CANDIDATES = (4, 8, 16)
+
+    def __init__(self):
+        self.table: dict[tuple, int] = {}
+        self.timings: dict[tuple, dict] = {}
+
+    @staticmethod
+    def key(inst: Instance, spike_rate: float) -> tuple:
+        mean_len = float(inst.d_in.row_len.float().mean() + inst.d_rec.row_len.float().mean()) / 2
+        return (inst.spec.N, int(round(math.log2(max(mean_len, 1.0)))), int(round(math.log2(max(spike_rate, 1e-4)))))
+
+    @staticmethod
+    def spike_rate(inst: Instance) -> float:
+        z = net.spikes_from_bits(inst.batch.z_rec[0].cpu().numpy().view(np.uint32), inst.spec.N)
+        return float(z.mean())
+
+    def _time(self, inst: Instance, warps: int, reps: int = 3) -> float:
+        abi.snn_classifier_set_schedule(inst.cls.handle, warps)
+        s = torch.cuda.current_stream()
+        best = float("inf")
+        for _ in range(reps):
+            for t in (inst.batch.v, inst.batch.a, inst.batch.y, inst.batch.ysum, inst.batch.x_bits,
+                      inst.batch.z_bits):
+                t.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            abi.snn_step_neurons(inst.cls.handle, inst.batch.desc, 0, inst.spec.T, s)
+            b.record(s)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    def tune(self, instances) -> dict:
+        for inst in instances:
+            # a sample trial at the default schedule gives the spike rate of the class
+            abi.snn_classifier_set_schedule(inst.cls.handle, 8)
+            self._time(inst, 8, reps=1)
+            k = self.key(inst, self.spike_rate(inst))
+            if k not in self.table:
+                times = {w: self._time(inst, w) for w in self.CANDIDATES if inst.spec.N <= 8 * 32 * w}
+                self.table[k] = min(times, key=times.get)
+                self.timings[k] = times
+            abi.snn_classifier_set_schedule(inst.cls.handle, self.table[k])
+        return self.table

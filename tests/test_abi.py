@@ -38,7 +38,7 @@ def test_binding_covers_every_declared_symbol(lib_path):
     from paper_2510_19764_gb300 import abi
     assert sorted(abi.EXPORTED) == _declared_symbols()
     lib = abi.load()
-    assert lib.snn_abi_version() == 1
+    assert lib.snn_abi_version() == 3
     for name in abi.EXPORTED:
         assert callable(getattr(abi, name)), name
 
@@ -59,9 +59,9 @@ def test_struct_layouts_match_header():
     from paper_2510_19764_gb300 import abi
     assert ctypes.sizeof(abi.RaggedDesc) == 24 + 8 * 8 + 8
     assert ctypes.sizeof(abi.RewireStats) == 32
-    assert ctypes.sizeof(abi.Adam) == 56
+    assert ctypes.sizeof(abi.Adam) == 64
     assert ctypes.sizeof(abi.ClassifierDesc) == 168
-    assert ctypes.sizeof(abi.Batch) == 8 + 18 * 8
+    assert ctypes.sizeof(abi.Batch) == 8 + 19 * 8
     assert ctypes.sizeof(abi.TopoParams) == 24 + 15 * 8
     assert ctypes.sizeof(abi.TopoRewire) == 6 * 8 + 8
     assert ctypes.sizeof(abi.TopoState) == 10 * 8

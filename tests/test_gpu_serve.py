@@ -1,0 +1,48 @@
+"""Serving loop: every request's result is identical served alone (one at a time) and
+served in the mix (continuous batching across models, overlapping launches), including
+fine-tuning jobs on private weight copies."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2510_19764_gb300 import abi, build
+    build.build()
+    abi.load()
+
+
+def test_results_identical_alone_and_in_the_mix():
+    from paper_2510_19764_gb300 import serve
+    task = synth.spoken_digit_task(5, n_in=serve.N_IN, n_classes=serve.N_CLASSES, T=serve.T_MAX, n_bins=serve.N_BINS)
+    models = [serve.Model(0, 64, task, max_batch=8), serve.Model(1, 160, task, max_batch=8),
+              serve.Model(2, 96, task, max_batch=8)]
+    reqs = serve.poisson_requests(48, 1000.0, len(models), seed=3, finetune_frac=0.15, t_range=(20, 120))
+    assert any(r.finetune for r in reqs)
+    eng = serve.Engine(models, max_batch=8, slots_per_model=2, n_streams=4)
+    mixed = eng.run(reqs, realtime=False)
+    torch.cuda.synchronize()
+    assert eng.stats["max_batch_seen"] > 1 and eng.stats["max_in_flight"] > 1
+    alone = serve.Engine(models, max_batch=8, slots_per_model=1, n_streams=1).run_plain(reqs, realtime=False)
+    assert [r.rid for r in mixed] == [r.rid for r in alone] == list(range(len(reqs)))
+    for a, b in zip(mixed, alone):
+        np.testing.assert_array_equal(a.ysum, b.ysum)
+        assert a.pred == b.pred
+    assert all(np.abs(r.ysum).sum() > 0 for r in mixed)
+
+
+def test_realtime_loop_reports_latency():
+    from paper_2510_19764_gb300 import serve
+    task = synth.spoken_digit_task(5, n_in=serve.N_IN, n_classes=serve.N_CLASSES, T=serve.T_MAX, n_bins=serve.N_BINS)
+    models = [serve.Model(0, 128, task, max_batch=16)]
+    reqs = serve.poisson_requests(60, 2000.0, 1, seed=4, finetune_frac=0.0, t_range=(50, 200))
+    eng = serve.Engine(models, max_batch=16)
+    t0 = torch.cuda.Event(enable_timing=True)
+    res = eng.run(reqs, realtime=True)
+    s = serve.latency_summary(res, max(r.latency for r in res) + reqs[-1].arrival)
+    assert s["requests"] == 60 and 0 < s["p50_ms"] <= s["p99_ms"]
