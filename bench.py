@@ -48,6 +48,8 @@ def parse():
                     help="classifier (default, the benchmark line); batched: 64 uneven instances, plain vs "
                          "graph-batched; serve: request loop latency; topo: topographic map steps/s")
     ap.add_argument("--scale", type=int, default=2, help="topo: grid side 16*scale")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 4, 8, 16],
+                    help="forward row schedule (warps per trial); 0 = the library default")
     ap.add_argument("--topo-steps", type=int, default=10000)
     return ap.parse_args()
 
@@ -190,6 +192,8 @@ def run_ours(args, world, rank, local):
     h_desc = [(torch.as_tensor(tb.labels).pin_memory(), torch.as_tensor(tb.bin_len).pin_memory(),
                torch.as_tensor(tb.trial_ids).pin_memory()) for tb in batches]
     batch = net.DeviceBatch(cls, batches[0].labels, batches[0].bin_len, batches[0].trial_ids, T, device=dev)
+    if args.schedule:
+        abi.snn_classifier_set_schedule(cls.handle, args.schedule)
     stream = torch.cuda.current_stream()
     stats = torch.zeros((2, 4), dtype=torch.int64, device=dev)
     lr, l1 = 1e-3, 1e-5

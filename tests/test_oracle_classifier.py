@@ -255,3 +255,27 @@ def test_poisson_time_warp_bins():
     thr = synth.rates_to_thresholds(rates, 1.0)
     fired = [oc.poisson_input(thr, 0, 7, 0, t, 1).all() for t in range(40)]
     assert fired == [14 <= t < 21 for t in range(40)]
+
+
+def test_eprop_synapse_vectorised_over_trials_equals_trace_form():
+    """The per-synapse trace recursion vectorised over trials (used for full-size sampled
+    parity) gives the same sums as eprop_gradients slot by slot."""
+    n_in, N, K, T, B = 12, 9, 3, 60, 4
+    p = oc.NeuronParams(tau_m=20.0, v_thr=0.6, beta=0.3, tau_a=100.0)
+    in_rag = synth.random_ragged(4, n_in, N, 0.5, w_std=0.4)
+    in_rag.w = np.where(in_rag.ind >= 0, in_rag.w + 0.15, 0.0)
+    rec_rag = synth.random_ragged(5, N, N, 0.4, no_autapse=True, w_std=0.3)
+    rng = np.random.default_rng(8)
+    net = _net(n_in, N, K, in_rag, rec_rag, rng.normal(0, 0.5, (K, N)), np.zeros(K), p)
+    thr = synth.rates_to_thresholds(rng.uniform(50, 250, (K, 1, n_in)), 1.0)
+    recs = [oc.forward_trial(net, thr, b % K, T, b, 77, T) for b in range(B)]
+    G_in = sum(oc.eprop_gradients(net, r["x"], r["z"], r["psi"], r["d"])[0] for r in recs)
+    G_rec = sum(oc.eprop_gradients(net, r["x"], r["z"], r["psi"], r["d"])[1] for r in recs)
+    for G, rag, key in ((G_in, in_rag, "x"), (G_rec, rec_rag, "z")):
+        for i in range(rag.P):
+            for s in range(rag.row_len[i]):
+                j = rag.ind[i, s]
+                pre = np.array([r[key][:, i] for r in recs])
+                psi = np.array([r["psi"][:, j] for r in recs])
+                L = np.array([r["d"] @ net.W_out[:, j] for r in recs])
+                np.testing.assert_allclose(oc.eprop_synapse(pre, psi, L, p), G[i, s], rtol=1e-12, atol=1e-13)
