@@ -74,6 +74,9 @@ struct InputParams {
 __device__ __forceinline__ float exp_real(float x) { return expf(x); }
 __device__ __forceinline__ double exp_real(double x) { return exp(x); }
 
+// Signed value of the low 52 bits of a packed accumulator (see k_pack).
+__device__ __forceinline__ long long sext52(long long a) { return (long long)((unsigned long long)a << 12) >> 12; }
+
 // Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
 // only, so they are drawn ahead of the sequential simulation.  Thread = 4 channels (one
 // Philox block); the nibbles of 8 consecutive threads form one 32-channel word.
@@ -122,8 +125,10 @@ __global__ void k_input(InputParams p) {
 // spikes of step t (drawn ahead of time by k_input) are listed by warp 0.  Per step t:
 //  (A) warps take every nwarps-th row of the lists of step t-1, two rows at a time; each
 //      slot is one packed 64-bit load (target index | fixed-point weight) and one
-//      branch-free shared-memory atomic (invalid lanes add 0 to their own spare
-//      accumulator); hidden rows also add their readout column.  The last warp
+//      shared-memory atomic of that whole word (padding slots of a row's last chunk add
+//      0 to per-lane spare accumulators); hidden rows also add their readout column.
+//      Phase B reads the low 52 bits of each accumulator sign-extended, which is the
+//      exact weight sum while it stays below 2^11 in magnitude.  The last warp
 //      meanwhile finishes the readout of step t-1 (leak, softmax, d record).
 //  (B) each thread updates its NPT neurons (state in registers) and writes psi.
 template <typename real, int NPT, int TH>
@@ -235,21 +240,17 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             const long long oB = roB ? p.out_wf[(size_t)lane * N + iB] : 0ll;
             const int nmax = nA > nB ? nA : nB;
             for (int s0 = 0; s0 < nmax; s0 += 128) {
-                long long wA[4], wB[4];
+                unsigned long long wA[4], wB[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int sl = s0 + q * 32 + lane;
-                    wA[q] = pkA[sl < nA ? sl : 0];
-                    wB[q] = pkB[sl < nB ? sl : 0];
+                    // warp-uniform chunk tests; chunk slots past the length are padding
+                    wA[q] = s0 + q * 32 < nA ? (unsigned long long)pkA[s0 + q * 32 + lane] : 0ull;
+                    wB[q] = s0 + q * 32 < nB ? (unsigned long long)pkB[s0 + q * 32 + lane] : 0ull;
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int sl = s0 + q * 32 + lane;
-                    const bool okA = sl < nA, okB = sl < nB;
-                    atomicAdd(acc + (okA ? (int)((unsigned long long)wA[q] >> 52) : N + lane),
-                              okA ? (unsigned long long)((wA[q] << 12) >> 12) : 0ull);
-                    atomicAdd(acc + (okB ? (int)((unsigned long long)wB[q] >> 52) : N + lane),
-                              okB ? (unsigned long long)((wB[q] << 12) >> 12) : 0ull);
+                    if (s0 + q * 32 < nA) atomicAdd(acc + (unsigned)(wA[q] >> 52), wA[q]);
+                    if (s0 + q * 32 < nB) atomicAdd(acc + (unsigned)(wB[q] >> 52), wB[q]);
                 }
             }
             if (roA) atomicAdd(yacc + lane, (unsigned long long)oA);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
         for (int q = 0; q < NPT; ++q) {
             const int j = tid + q * TH;
             if (j < N) {
-                const real I = from_fixed<real>(Iacc[j]);
+                const real I = from_fixed<real>(sext52(Iacc[j]));
                 Iacc[j] = 0;
                 const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
                 const real v = p.alpha * (zp ? vr[q] - p.v_thr : vr[q]) + I;
@@ -325,13 +326,21 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
 
 // Packed forward shadow of a ragged matrix: bits 63..52 target index, bits 51..0 the
 // weight in fixed point (40 fractional bits, two's complement), one 64-bit load per slot.
+// The forward adds the whole packed word to the target's accumulator: the low 52 bits
+// of the sum are the weight sum modulo 2^52 (read back sign-extended), the index bits
+// only pile up above them.  Slots past the row length (up to the capacity C, a multiple
+// of 32) hold weight 0 aimed at accumulator spare + (slot mod 32), so a warp can add a
+// whole 32-slot chunk with no per-lane test and no two lanes on one address.
 template <typename real>
 __global__ void k_pack(const real* __restrict__ w, const int32_t* __restrict__ ind, const int32_t* __restrict__ len,
-                       int C, long long* __restrict__ pk, long long n) {
+                       int C, int spare, long long* __restrict__ pk, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int row = (int)(i / C), s = (int)(i % C);
-    if (s >= len[row]) return;
+    if (s >= len[row]) {
+        pk[i] = (long long)((unsigned long long)(unsigned)(spare + (s & 31)) << 52);
+        return;
+    }
     const long long f = to_fixed(w[i]) & ((1ll << 52) - 1);
     pk[i] = (long long)(((unsigned long long)(unsigned)ind[i] << 52) | (unsigned long long)f);
 }
@@ -353,94 +362,137 @@ __global__ void k_reduce_gb(const real* __restrict__ gb_part, real* __restrict__
     G_b[k] = s;
 }
 
-// The reverse-time scans.  CTA = (trial, 128 hidden neurons); steps are walked
-// backwards in chunks of BWD_TCH.  Per chunk the psi tile [BWD_TCH][128] and the
-// readout error d are staged in shared memory; warp 0 extends the filtered readout error
-//   D_k^t = d_k^{t+1} + alpha D_k^{t+1}   (D^{T-1} = 0)
-// through the chunk (the x == 0 CTA of each trial also stores D and sum_t d_k^t for the
-// readout gradients), then every thread runs its neuron's adjoint recurrences
-//   lam = sum_k W_out[k][j] D_k, mu, h, delta   over the chunk from shared memory.
+// Filtered readout error D_k^t = d_k^{t+1} + alpha D_k^{t+1} (D^{T-1} = 0), i.e.
+// D_k^t = sum_{u > t} alpha^{u-t-1} d_k^u, and the bias gradient partial sum_t d_k^t.
+// One warp per (trial, readout): lane L scans steps [L S, (L+1) S) backwards with a zero
+// carry, then the carries D^{(L+1) S} are chained across lanes from the last lane down
+// (D^t = local^t + alpha^{(L+1) S - t} carry_L).
+template <typename real>
+__global__ void k_readout_scan(const real* __restrict__ d, real* __restrict__ Dout, real* __restrict__ gb_part,
+                               int B, int T, int K, int Kp, real alpha) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (w >= B * Kp) return;
+    const int b = w / Kp, k = w % Kp;
+    const int S = (T + 31) / 32;
+    const int s0 = lane * S, s1 = min(T, s0 + S);
+    const real* db = d + (size_t)b * T * K;
+    real* Db = Dout + (size_t)b * T * Kp;
+    if (k >= K) {
+        for (int t = s0; t < s1; ++t) Db[(size_t)t * Kp + k] = real(0);
+        return;
+    }
+    // local backward scan with zero carry: E^t = d^{t+1} + alpha E^{t+1} inside the chunk
+    real E = 0, gsum = 0, apow = 1;   // apow = alpha^{s1 - s0} at the end
+    for (int t = s1 - 1; t >= s0; --t) {
+        const real dn = (t + 1 < T) ? db[(size_t)(t + 1) * K + k] : real(0);
+        E = (t == T - 1) ? real(0) : dn + alpha * E;
+        gsum += db[(size_t)t * K + k];
+        apow *= alpha;
+    }
+    const real E0 = E;                       // E at the chunk's first step s0
+    // carry_L = D^{s1}: chain from the last lane: D^{s0 of lane L} = E0_L + alpha^{len_L} carry_L
+    real carry = 0;
+    for (int L = 30; L >= 0; --L) {
+        const real e0_next = __shfl_sync(0xffffffffu, E0, L + 1);
+        const real ap_next = __shfl_sync(0xffffffffu, apow, L + 1);
+        const real c_next = __shfl_sync(0xffffffffu, carry, L + 1);
+        if (lane == L) carry = e0_next + ap_next * c_next;
+    }
+    // final values: D^t = E^t + alpha^{s1 - t} carry
+    real Dt = 0, ap = alpha;
+    for (int t = s1 - 1; t >= s0; --t) {
+        const real dn = (t + 1 < T) ? db[(size_t)(t + 1) * K + k] : real(0);
+        Dt = (t == T - 1) ? real(0) : dn + alpha * Dt;
+        Db[(size_t)t * Kp + k] = (t == T - 1) ? real(0) : Dt + ap * carry;
+        ap *= alpha;
+    }
+    gsum = warp_sum(gsum);
+    if (lane == 0) gb_part[(size_t)b * K + k] = gsum;
+}
+
+// The adjoint scan.  CTA = (trial, BWD_THREADS hidden neurons); steps are walked backwards
+// in chunks of BWD_TCH.  Each thread prefetches its neuron's psi for the next chunk into
+// registers while it runs the current chunk; the chunk's filtered readout error D
+// [BWD_TCH][KP] is double-buffered in shared memory (one barrier per chunk).  Per step:
+//   lam = sum_k W_out[k][j] D_k,  mu = beta lam' psi' + (rho - beta psi') mu',
+//   h = psi (lam - mu),  delta = h' + alpha delta'   (primes: step t+1; zero after T-1).
 constexpr int BWD_THREADS = 128;
 constexpr int BWD_TCH = 32;
 
 template <typename real, int KV>
 __global__ void __launch_bounds__(BWD_THREADS)
-    k_backward(const real* __restrict__ psi, const real* __restrict__ d, const real* __restrict__ W_out,
-               real* __restrict__ delta, real* __restrict__ Dout, real* __restrict__ gb_part, int T, int N, int K,
-               real alpha, real rho, real beta) {
+    k_backward(const real* __restrict__ psi, const real* __restrict__ Dg, const real* __restrict__ W_out,
+               real* __restrict__ delta, int T, int N, int K, real alpha, real rho, real beta) {
     constexpr int KP = 4 * KV;
-    __shared__ real ps_s[BWD_TCH][BWD_THREADS];
-    __shared__ __align__(16) real D_s[BWD_TCH][KP];
-    __shared__ real d_s[BWD_TCH + 1][KP];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int j0 = blockIdx.x * BWD_THREADS;
-    const int j = j0 + tid;
+    __shared__ __align__(16) real D_s[2][BWD_TCH][KP];
+    const int tid = threadIdx.x;
+    const int j = blockIdx.x * BWD_THREADS + tid;
     const int b = blockIdx.y;
-    const bool writer = blockIdx.x == 0;
+    const bool ok = j < N;
     real wc[KP];
 #pragma unroll
-    for (int k = 0; k < KP; ++k) wc[k] = (k < K && j < N) ? W_out[(size_t)k * N + j] : real(0);
-    real lam_next = 0, psi_next = 0, mu = 0, h_next = 0, dl = 0;
-    real Dk = 0, gsum = 0;
+    for (int k = 0; k < KP; ++k) wc[k] = (k < K && ok) ? W_out[(size_t)k * N + j] : real(0);
+    const real* pb = psi + (size_t)b * T * N + (ok ? j : 0);
+    const real* Db = Dg + (size_t)b * T * KP;
+    real* db = delta + (size_t)b * T * N + (ok ? j : 0);
     const int n_chunks = (T + BWD_TCH - 1) / BWD_TCH;
-    for (int ch = n_chunks - 1; ch >= 0; --ch) {
-        const int tb = ch * BWD_TCH;
-        const int nt = min(BWD_TCH, T - tb);
-        __syncthreads();
-        for (int idx = tid; idx < nt * BWD_THREADS; idx += BWD_THREADS) {
-            const int r = idx / BWD_THREADS, c = idx % BWD_THREADS;
-            ps_s[r][c] = (j0 + c < N) ? psi[((size_t)b * T + tb + r) * N + j0 + c] : real(0);
-        }
-        // d rows tb .. tb + nt (one past the chunk, for d^{t+1})
-        for (int idx = tid; idx < (nt + 1) * KP; idx += BWD_THREADS) {
-            const int r = idx / KP, k = idx % KP;
-            const int t = tb + r;
-            d_s[r][k] = (k < K && t < T) ? d[((size_t)b * T + t) * K + k] : real(0);
-        }
-        __syncthreads();
-        if (warp == 0 && lane < KP) {
-            for (int r = nt - 1; r >= 0; --r) {
-                const int t = tb + r;
-                Dk = (t == T - 1 || lane >= K) ? real(0) : d_s[r + 1][lane] + alpha * Dk;
-                D_s[r][lane] = Dk;
-                gsum += d_s[r][lane];
-                if (writer) Dout[((size_t)b * T + t) * KP + lane] = Dk;
-            }
-        }
-        __syncthreads();
-        for (int r = nt - 1; r >= 0; --r) {
-            const int t = tb + r;
-            const real ps = ps_s[r][tid];
-            real lam = 0;
+    real pcur[BWD_TCH], pnext[BWD_TCH];
+    auto load_chunk = [&](int ch, real (&dst)[BWD_TCH], int buf) {
+        const int tb = ch * BWD_TCH, nt = min(BWD_TCH, T - tb);
 #pragma unroll
-            for (int k = 0; k < KP; ++k) lam += wc[k] * D_s[r][k];
-            if (t == T - 1) {
-                mu = 0;
-                dl = 0;
-            } else {
-                mu = beta * lam_next * psi_next + (rho - beta * psi_next) * mu;
-                dl = h_next + alpha * dl;
+        for (int r = 0; r < BWD_TCH; ++r) dst[r] = (r < nt && ok) ? pb[(size_t)(tb + r) * N] : real(0);
+        for (int idx = tid; idx < nt * KP; idx += BWD_THREADS) D_s[buf][idx / KP][idx % KP] = Db[(size_t)tb * KP + idx];
+    };
+    load_chunk(n_chunks - 1, pcur, (n_chunks - 1) & 1);
+    __syncthreads();
+    real lam_next = 0, psi_next = 0, mu = 0, h_next = 0, dl = 0;
+    for (int ch = n_chunks - 1; ch >= 0; --ch) {
+        const int tb = ch * BWD_TCH, nt = min(BWD_TCH, T - tb);
+        const int buf = ch & 1;
+        if (ch > 0) load_chunk(ch - 1, pnext, buf ^ 1);
+#pragma unroll
+        for (int r = BWD_TCH - 1; r >= 0; --r) {
+            if (r < nt) {
+                const int t = tb + r;
+                const real ps = pcur[r];
+                real lam = 0;
+#pragma unroll
+                for (int k = 0; k < KP; ++k) lam += wc[k] * D_s[buf][r][k];
+                if (t == T - 1) {
+                    mu = 0;
+                    dl = 0;
+                } else {
+                    mu = beta * lam_next * psi_next + (rho - beta * psi_next) * mu;
+                    dl = h_next + alpha * dl;
+                }
+                const real h = ps * (lam - mu);
+                if (ok) db[(size_t)t * N] = dl;
+                h_next = h;
+                lam_next = lam;
+                psi_next = ps;
             }
-            const real h = ps * (lam - mu);
-            if (j < N) delta[((size_t)b * T + t) * N + j] = dl;
-            h_next = h;
-            lam_next = lam;
-            psi_next = ps;
         }
+#pragma unroll
+        for (int r = 0; r < BWD_TCH; ++r) pcur[r] = pnext[r];
+        __syncthreads();
     }
-    if (writer && warp == 0 && lane < K) gb_part[(size_t)b * K + lane] = gsum;
 }
 
-// Gather: grid (spike-word columns, KS).  CTA = the 32 presynaptic rows of one bit word
-// (input words first, then hidden words), one warp per row.  The CTA stages the words of
-// its whole (trial, step) range in shared memory, then each warp ballots its bit over
-// them and, two spikes at a time, sums delta at its row's targets (hidden rows also sum
-// D into the readout gradient).
-constexpr int GATHER_THREADS = 1024;
+// Gather: grid (spike-word columns x 32 / ROWS, KS, slot groups).  CTA = ROWS presynaptic
+// rows of one bit word (input words first, then hidden words) for one group of 128 slots;
+// one warp per row, 4 slot chunks per lane.  The CTA stages the spike words of its whole
+// (trial, step) range in shared memory; each warp walks its bit through them with
+// ballots, collects EV spike times (across as many 32-step windows as it takes) and then
+// issues their delta loads together, so a sparse row still keeps 4 EV loads in flight
+// per lane.  The group-0 warps of hidden rows also sum D into the
+// readout gradient.  CTAs whose rows all end before their group exit before staging.
 constexpr int GATHER_SPAN = 8192;
+constexpr int GATHER_ROWS = 32;   // rows (warps) per CTA: 32 or 16
+constexpr int GATHER_EV = 4;      // spike events whose loads are issued together
 
-template <typename real, int MAXCH>
-__global__ void __launch_bounds__(GATHER_THREADS)
+template <typename real, int ROWS, int EV>
+__global__ void __launch_bounds__(ROWS * 32, 1)
     k_gather(const uint32_t* __restrict__ x_rec, const uint32_t* __restrict__ z_rec, int Win, int Wh,
              const int32_t* __restrict__ in_len, const int32_t* __restrict__ in_ind, int in_C, int n_in,
              const int32_t* __restrict__ rec_len, const int32_t* __restrict__ rec_ind, int rec_C, int N,
@@ -449,64 +501,95 @@ __global__ void __launch_bounds__(GATHER_THREADS)
              real* __restrict__ part_out) {
     __shared__ uint32_t words[GATHER_SPAN];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    const int col = blockIdx.x;
+    constexpr int SPLIT = 32 / ROWS;
+    const int col = blockIdx.x / SPLIT;
+    const int r0 = (blockIdx.x % SPLIT) * ROWS;    // first row of the word this CTA owns
     const int ks = blockIdx.y;
+    const int g = blockIdx.z;                       // slot group: slots [128 g, 128 g + 128)
     const bool is_in = col < Win;
     const int wi = is_in ? col : col - Win;
-    const int i = wi * 32 + warp;
+    const int i = wi * 32 + r0 + warp;
     const int P = is_in ? n_in : N;
     const bool row_ok = i < P;
+    const int len = row_ok ? (is_in ? in_len[i] : rec_len[i]) : 0;
+    const int s_base = 128 * g;
+    const bool readout = !is_in && g == 0;
+    const bool active = row_ok && (len > s_base || readout);
+    if (!__syncthreads_or(active)) return;
     const uint32_t* bits = is_in ? x_rec : z_rec;
     const int W = is_in ? Win : Wh;
     const int C = is_in ? in_C : rec_C;
     const long long bt0 = (long long)ks * bt_per;
     const long long bt1 = min(BT, bt0 + bt_per);
-    for (int k = threadIdx.x; k < GATHER_SPAN; k += GATHER_THREADS) {
+    for (int k = threadIdx.x; k < GATHER_SPAN; k += ROWS * 32) {
         const long long my = bt0 + k;
         words[k] = (my < bt1) ? bits[my * W + wi] : 0u;
     }
-    const int len = row_ok ? (is_in ? in_len[i] : rec_len[i]) : 0;
     const int32_t* ri = (is_in ? in_ind : rec_ind) + (size_t)(row_ok ? i : 0) * C;
-    int tgt[MAXCH];
-    real acc[MAXCH];
+    const int nq = len > s_base ? min(4, (len - s_base + 31) >> 5) : 0;   // warp-uniform
+    int tgt[4];
+    real acc[4];
 #pragma unroll
-    for (int c = 0; c < MAXCH; ++c) {
-        const int s = c * 32 + lane;
-        tgt[c] = (s < len) ? ri[s] : -1;
-        acc[c] = 0;
+    for (int q = 0; q < 4; ++q) {
+        const int s = s_base + q * 32 + lane;
+        tgt[q] = (q < nq && s < len) ? ri[s] : -1;
+        acc[q] = 0;
     }
     real acc_o = 0;
-    const bool do_out = !is_in && row_ok && lane < K;
-    const uint32_t bit = 1u << warp;
+    const bool do_out = readout && row_ok && lane < K;
+    const uint32_t bit = 1u << (r0 + warp);
     __syncthreads();
-    if (!row_ok) return;
+    if (!active) return;
     const int span = bt1 > bt0 ? (int)(bt1 - bt0) : 0;
-    for (int sub = 0; sub < span; sub += 32) {
-        uint32_t spk = __ballot_sync(0xffffffffu, (words[sub + lane] & bit) != 0u);
-        while (spk) {
-            const long long e0 = bt0 + sub + __ffs(spk) - 1;
-            spk &= spk - 1u;
-            const bool two = spk != 0u;
-            const long long e1 = two ? bt0 + sub + __ffs(spk) - 1 : e0;
-            if (two) spk &= spk - 1u;
-            const real* d0 = delta + e0 * N;
-            const real* d1 = delta + e1 * N;
-            real v0[MAXCH], v1[MAXCH];
+    const real* delta0 = delta + bt0 * N;
+    const real* D0 = D + bt0 * Kp;
+    int sub = 0, wbase = 0;
+    uint32_t spk = 0u;                               // warp-uniform (a ballot)
+    for (;;) {
+        int off[EV];
+        int nv = 0;
 #pragma unroll
-            for (int c = 0; c < MAXCH; ++c) {
-                v0[c] = tgt[c] >= 0 ? d0[tgt[c]] : real(0);
-                v1[c] = (two && tgt[c] >= 0) ? d1[tgt[c]] : real(0);
+        for (int k = 0; k < EV; ++k) {
+            while (spk == 0u && sub < span) {
+                spk = __ballot_sync(0xffffffffu, (words[sub + lane] & bit) != 0u);
+                wbase = sub;
+                sub += 32;
             }
+            off[k] = wbase + (spk ? __ffs(spk) - 1 : 0);
+            if (spk) {
+                spk &= spk - 1u;
+                ++nv;
+            }
+        }
+        if (nv == 0) break;
+        real v[EV][4];
 #pragma unroll
-            for (int c = 0; c < MAXCH; ++c) acc[c] += v0[c] + v1[c];
-            if (do_out) acc_o += D[e0 * Kp + lane] + (two ? D[e1 * Kp + lane] : real(0));
+        for (int k = 0; k < EV; ++k) {
+            const real* rowp = delta0 + (size_t)off[k] * N;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[k][q] = (k < nv && q < nq && tgt[q] >= 0) ? rowp[tgt[q]] : real(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            real s = 0;
+#pragma unroll
+            for (int k = 0; k < EV; k += 4) s += (v[k][q] + v[k + 1][q]) + (v[k + 2][q] + v[k + 3][q]);
+            acc[q] += s;
+        }
+        if (do_out) {
+            real o = 0;
+#pragma unroll
+            for (int k = 0; k < EV; ++k)
+                if (k < nv) o += D0[(size_t)off[k] * Kp + lane];
+            acc_o += o;
         }
     }
     real* part = is_in ? part_in : part_rec;
 #pragma unroll
-    for (int c = 0; c < MAXCH; ++c) {
-        const int s = c * 32 + lane;
-        if (s < len) part[((size_t)ks * P + i) * C + s] = acc[c];
+    for (int q = 0; q < 4; ++q) {
+        const int s = s_base + q * 32 + lane;
+        if (q < nq && s < len) part[((size_t)ks * P + i) * C + s] = acc[q];
     }
     if (do_out) part_out[((size_t)ks * N + i) * K + lane] = acc_o;
 }
@@ -631,10 +714,10 @@ static snn_status refresh_fixed(snn_classifier* c, cudaStream_t s) {
     const long long n_in = (long long)d.w_in->d.P * d.w_in->d.C, n_rec = (long long)d.w_rec->d.P * d.w_rec->d.C,
                     n_out = (long long)d.K * d.N;
     k_pack<real><<<ceil_div(n_in, 256), 256, 0, s>>>((const real*)d.w_in->d.w, d.w_in->d.ind, d.w_in->d.row_len,
-                                                      d.w_in->d.C, (long long*)c->wf_in, n_in);
+                                                      d.w_in->d.C, d.N, (long long*)c->wf_in, n_in);
     SNN_LAUNCH_CHECK();
     k_pack<real><<<ceil_div(n_rec, 256), 256, 0, s>>>((const real*)d.w_rec->d.w, d.w_rec->d.ind, d.w_rec->d.row_len,
-                                                       d.w_rec->d.C, (long long*)c->wf_rec, n_rec);
+                                                       d.w_rec->d.C, d.N, (long long*)c->wf_rec, n_rec);
     SNN_LAUNCH_CHECK();
     k_to_fixed<real><<<ceil_div(n_out, 256), 256, 0, s>>>((const real*)d.W_out, (long long*)c->wf_out, n_out);
     SNN_LAUNCH_CHECK();
@@ -722,12 +805,12 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
 }
 
 template <typename real, int KV>
-static void launch_backward(const snn_classifier* c, const snn_batch* bt, real* gb_part, cudaStream_t s) {
+static void launch_backward(const snn_classifier* c, const snn_batch* bt, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
     dim3 g(ceil_div(d.N, BWD_THREADS), bt->B);
-    k_backward<real, KV><<<g, BWD_THREADS, 0, s>>>((const real*)bt->psi_rec, (const real*)bt->d_rec,
-                                                   (const real*)d.W_out, (real*)bt->delta, (real*)bt->Dout, gb_part,
-                                                   bt->T, d.N, d.K, (real)c->alpha, (real)c->rho, (real)d.beta);
+    k_backward<real, KV><<<g, BWD_THREADS, 0, s>>>((const real*)bt->psi_rec, (const real*)bt->Dout,
+                                                   (const real*)d.W_out, (real*)bt->delta, bt->T, d.N, d.K,
+                                                   (real)c->alpha, (real)c->rho, (real)d.beta);
 }
 
 template <typename real>
@@ -736,15 +819,18 @@ static snn_status grad_impl(snn_classifier* c, const snn_batch* bt, cudaStream_t
     const int B = bt->B, T = bt->T, N = d.N, K = d.K, Kp = (K + 3) & ~3;
     const int Win = (d.n_in + 31) / 32, Wh = (N + 31) / 32;
     real* gb_part = (real*)c->part_out + (size_t)c->KS * N * K;
+    k_readout_scan<real><<<ceil_div((long long)B * Kp * 32, 256), 256, 0, s>>>(
+        (const real*)bt->d_rec, (real*)bt->Dout, gb_part, B, T, K, Kp, (real)c->alpha);
+    SNN_LAUNCH_CHECK();
     switch (Kp / 4) {
-        case 1: launch_backward<real, 1>(c, bt, gb_part, s); break;
-        case 2: launch_backward<real, 2>(c, bt, gb_part, s); break;
-        case 3: launch_backward<real, 3>(c, bt, gb_part, s); break;
-        case 4: launch_backward<real, 4>(c, bt, gb_part, s); break;
-        case 5: launch_backward<real, 5>(c, bt, gb_part, s); break;
-        case 6: launch_backward<real, 6>(c, bt, gb_part, s); break;
-        case 7: launch_backward<real, 7>(c, bt, gb_part, s); break;
-        default: launch_backward<real, 8>(c, bt, gb_part, s); break;
+        case 1: launch_backward<real, 1>(c, bt, s); break;
+        case 2: launch_backward<real, 2>(c, bt, s); break;
+        case 3: launch_backward<real, 3>(c, bt, s); break;
+        case 4: launch_backward<real, 4>(c, bt, s); break;
+        case 5: launch_backward<real, 5>(c, bt, s); break;
+        case 6: launch_backward<real, 6>(c, bt, s); break;
+        case 7: launch_backward<real, 7>(c, bt, s); break;
+        default: launch_backward<real, 8>(c, bt, s); break;
     }
     SNN_LAUNCH_CHECK();
     k_reduce_gb<real><<<1, 32, 0, s>>>(gb_part, (real*)d.G_b, B, K);
@@ -753,21 +839,14 @@ static snn_status grad_impl(snn_classifier* c, const snn_batch* bt, cudaStream_t
     const int KS = c->KS;
     const long long bt_per = ((BT + KS - 1) / KS + 31) / 32 * 32;
     SNN_REQUIRE(bt_per <= GATHER_SPAN, "snn_eprop_update: internal K-split too small");
-    dim3 gg(Win + Wh, KS);
     const snn_ragged_desc& ri = d.w_in->d;
     const snn_ragged_desc& rr = d.w_rec->d;
-    int Cmax = ri.C > rr.C ? ri.C : rr.C;
-#define SNN_GATHER(MC)                                                                                        \
-    k_gather<real, MC><<<gg, GATHER_THREADS, 0, s>>>(                                                          \
-        bt->x_rec, bt->z_rec, Win, Wh, ri.row_len, ri.ind, ri.C, d.n_in, rr.row_len, rr.ind, rr.C, N,          \
-        (const real*)bt->delta, (const real*)bt->Dout, K, Kp, BT, bt_per, (real*)c->part_in, (real*)c->part_rec, \
-        (real*)c->part_out)
-    if (Cmax <= 64) SNN_GATHER(2);
-    else if (Cmax <= 128) SNN_GATHER(4);
-    else if (Cmax <= 320) SNN_GATHER(10);
-    else if (Cmax <= 512) SNN_GATHER(16);
-    else SNN_GATHER(64);
-#undef SNN_GATHER
+    const int Cmax = ri.C > rr.C ? ri.C : rr.C;
+    dim3 gg((Win + Wh) * (32 / GATHER_ROWS), KS, (Cmax + 127) / 128);
+    k_gather<real, GATHER_ROWS, GATHER_EV><<<gg, GATHER_ROWS * 32, 0, s>>>(
+        bt->x_rec, bt->z_rec, Win, Wh, ri.row_len, ri.ind, ri.C, d.n_in,
+        rr.row_len, rr.ind, rr.C, N, (const real*)bt->delta, (const real*)bt->Dout, K, Kp, BT, bt_per,
+        (real*)c->part_in, (real*)c->part_rec, (real*)c->part_out);
     SNN_LAUNCH_CHECK();
     k_reduce_ragged<real><<<ceil_div((long long)ri.P * ri.C, 256), 256, 0, s>>>((const real*)c->part_in, ri.row_len,
                                                                                 ri.P, ri.C, KS, (real*)ri.grad);
