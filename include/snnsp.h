@@ -58,7 +58,7 @@ typedef void* snn_stream;        /* cudaStream_t */
 /* Message for the most recent failing call on this host thread ("" if none). */
 const char* snn_last_error(void);
 /* ABI version of this header (bumped on any incompatible change). */
-int32_t snn_abi_version(void);   /* 3 */
+int32_t snn_abi_version(void);   /* 4 */
 
 /* ==================================================================================
  * Ragged sparse matrix (Sec. 2.1, Fig. 1; DEEP R bitfields Sec. 2.1.2, Fig. 2)
@@ -173,7 +173,8 @@ typedef struct {
     double tau_a;         /* adaptation time constant (ms); <= 0 means LIF (rho = 0) */
     double dt;            /* step (ms) */
     int32_t n_classes, n_bins;
-    const uint64_t* in_thr;  /* device [n_classes][n_bins][n_in] Poisson thresholds */
+    const uint32_t* in_thr;  /* device [n_classes][n_bins][n_in] Poisson thresholds:
+                                floor(p * 2^32), saturated at 2^32 - 1 */
     uint64_t in_seed;        /* Philox seed of the input spikes (purpose INPUT) */
     snn_ragged* w_in;        /* P = n_in, Q = N */
     snn_ragged* w_rec;       /* P = N, Q = N, no_autapse = 1 */
@@ -235,7 +236,8 @@ snn_status snn_destroy_classifier(snn_classifier* c);
 /* Advance every trial of the batch by n_steps steps, t0 .. t0+n_steps-1 (t0 + n_steps
  * <= T), in ONE launch (one CTA per trial).  Per step t (Sec. 2.2.1 equations with the
  * one-step synaptic delay):
- *   x^t    : input spikes, channel c fires iff Philox(INPUT; (trial_id, t, c/4, 0))[c%4]
+ *   x^t    : input spikes, channel c fires iff the 32-bit half c%2 (0 low, 1 high) of
+ *            Philox(INPUT; (trial_id, t, c/8, 0))[(c%8)/2]
  *            < in_thr[label][min(n_bins-1, t / bin_len)][c]
  *   I^t    : ragged propagation of x^{t-1} through w_in and z^{t-1} through w_rec
  *   v, a, z, psi : v = alpha (v - z v_thr) + I, a = rho a + z_prev, A = v_thr + beta a,

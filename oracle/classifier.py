@@ -71,14 +71,17 @@ def lif_params(v_thr: float = 1.0, tau_m: float = 20.0, dt: float = 1.0) -> Neur
 # ------------------------------------------------------------------------------ input
 
 def poisson_input(thr: np.ndarray, label: int, bin_len: int, trial_id: int, t: int, seed: int) -> np.ndarray:
-    """Input spikes x^t of one trial: channel ch fires iff its Philox word is below the
-    threshold of its class template at the current (time-warped) bin."""
+    """Input spikes x^t of one trial: channel ch fires iff its 32-bit Philox draw is below
+    the 32-bit threshold of its class template at the current (time-warped) bin.  One
+    Philox block serves 8 channels: channel ch takes half ch % 2 (0 low, 1 high) of word
+    (ch % 8) // 2 of counter (trial_id, t, ch // 8, 0)."""
     n_bins, n_in = thr.shape[1], thr.shape[2]
     b = min(n_bins - 1, t // int(bin_len))
     ch = np.arange(n_in, dtype=np.uint64)
-    u = philox.draw(seed, philox.INPUT, np.uint64(trial_id), np.uint64(t), ch // np.uint64(4), 0,
-                    word=(ch % np.uint64(4)).astype(np.int64))
-    return u < thr[int(label), b, :]
+    u = philox.draw(seed, philox.INPUT, np.uint64(trial_id), np.uint64(t), ch // np.uint64(8), 0,
+                    word=((ch % np.uint64(8)) // np.uint64(2)).astype(np.int64))
+    half = (u >> (np.uint64(32) * (ch % np.uint64(2)))) & np.uint64(0xFFFFFFFF)
+    return half < thr[int(label), b, :].astype(np.uint64)
 
 
 # ------------------------------------------------------------------------- propagation

@@ -18,6 +18,8 @@ Conventions used by the whole method (both sides implement them independently):
   counter = (c0, c1, c2, c3) purpose-specific fields
   uniform integer in [0, n):  (u * n) >> 64              (multiply-high, Lemire)
   Bernoulli(p):               u < thr,  thr = floor(p * 2^64) (saturated)
+  32-bit Bernoulli(p) (classifier input only): one 32-bit half h of a word, h < thr32,
+                              thr32 = floor(p * 2^32) (saturated)
 """
 from __future__ import annotations
 
@@ -30,7 +32,8 @@ W1 = 0xBB67AE8584CAA73B
 MASK64 = (1 << 64) - 1
 
 # purposes (key word 1)
-INPUT = 1          # classifier Poisson input: counter (trial, t, ch // 4, 0), word ch % 4
+INPUT = 1          # classifier Poisson input: counter (trial, t, ch // 8, 0), word (ch % 8) // 2,
+                   # 32-bit half ch % 2 (0: low, 1: high)
 SIGN = 2           # DEEP R sign bitfield init: counter (row, word, 0, 0), word 0 low 32 bits
 DEEPR_DIST = 3     # DEEP R activation rows: counter (rewire, round, k // 4, 0), word k % 4
 DEEPR_FORM = 4     # DEEP R new target: counter (rewire, row, k, 0), word 0

@@ -33,14 +33,9 @@ struct FwdParams {
     int32_t* status;
     const int32_t* labels;
     const int32_t* in_len;
-    const int32_t* in_ind;
-    const long long* in_pk;    // packed (index | fixed-point weight) shadows of the ragged rows
-    int in_C;
     const int32_t* rec_len;
-    const int32_t* rec_ind;
-    const long long* rec_pk;
-    int rec_C;
-    const long long* out_wf;   // [K][N]
+    const unsigned long long* pk;   // packed rows (see k_pack), Cf slots each
+    int Cf;
     const real* b_out;
     real* v;
     real* a;
@@ -62,7 +57,7 @@ struct FwdParams {
 struct InputParams {
     int n_in, Win, T, t0, n_steps, n_bins, n_classes, B;
     const int32_t* trial_T;
-    const uint64_t* in_thr;
+    const uint32_t* in_thr;
     uint64_t seed;
     const int32_t* labels;
     const int32_t* bin_len;
@@ -78,13 +73,14 @@ __device__ __forceinline__ double exp_real(double x) { return exp(x); }
 __device__ __forceinline__ long long sext52(long long a) { return (long long)((unsigned long long)a << 12) >> 12; }
 
 // Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
-// only, so they are drawn ahead of the sequential simulation.  Thread = 4 channels (one
-// Philox block); the nibbles of 8 consecutive threads form one 32-channel word.
+// only, so they are drawn ahead of the sequential simulation.  Thread = 8 channels (one
+// Philox block, one 32-bit half of a word per channel); the bytes of 4 consecutive
+// threads form one 32-channel word.
 __global__ void k_input(InputParams p) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int G = p.Win * 8;
+    const int G = p.Win * 4;
     const long long total = (long long)p.B * p.n_steps * G;
-    uint32_t nib = 0;
+    uint32_t byte = 0;
     int gi = (int)(g % G);
     long long bt = g / G;
     if (g < total) {
@@ -96,25 +92,25 @@ __global__ void k_input(InputParams p) {
             label = min(max(label, 0), p.n_classes - 1);
             bin_len = max(bin_len, 1);
         }
-        if (4 * gi < p.n_in && (!p.trial_T || t < p.trial_T[b])) {
+        if (8 * gi < p.n_in && (!p.trial_T || t < p.trial_T[b])) {
             const int bin = min(p.n_bins - 1, t / bin_len);
-            const uint64_t* thr = p.in_thr + ((size_t)label * p.n_bins + bin) * p.n_in;
+            const uint32_t* thr = p.in_thr + ((size_t)label * p.n_bins + bin) * p.n_in;
             const u64x4 r = philox(p.seed, PH_INPUT, (uint64_t)p.trial_ids[b], (uint64_t)t, (uint64_t)gi, 0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int c = 4 * gi + q;
-                if (c < p.n_in && r[q] < thr[c]) nib |= 1u << q;
+            for (int q = 0; q < 8; ++q) {
+                const int c = 8 * gi + q;
+                const uint32_t h = (uint32_t)(r[q >> 1] >> (32 * (q & 1)));
+                if (c < p.n_in && h < thr[c]) byte |= 1u << q;
             }
         }
     }
-    uint32_t word = nib << (4 * (gi & 7));
+    uint32_t word = byte << (8 * (gi & 3));
     word |= __shfl_xor_sync(0xffffffffu, word, 1);
     word |= __shfl_xor_sync(0xffffffffu, word, 2);
-    word |= __shfl_xor_sync(0xffffffffu, word, 4);
-    if (g < total && (gi & 7) == 0) {
+    if (g < total && (gi & 3) == 0) {
         const int b = (int)(bt / p.n_steps);
         const int t = p.t0 + (int)(bt % p.n_steps);
-        p.x_rec[((size_t)b * p.T + t) * p.Win + (gi >> 3)] = word;
+        p.x_rec[((size_t)b * p.T + t) * p.Win + (gi >> 2)] = word;
     }
 }
 
@@ -126,20 +122,22 @@ __global__ void k_input(InputParams p) {
 //  (A) warps take every nwarps-th row of the lists of step t-1, two rows at a time; each
 //      slot is one packed 64-bit load (target index | fixed-point weight) and one
 //      shared-memory atomic of that whole word (padding slots of a row's last chunk add
-//      0 to per-lane spare accumulators); hidden rows also add their readout column.
-//      Phase B reads the low 52 bits of each accumulator sign-extended, which is the
-//      exact weight sum while it stays below 2^11 in magnitude.  The last warp
+//      0 to per-lane spare accumulators).  Hidden rows carry their readout column as K
+//      extra slots aimed at the readout accumulators, so W_out z^{t-1} is summed by the
+//      same loop.  Accumulators are read as their low 52 bits sign-extended, which is
+//      the exact weight sum while it stays below 2^11 in magnitude.  The last warp
 //      meanwhile finishes the readout of step t-1 (leak, softmax, d record).
-//  (B) each thread updates its NPT neurons (state in registers) and writes psi.
+//  (B) each thread updates its NPT neurons (state in registers) and writes psi; warp 1
+//      moves the readout sums of step t out of the accumulators for the next readout.
 template <typename real, int NPT, int TH>
 __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh, n_in = p.n_in;
     const int R = n_in + N;
-    long long* Iacc = (long long*)smem;           // [N + 32] (slots N.. are per-lane spares)
-    long long* yfix = Iacc + N + 32;              // [2][32] readout accumulators
-    int* lens = (int*)(yfix + 64);                // [R]
-    int* list = lens + R;                         // [2][R] spiking rows by step parity
+    long long* Iacc = (long long*)smem;           // [N + 64]: neurons, 32 per-lane spares, readouts
+    long long* yfix = Iacc + N + 64;              // [32] readout sums of the last finished step
+    int* lens = (int*)(yfix + 32);                // [R + 1] packed row lengths (row R: empty)
+    int* list = lens + R + 1;                     // [2][R] spiking rows by step parity
     int* lcnt = list + 2 * R;                     // [2]
     uint32_t* xw = (uint32_t*)(lcnt + 2);         // [Win] input spike words of the current step
     uint32_t* zb = xw + Win;                      // [2][Wh]
@@ -162,10 +160,11 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             vr[q] = j < N ? p.v[(size_t)b * N + j] : real(0);
             ar[q] = j < N ? p.a[(size_t)b * N + j] : real(0);
         }
-        for (int j = tid; j < N + 32; j += TH) Iacc[j] = 0;
-        for (int j = tid; j < N; j += TH) lens[n_in + j] = p.rec_len[j];
+        for (int j = tid; j < N + 64; j += TH) Iacc[j] = 0;
+        for (int j = tid; j < N; j += TH) lens[n_in + j] = p.rec_len[j] + K;
         for (int i = tid; i < n_in; i += TH) lens[i] = p.in_len[i];
-        if (tid < 64) yfix[tid] = 0;
+        if (tid == 0) lens[R] = 0;
+        if (tid < 32) yfix[tid] = 0;
         for (int w = tid; w < Wh; w += TH) zb[prv * Wh + w] = p.z_bits[(size_t)b * Wh + w];
         if (warp == 0) {
             // lists of step t0-1 from the state's spike words
@@ -194,11 +193,9 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     unsigned long long* acc = (unsigned long long*)Iacc;
 
     auto readout = [&](int s) {
-        long long* yb = yfix + 32 * (s & 1);
         real ynew = 0, ex = 0;
         if (lane < K) {
-            yk = p.alpha * yk + from_fixed<real>(yb[lane]) + bk;
-            yb[lane] = 0;
+            yk = p.alpha * yk + from_fixed<real>(sext52(yfix[lane])) + bk;
             ynew = yk;
             ysk += yk;
         }
@@ -215,7 +212,6 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
         const int cur = t & 1, prv = cur ^ 1;
         const uint32_t* zprv = zb + prv * Wh;
         uint32_t* zcur = zb + cur * Wh;
-        unsigned long long* yacc = (unsigned long long*)(yfix + 32 * cur);
         const int* lprv = list + prv * R;
         int* lcur = list + cur * R;
         // ---------------- phase A
@@ -229,23 +225,18 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
         if (warp == RO_WARP && t > t0) readout(t - 1);
         for (int k = warp; k < n_rows; k += 2 * nwarps) {
             const int rA = lprv[k];
-            const int rB = (k + nwarps < n_rows) ? lprv[k + nwarps] : -1;
-            const bool hA = rA >= n_in, hB = rB >= n_in;
-            const int iA = hA ? rA - n_in : rA, iB = hB ? rB - n_in : (rB < 0 ? 0 : rB);
-            const int nA = lens[rA], nB = rB >= 0 ? lens[rB] : 0;
-            const long long* pkA = hA ? p.rec_pk + (size_t)iA * p.rec_C : p.in_pk + (size_t)iA * p.in_C;
-            const long long* pkB = hB ? p.rec_pk + (size_t)iB * p.rec_C : p.in_pk + (size_t)iB * p.in_C;
-            const bool roA = hA && lane < K, roB = hB && lane < K;
-            const long long oA = roA ? p.out_wf[(size_t)lane * N + iA] : 0ll;
-            const long long oB = roB ? p.out_wf[(size_t)lane * N + iB] : 0ll;
+            const int rB = (k + nwarps < n_rows) ? lprv[k + nwarps] : R;   // R: empty row
+            const int nA = lens[rA], nB = lens[rB];
+            const unsigned long long* pkA = p.pk + (size_t)rA * p.Cf;
+            const unsigned long long* pkB = p.pk + (size_t)(rB < R ? rB : 0) * p.Cf;
             const int nmax = nA > nB ? nA : nB;
             for (int s0 = 0; s0 < nmax; s0 += 128) {
                 unsigned long long wA[4], wB[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     // warp-uniform chunk tests; chunk slots past the length are padding
-                    wA[q] = s0 + q * 32 < nA ? (unsigned long long)pkA[s0 + q * 32 + lane] : 0ull;
-                    wB[q] = s0 + q * 32 < nB ? (unsigned long long)pkB[s0 + q * 32 + lane] : 0ull;
+                    wA[q] = s0 + q * 32 < nA ? pkA[s0 + q * 32 + lane] : 0ull;
+                    wB[q] = s0 + q * 32 < nB ? pkB[s0 + q * 32 + lane] : 0ull;
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -253,8 +244,6 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
                     if (s0 + q * 32 < nB) atomicAdd(acc + (unsigned)(wB[q] >> 52), wB[q]);
                 }
             }
-            if (roA) atomicAdd(yacc + lane, (unsigned long long)oA);
-            if (roB) atomicAdd(yacc + lane, (unsigned long long)oB);
         }
         __syncthreads();
         // ---------------- phase B: neurons; spike lists of step t
@@ -264,6 +253,10 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             const int pos = atomicAdd(&lcnt[cur], __popc(word));
             for (int k = 0; word; ++k, word &= word - 1u) lcur[pos + k] = lane * 32 + __ffs(word) - 1;
             xw[lane] = 0u;
+        }
+        if (warp == 1 && lane < K) {               // readout sums of step t (W_out z^{t-1})
+            yfix[lane] = Iacc[N + 32 + lane];
+            Iacc[N + 32 + lane] = 0;
         }
         real* psi_t = psi_b ? psi_b + (size_t)t * N : nullptr;
 #pragma unroll
@@ -324,32 +317,44 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     }
 }
 
-// Packed forward shadow of a ragged matrix: bits 63..52 target index, bits 51..0 the
-// weight in fixed point (40 fractional bits, two's complement), one 64-bit load per slot.
-// The forward adds the whole packed word to the target's accumulator: the low 52 bits
-// of the sum are the weight sum modulo 2^52 (read back sign-extended), the index bits
-// only pile up above them.  Slots past the row length (up to the capacity C, a multiple
-// of 32) hold weight 0 aimed at accumulator spare + (slot mod 32), so a warp can add a
-// whole 32-slot chunk with no per-lane test and no two lanes on one address.
+// Packed forward rows: row r < n_in is input row r, row n_in + j is hidden row j; Cf
+// slots each.  A slot is bits 63..52 target accumulator, bits 51..0 the weight in fixed
+// point (40 fractional bits, two's complement): one 64-bit load per slot.  Hidden row j
+// holds its len_j synapses, then its readout column W_out[k][j] aimed at accumulators
+// N + 32 + k.  The forward adds the whole packed word to the target's accumulator: the
+// low 52 bits of the sum are the weight sum modulo 2^52 (read back sign-extended), the
+// target bits only pile up above them.  Slots past a row's length hold weight 0 aimed at
+// the per-lane spare N + (slot mod 32), so a warp adds a row's last 32-slot chunk whole,
+// with no per-lane test and no two lanes on one address.
 template <typename real>
-__global__ void k_pack(const real* __restrict__ w, const int32_t* __restrict__ ind, const int32_t* __restrict__ len,
-                       int C, int spare, long long* __restrict__ pk, long long n) {
+__global__ void k_pack(const real* __restrict__ w_in, const int32_t* __restrict__ ind_in,
+                       const int32_t* __restrict__ len_in, int C_in, int n_in, const real* __restrict__ w_rec,
+                       const int32_t* __restrict__ ind_rec, const int32_t* __restrict__ len_rec, int C_rec,
+                       const real* __restrict__ W_out, int K, int N, int Cf, unsigned long long* __restrict__ pk,
+                       long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int row = (int)(i / C), s = (int)(i % C);
-    if (s >= len[row]) {
-        pk[i] = (long long)((unsigned long long)(unsigned)(spare + (s & 31)) << 52);
-        return;
+    const int r = (int)(i / Cf), s = (int)(i % Cf);
+    unsigned tgt = (unsigned)(N + (s & 31));
+    long long f = 0;
+    if (r < n_in) {
+        if (s < len_in[r]) {
+            const size_t e = (size_t)r * C_in + s;
+            tgt = (unsigned)ind_in[e];
+            f = to_fixed(w_in[e]);
+        }
+    } else {
+        const int j = r - n_in, L = len_rec[j];
+        if (s < L) {
+            const size_t e = (size_t)j * C_rec + s;
+            tgt = (unsigned)ind_rec[e];
+            f = to_fixed(w_rec[e]);
+        } else if (s < L + K) {
+            tgt = (unsigned)(N + 32 + (s - L));
+            f = to_fixed(W_out[(size_t)(s - L) * N + j]);
+        }
     }
-    const long long f = to_fixed(w[i]) & ((1ll << 52) - 1);
-    pk[i] = (long long)(((unsigned long long)(unsigned)ind[i] << 52) | (unsigned long long)f);
-}
-
-// Fixed-point shadow of a dense weight array (40 fractional bits).
-template <typename real>
-__global__ void k_to_fixed(const real* __restrict__ w, long long* __restrict__ wf, long long n) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) wf[i] = to_fixed(w[i]);
+    pk[i] = ((unsigned long long)tgt << 52) | ((unsigned long long)f & ((1ull << 52) - 1));
 }
 
 // ------------------------------------------------------------------ backward
@@ -418,7 +423,7 @@ __global__ void k_readout_scan(const real* __restrict__ d, real* __restrict__ Do
 //   lam = sum_k W_out[k][j] D_k,  mu = beta lam' psi' + (rho - beta psi') mu',
 //   h = psi (lam - mu),  delta = h' + alpha delta'   (primes: step t+1; zero after T-1).
 constexpr int BWD_THREADS = 128;
-constexpr int BWD_TCH = 32;
+constexpr int BWD_TCH = 8;
 
 template <typename real, int KV>
 __global__ void __launch_bounds__(BWD_THREADS)
@@ -488,7 +493,7 @@ __global__ void __launch_bounds__(BWD_THREADS)
 // per lane.  The group-0 warps of hidden rows also sum D into the
 // readout gradient.  CTAs whose rows all end before their group exit before staging.
 constexpr int GATHER_SPAN = 8192;
-constexpr int GATHER_ROWS = 32;   // rows (warps) per CTA: 32 or 16
+constexpr int GATHER_ROWS = 16;   // rows (warps) per CTA: 32, 16 or 8
 constexpr int GATHER_EV = 4;      // spike events whose loads are issued together
 
 template <typename real, int ROWS, int EV>
@@ -678,7 +683,8 @@ __global__ void k_adam_dense(real* __restrict__ w, real* __restrict__ m, real* _
 
 // ------------------------------------------------------------------ host side
 static size_t fwd_smem(int n_in, int N, int Win, int Wh) {
-    return (size_t)(N + 32) * 8 + 64 * 8 + (size_t)(n_in + N) * 4 * 3 + 8 + (size_t)(Win + 2 * Wh) * 4;
+    return (size_t)(N + 64) * 8 + 32 * 8 + (size_t)(n_in + N + 1) * 4 + (size_t)(n_in + N) * 4 * 2 + 8 +
+           (size_t)(Win + 2 * Wh) * 4;
 }
 
 template <typename real, int NPT, int TH>
@@ -711,15 +717,11 @@ static snn_status launch_forward_th(const FwdParams<real>& p, int B, size_t smem
 template <typename real>
 static snn_status refresh_fixed(snn_classifier* c, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
-    const long long n_in = (long long)d.w_in->d.P * d.w_in->d.C, n_rec = (long long)d.w_rec->d.P * d.w_rec->d.C,
-                    n_out = (long long)d.K * d.N;
-    k_pack<real><<<ceil_div(n_in, 256), 256, 0, s>>>((const real*)d.w_in->d.w, d.w_in->d.ind, d.w_in->d.row_len,
-                                                      d.w_in->d.C, d.N, (long long*)c->wf_in, n_in);
-    SNN_LAUNCH_CHECK();
-    k_pack<real><<<ceil_div(n_rec, 256), 256, 0, s>>>((const real*)d.w_rec->d.w, d.w_rec->d.ind, d.w_rec->d.row_len,
-                                                       d.w_rec->d.C, d.N, (long long*)c->wf_rec, n_rec);
-    SNN_LAUNCH_CHECK();
-    k_to_fixed<real><<<ceil_div(n_out, 256), 256, 0, s>>>((const real*)d.W_out, (long long*)c->wf_out, n_out);
+    const long long n = (long long)(d.n_in + d.N) * c->Cf;
+    k_pack<real><<<ceil_div(n, 256), 256, 0, s>>>(
+        (const real*)d.w_in->d.w, d.w_in->d.ind, d.w_in->d.row_len, d.w_in->d.C, d.n_in, (const real*)d.w_rec->d.w,
+        d.w_rec->d.ind, d.w_rec->d.row_len, d.w_rec->d.C, (const real*)d.W_out, d.K, d.N, c->Cf,
+        (unsigned long long*)c->pk, n);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -745,7 +747,7 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     ip.x_rec = bt->x_rec;
     ip.status = d.w_in->status;
     ip.trial_T = bt->trial_T;
-    const long long groups = (long long)bt->B * n_steps * Win * 8;
+    const long long groups = (long long)bt->B * n_steps * Win * 4;
     k_input<<<ceil_div(groups, 256), 256, 0, s>>>(ip);
     SNN_LAUNCH_CHECK();
 
@@ -768,14 +770,9 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.status = d.w_in->status;
     p.labels = bt->labels;
     p.in_len = d.w_in->d.row_len;
-    p.in_ind = d.w_in->d.ind;
-    p.in_pk = (const long long*)c->wf_in;
-    p.in_C = d.w_in->d.C;
     p.rec_len = d.w_rec->d.row_len;
-    p.rec_ind = d.w_rec->d.ind;
-    p.rec_pk = (const long long*)c->wf_rec;
-    p.rec_C = d.w_rec->d.C;
-    p.out_wf = (const long long*)c->wf_out;
+    p.pk = (const unsigned long long*)c->pk;
+    p.Cf = c->Cf;
     p.b_out = (const real*)d.b_out;
     p.v = (real*)bt->v;
     p.a = (real*)bt->a;
@@ -906,7 +903,7 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     SNN_REQUIRE(d->max_B > 0 && d->max_T > 0, "snn_create_classifier: max_B, max_T must be > 0");
     SNN_REQUIRE(d->w_in->d.C <= 2048 && d->w_rec->d.C <= 2048, "snn_create_classifier: row capacity must be <= 2048");
     SNN_REQUIRE(d->N <= 8 * 256, "snn_create_classifier: N must be <= 2048");
-    SNN_REQUIRE(d->N < 4096, "snn_create_classifier: N must fit the 12-bit packed target index");
+    SNN_REQUIRE(d->N + 64 <= 4096, "snn_create_classifier: N + 64 accumulators must fit the 12-bit packed target");
     SNN_REQUIRE(d->n_in <= 1024, "snn_create_classifier: n_in must be <= 1024");
     snn_classifier* c = (snn_classifier*)calloc(1, sizeof(snn_classifier));
     if (!c) {
@@ -920,6 +917,8 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     long long BT = (long long)d->max_B * d->max_T;
     // K-splits of the gather: each CTA stages at most 8192 (trial, step) spike words
     c->KS = (int)((BT + 8191) / 8192);
+    const int c_rec = d->w_rec->d.C + d->K;
+    c->Cf = ((d->w_in->d.C > c_rec ? d->w_in->d.C : c_rec) + 31) / 32 * 32;
     size_t rsz = d->dtype == SNN_F32 ? 4 : 8;
     size_t n_in_part = (size_t)c->KS * d->w_in->d.P * d->w_in->d.C * rsz;
     size_t n_rec_part = (size_t)c->KS * d->w_rec->d.P * d->w_rec->d.C * rsz;
@@ -927,9 +926,7 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     cudaError_t e = cudaMalloc(&c->part_in, n_in_part);
     if (e == cudaSuccess) e = cudaMalloc(&c->part_rec, n_rec_part);
     if (e == cudaSuccess) e = cudaMalloc(&c->part_out, n_out_part);
-    if (e == cudaSuccess) e = cudaMalloc(&c->wf_in, (size_t)d->w_in->d.P * d->w_in->d.C * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&c->wf_rec, (size_t)d->w_rec->d.P * d->w_rec->d.C * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&c->wf_out, (size_t)d->K * d->N * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->pk, (size_t)(d->n_in + d->N) * c->Cf * 8);
     if (e != cudaSuccess) {
         snn_destroy_classifier(c);
         set_error("snn_create_classifier: cudaMalloc failed: %s", cudaGetErrorString(e));
@@ -954,9 +951,7 @@ snn_status snn_destroy_classifier(snn_classifier* c) {
     cudaFree(c->part_in);
     cudaFree(c->part_rec);
     cudaFree(c->part_out);
-    cudaFree(c->wf_in);
-    cudaFree(c->wf_rec);
-    cudaFree(c->wf_out);
+    cudaFree(c->pk);
     free(c);
     return SNN_OK;
 }

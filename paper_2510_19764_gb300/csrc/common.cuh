@@ -205,7 +205,6 @@ struct snn_classifier {
     void* part_in;           // [KS][P_in*C_in] partial gradients
     void* part_rec;          // [KS][N*C_rec]
     void* part_out;          // [KS][N][K]
-    void* wf_in;             // [P_in*C_in] int64 fixed-point shadow of w_in (refreshed per forward call)
-    void* wf_rec;            // [N*C_rec]
-    void* wf_out;            // [K*N]
+    void* pk;                // [(n_in + N) * Cf] packed forward rows (refreshed per forward call)
+    int32_t Cf;              // slots per packed row: max(C_in, C_rec + K) rounded up to 32
 };

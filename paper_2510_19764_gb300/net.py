@@ -128,7 +128,7 @@ class DeviceClassifier:
         self.b_v = torch.zeros_like(self.b_out)
         self.G_out = torch.zeros_like(self.W_out)
         self.G_b = torch.zeros_like(self.b_out)
-        self.in_thr = _u64_tensor(in_thr, device)
+        self.in_thr = _u32_tensor(in_thr, device)
         n_classes, n_bins, _ = in_thr.shape
         d = abi.ClassifierDesc()
         d.n_in, d.N, d.K, d.dtype = n_in, N, K, dtype

@@ -23,26 +23,27 @@ from dataclasses import dataclass
 
 import numpy as np
 
-TWO64 = float(2 ** 64)
+TWO32 = float(2 ** 32)
 
 
 def rate_threshold(p: float) -> int:
-    """Encode a per-step spike probability p as a 64-bit threshold.
+    """Encode a per-step spike probability p as a 32-bit threshold.
 
-    A Philox word u (uint64) fires iff u < thr.  thr = floor(p * 2^64) for p < 1,
-    saturated at 2^64 - 1 for p >= 1 and 0 for p <= 0.  p * 2^64 is an exact
+    A 32-bit Philox draw h fires iff h < thr.  thr = floor(p * 2^32) for p < 1,
+    saturated at 2^32 - 1 for p >= 1 and 0 for p <= 0.  p * 2^32 is an exact
     power-of-two scaling of the double p, so the conversion is exact.
     """
     if p <= 0.0:
         return 0
     if p >= 1.0:
-        return (1 << 64) - 1
-    return int(p * TWO64)
+        return (1 << 32) - 1
+    return int(p * TWO32)
 
 
 def rates_to_thresholds(rates_hz: np.ndarray, dt_ms: float) -> np.ndarray:
+    """uint32 thresholds of per-step spike probabilities rate * dt."""
     flat = [rate_threshold(float(r) * dt_ms * 1e-3) for r in np.asarray(rates_hz, dtype=np.float64).ravel()]
-    return np.array(flat, dtype=np.uint64).reshape(np.shape(rates_hz))
+    return np.array(flat, dtype=np.uint32).reshape(np.shape(rates_hz))
 
 
 # --------------------------------------------------------------------------------------

@@ -279,3 +279,32 @@ def test_eprop_synapse_vectorised_over_trials_equals_trace_form():
                 psi = np.array([r["psi"][:, j] for r in recs])
                 L = np.array([r["d"] @ net.W_out[:, j] for r in recs])
                 np.testing.assert_allclose(oc.eprop_synapse(pre, psi, L, p), G[i, s], rtol=1e-12, atol=1e-13)
+
+
+def test_neuron_constants_match_paper():
+    """NeuronParams' defaults are the printed constants; alpha, rho and psi's peak follow
+    from them by the printed formulas (psi peaks at gain / v_thr where v = A, and is
+    zero once |v - A| >= v_thr)."""
+    import os
+    tab = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "classifier_parameters.txt")
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            name, value = line.split(";", 1)[0].split()[:2]
+            tab[name] = float(value)
+    p = oc.NeuronParams()
+    assert (p.tau_m, p.v_thr, p.tau_a, p.beta, p.dt) == (tab["tau_mem"], tab["v_thr"], tab["tau_adapt"],
+                                                        tab["beta"], tab["dt"])
+    assert p.alpha == pytest.approx(math.exp(-1.0 / 20.0), rel=1e-15)
+    assert p.rho == pytest.approx(math.exp(-1.0 / 2000.0), rel=1e-15)
+    # z_prev = 0, v_prev = 0: v = I; a_prev = 2 / rho: a = 2, A = v_thr + 2 beta
+    A = p.v_thr + 2.0 * p.beta
+    I = np.array([A, A + 0.5 * p.v_thr, A - p.v_thr, A + 2 * p.v_thr, A - 1e-9])
+    v, a, z, psi, A_out = oc.neuron_step(np.zeros(5), np.full(5, 2.0 / p.rho), np.zeros(5), I, p)
+    np.testing.assert_allclose(a, 2.0, rtol=1e-15)
+    np.testing.assert_allclose(A_out, 0.6 + 2 * 0.0174, rtol=1e-15)
+    # peak gain / v_thr = 0.3 / 0.6 at v = A, half of it halfway out, zero at the edges
+    np.testing.assert_allclose(psi[:4], [0.5, 0.25, 0.0, 0.0], atol=1e-12)
+    assert tab["psi_gain"] / tab["v_thr"] == pytest.approx(0.5)
+    np.testing.assert_array_equal(z, [1, 1, 0, 1, 0])

@@ -1,6 +1,7 @@
 """Pins of the topographic-map oracle: analytic neuron solution, STDP pair rule,
 Fig. 3's worked example, closed-form formation rates, input statistics."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -186,3 +187,41 @@ def test_short_run_invariants():
                 assert len(set(tg)) == len(tg)
                 assert np.all((proj[2][i, :proj[0][i]] >= 0) & (proj[2][i, :proj[0][i]] <= p.g_max))
     assert spikes > 0
+
+
+def _paper_tables():
+    rows = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "topo_parameter_tables.txt")
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        fields, src = line.split(";", 1)
+        name, value = fields.split()[:2]
+        rows[name] = (float(value), "reading" in src)
+    return rows
+
+
+def test_parameters_match_paper_tables():
+    """TopoParams' defaults are the printed table values (apart from the lines the
+    fixture marks as readings), and the derived quantities follow the printed formulas:
+    A+ = 0.1 g_max, A- = B A+ tau+ / tau-, g_theta = g_max / 2."""
+    tab = _paper_tables()
+    p = topo.TopoParams()
+    direct = {"tau_m": p.tau_m, "V_rest": p.V_rest, "E_exc": p.E_exc, "V_theta": p.V_theta,
+              "V_reset": p.V_reset, "tau_ref": p.tau_ref, "tau_s": p.tau_s, "t_stim": p.t_stim,
+              "g_max": p.g_max, "B_ratio": p.B_ratio, "tau_plus": p.tau_plus, "tau_minus": p.tau_minus,
+              "p_form_ff": p.p_form_ff, "sigma_ff": p.sigma_ff, "p_form_lat": p.p_form_lat,
+              "sigma_lat": p.sigma_lat, "p_elim_dep": p.p_elim_dep, "p_elim_pot": p.p_elim_pot,
+              "A_plus_over_g_max": p.A_plus / p.g_max, "g_theta_over_g_max": p.g_theta / p.g_max}
+    for name, got in direct.items():
+        value, reading = tab[name]
+        assert not reading, name
+        assert got == pytest.approx(value, rel=1e-12), name
+    assert p.A_minus == pytest.approx(1.2 * 0.1 * 0.2 * 20.0 / 64.0, rel=1e-12)
+    # the scaled sheet: L = L0 s with s = 2 for the 32 x 32 workload
+    assert p.L == 2 * int(tab["L0"][0])
+    # reading lines are the documented replacements, not silent changes
+    assert all(tab[n][1] for n in ("t_d", "C_m", "f_base", "f_peak", "sigma_stim", "N_attempts", "h", "t_rewiring"))
+    # rewiring every t_rewiring / h steps, as printed (10), at the oracle's 1 ms step
+    assert p.rewire_every == round(tab["t_rewiring"][0] / tab["h"][0])
