@@ -29,6 +29,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# library kernels per training batch: forward call 4 (k_input, k_pack, k_forward,
+# k_softmax_d), gradient 7 (k_readout_scan, k_reduce_gb, k_backward, k_gather,
+# k_reduce_ragged x2, k_reduce_out), Adam 4 (k_adam_ragged x2, k_adam_dense x2),
+# DEEP R 6 (eliminate, distribute, form per projection)
+LAUNCHES_PER_BATCH = 21
 METRIC = "e-prop+DEEP R training samples/s"
 UNIT = "samples/s"
 WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}
@@ -236,6 +241,7 @@ def run_ours(args, world, rank, local):
         one_step(i, d_desc[i], False)
     barrier()
     # ---- device-resident timed region
+    stats.zero_()
     with ClockSampler(local) as clk:
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
@@ -258,6 +264,8 @@ def run_ours(args, world, rank, local):
             per_call[c] += ev[c].elapsed_time(ev[c + 1])
     per_call = [x / len(ev_pairs) for x in per_call]
     events, spikes = count_events(batch, cls, dev)
+    rewired = int(stats[:, 0].sum().item() + stats[:, 1].sum().item())     # removed + formed, timed batches
+    active = int(cls.w_in.row_len.sum().item() + cls.w_rec.row_len.sum().item())
     # ---- end-to-end leg through the public calls, host buffers each step
     out_host = torch.empty((B, W["K"]), dtype=torch.float32).pin_memory()
     stats_host = torch.empty((2, 4), dtype=torch.int64).pin_memory()
@@ -310,13 +318,18 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (per-batch records and adjoint > 4 GB rewritten every step)"},
         "synaptic_events_per_s": round(events * world / (ms_max / 1e3 / args.steps), 1),
+        # e-prop: the per-synapse trace form updates every active synapse of every trial at
+        # every step; the adjoint gather computes the same gradients from synaptic events
+        "synapse_updates_per_s": round(active * B * T * world / (ms_max / 1e3 / args.steps), 1),
+        # DEEP R: (removed + formed) over the rewiring calls' own time
+        "rewired_synapses_per_s": round(rewired / (per_call[3] * args.steps / 1e3), 1) if per_call[3] > 0 else None,
         "per_call_ms": {c: round(x, 4) for c, x in zip(calls, per_call)},
         "roofline": {"kernel": calls[dom], "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
                      "traffic": None, "peak_source": pk["source"]},
         "e2e": {"value": round(B * args.steps * world / (e2e_ms / 1e3), 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 18 * args.steps,
+        "gpu_launches": LAUNCHES_PER_BATCH * args.steps,
         "clocks": clocks,
         "status_ok": bool(ok),
     }

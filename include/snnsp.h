@@ -234,7 +234,8 @@ snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_tria
 snn_status snn_destroy_classifier(snn_classifier* c);
 
 /* Advance every trial of the batch by n_steps steps, t0 .. t0+n_steps-1 (t0 + n_steps
- * <= T), in ONE launch (one CTA per trial).  Per step t (Sec. 2.2.1 equations with the
+ * <= T), with all steps in one forward launch (one CTA per trial; the input spikes are
+ * drawn by a launch before it and d by a launch after it).  Per step t (Sec. 2.2.1 equations with the
  * one-step synaptic delay):
  *   x^t    : input spikes, channel c fires iff the 32-bit half c%2 (0 low, 1 high) of
  *            Philox(INPUT; (trial_id, t, c/8, 0))[(c%8)/2]

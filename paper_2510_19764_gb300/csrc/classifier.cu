@@ -4,7 +4,8 @@
 // Per step it propagates the previous step's input and hidden spikes through the two
 // ragged matrices into shared-memory fixed-point accumulators (sums independent of the
 // order of the atomic additions), draws the new input spikes from Philox, updates the
-// neurons, the leaky readout and its softmax, and records spikes (bits), psi and d.
+// neurons and the leaky readout, and records spikes (bits), psi and y; a second kernel
+// turns the recorded y into d = softmax(y) - onehot(label) for all steps in parallel.
 //
 // Gradient: e-prop's traces are linear in the presynaptic filtered spike train zbar_i
 // with coefficients that depend only on the postsynaptic neuron j, so
@@ -22,6 +23,7 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 namespace snn {
 
@@ -69,8 +71,22 @@ struct InputParams {
 __device__ __forceinline__ float exp_real(float x) { return expf(x); }
 __device__ __forceinline__ double exp_real(double x) { return exp(x); }
 
-// Signed value of the low 52 bits of a packed accumulator (see k_pack).
-__device__ __forceinline__ long long sext52(long long a) { return (long long)((unsigned long long)a << 12) >> 12; }
+// Forward accumulators: each is a pair of 32-bit words {H, L} summing the two parts of
+// every added fixed-point weight w = 2^20 w_hi + w_lo (w_hi = bits 51..20 of the packed
+// slot as a signed 32-bit value, w_lo = bits 19..0): both sums use native 32-bit
+// shared-memory atomics and are exact: L takes at most one addend (< 2^20) per spiking
+// row, rows hold no repeated target and n_in + N <= 3072 < 4096; H wraps modulo 2^32
+// like the 52-bit weights.  The total is 2^20 H + L.
+__device__ __forceinline__ void acc_add(unsigned* acc, unsigned long long w) {
+    const unsigned lo = (unsigned)w, hi = (unsigned)(w >> 32);
+    unsigned* a = acc + 2 * (hi >> 20);                   // target index: bits 63..52
+    atomicAdd(a, __funnelshift_r(lo, hi, 20));            // bits 51..20
+    atomicAdd(a + 1, lo & 0xFFFFFu);                      // bits 19..0
+}
+__device__ __forceinline__ long long acc_value(const long long* acc) {
+    const unsigned* a = (const unsigned*)acc;
+    return (long long)(int)a[0] * (1ll << 20) + (long long)a[1];
+}
 
 // Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
 // only, so they are drawn ahead of the sequential simulation.  Thread = 8 channels (one
@@ -121,22 +137,21 @@ __global__ void k_input(InputParams p) {
 // spikes of step t (drawn ahead of time by k_input) are listed by warp 0.  Per step t:
 //  (A) warps take every nwarps-th row of the lists of step t-1, two rows at a time; each
 //      slot is one packed 64-bit load (target index | fixed-point weight) and one
-//      shared-memory atomic of that whole word (padding slots of a row's last chunk add
-//      0 to per-lane spare accumulators).  Hidden rows carry their readout column as K
+//      pair of 32-bit shared-memory atomics (padding slots of a row's last chunk add 0
+//      to per-lane spare accumulators).  Hidden rows carry their readout column as K
 //      extra slots aimed at the readout accumulators, so W_out z^{t-1} is summed by the
-//      same loop.  Accumulators are read as their low 52 bits sign-extended, which is
-//      the exact weight sum while it stays below 2^11 in magnitude.  The last warp
-//      meanwhile finishes the readout of step t-1 (leak, softmax, d record).
+//      same loop.  The accumulated sums are exact while they stay below 2^11 in
+//      magnitude (see acc_add).
 //  (B) each thread updates its NPT neurons (state in registers) and writes psi; warp 1
-//      moves the readout sums of step t out of the accumulators for the next readout.
+//      advances the leaky readout y^t = alpha y^{t-1} + W_out z^{t-1} + b (one lane per
+//      output, sequential in t) and records y^t into the d record (softmax comes later).
 template <typename real, int NPT, int TH>
 __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh, n_in = p.n_in;
     const int R = n_in + N;
     long long* Iacc = (long long*)smem;           // [N + 64]: neurons, 32 per-lane spares, readouts
-    long long* yfix = Iacc + N + 64;              // [32] readout sums of the last finished step
-    int* lens = (int*)(yfix + 32);                // [R + 1] packed row lengths (row R: empty)
+    int* lens = (int*)(Iacc + N + 64);            // [R + 1] packed row lengths (row R: empty)
     int* list = lens + R + 1;                     // [2][R] spiking rows by step parity
     int* lcnt = list + 2 * R;                     // [2]
     uint32_t* xw = (uint32_t*)(lcnt + 2);         // [Win] input spike words of the current step
@@ -146,9 +161,7 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int nwarps = TH / 32;
-    constexpr int RO_WARP = nwarps - 1;
-    int label = p.labels[b];
-    label = min(max(label, 0), p.n_classes - 1);  // validity is reported by k_input
+    constexpr int RO_WARP = 1;                    // advances the readout in phase B
     const int t0 = p.t0;
     const int t_end = p.trial_T ? min(p.t0 + p.n_steps, max(p.trial_T[b], p.t0)) : p.t0 + p.n_steps;
     real vr[NPT], ar[NPT];
@@ -164,7 +177,6 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
         for (int j = tid; j < N; j += TH) lens[n_in + j] = p.rec_len[j] + K;
         for (int i = tid; i < n_in; i += TH) lens[i] = p.in_len[i];
         if (tid == 0) lens[R] = 0;
-        if (tid < 32) yfix[tid] = 0;
         for (int w = tid; w < Wh; w += TH) zb[prv * Wh + w] = p.z_bits[(size_t)b * Wh + w];
         if (warp == 0) {
             // lists of step t0-1 from the state's spike words
@@ -190,23 +202,7 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     real* d_b = p.d_rec ? p.d_rec + (size_t)b * p.T * K : nullptr;
     uint32_t xnext = (warp == 0 && lane < Win && t0 < t_end) ? xrec_b[(size_t)t0 * Win + lane] : 0u;
     __syncthreads();
-    unsigned long long* acc = (unsigned long long*)Iacc;
-
-    auto readout = [&](int s) {
-        real ynew = 0, ex = 0;
-        if (lane < K) {
-            yk = p.alpha * yk + from_fixed<real>(sext52(yfix[lane])) + bk;
-            ynew = yk;
-            ysk += yk;
-        }
-        const real mx = warp_max(lane < K ? ynew : -INFINITY);
-        if (lane < K) ex = exp_real(ynew - mx);
-        const real ssum = warp_sum(ex);
-        if (lane < K) {
-            if (d_b) d_b[(size_t)s * K + lane] = ex / ssum - (lane == label ? real(1) : real(0));
-            if (p.y_rec) p.y_rec[((size_t)b * p.T + s) * K + lane] = ynew;
-        }
-    };
+    unsigned* acc = (unsigned*)Iacc;
 
     for (int t = t0; t < t_end; ++t) {
         const int cur = t & 1, prv = cur ^ 1;
@@ -222,7 +218,6 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             zcur[w] = 0u;
         }
         if (tid == 32) lcnt[cur] = 0;
-        if (warp == RO_WARP && t > t0) readout(t - 1);
         for (int k = warp; k < n_rows; k += 2 * nwarps) {
             const int rA = lprv[k];
             const int rB = (k + nwarps < n_rows) ? lprv[k + nwarps] : R;   // R: empty row
@@ -240,8 +235,8 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (s0 + q * 32 < nA) atomicAdd(acc + (unsigned)(wA[q] >> 52), wA[q]);
-                    if (s0 + q * 32 < nB) atomicAdd(acc + (unsigned)(wB[q] >> 52), wB[q]);
+                    if (s0 + q * 32 < nA) acc_add(acc, wA[q]);
+                    if (s0 + q * 32 < nB) acc_add(acc, wB[q]);
                 }
             }
         }
@@ -254,16 +249,20 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             for (int k = 0; word; ++k, word &= word - 1u) lcur[pos + k] = lane * 32 + __ffs(word) - 1;
             xw[lane] = 0u;
         }
-        if (warp == 1 && lane < K) {               // readout sums of step t (W_out z^{t-1})
-            yfix[lane] = Iacc[N + 32 + lane];
+        if (warp == RO_WARP && lane < K) {         // y^t from the readout sums W_out z^{t-1}
+            yk = p.alpha * yk + from_fixed<real>(acc_value(Iacc + N + 32 + lane)) + bk;
             Iacc[N + 32 + lane] = 0;
+            ysk += yk;
+            if (d_b) d_b[(size_t)t * K + lane] = yk;
+            if (p.y_rec) p.y_rec[((size_t)b * p.T + t) * K + lane] = yk;
         }
         real* psi_t = psi_b ? psi_b + (size_t)t * N : nullptr;
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
             const int j = tid + q * TH;
+            bool spk = false;
             if (j < N) {
-                const real I = from_fixed<real>(sext52(Iacc[j]));
+                const real I = from_fixed<real>(acc_value(Iacc + j));
                 Iacc[j] = 0;
                 const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
                 const real v = p.alpha * (zp ? vr[q] - p.v_thr : vr[q]) + I;
@@ -277,18 +276,18 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
                     p.v_rec[(size_t)b * p.T * N + (size_t)t * N + j] = v;
                     p.a_rec[(size_t)b * p.T * N + (size_t)t * N + j] = aa;
                 }
-                const unsigned am = __activemask();
-                const unsigned zm = __ballot_sync(am, v >= A);
-                if (zm) {
-                    const int leader = __ffs(am) - 1;
-                    int pos = 0;
-                    if (lane == leader) {
-                        zcur[j >> 5] = zm;
-                        pos = atomicAdd(&lcnt[cur], __popc(zm));
-                    }
-                    pos = __shfl_sync(am, pos, leader);
-                    if (v >= A) lcur[pos + __popc(zm & lanemask_lt())] = n_in + j;
+                spk = v >= A;
+            }
+            // whole warp: j >> 5 is the same word for all its lanes (TH is a multiple of 32)
+            const unsigned zm = __ballot_sync(0xffffffffu, spk);
+            if (zm) {
+                int pos = 0;
+                if (lane == 0) {
+                    zcur[j >> 5] = zm;
+                    pos = atomicAdd(&lcnt[cur], __popc(zm));
                 }
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                if (spk) lcur[pos + __popc(zm & lanemask_lt())] = n_in + j;
             }
         }
         __syncthreads();
@@ -296,7 +295,6 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     if (t_end > t0) {
         const int last = t_end - 1;
         const int cl = last & 1;
-        if (warp == RO_WARP) readout(last);
         for (int w = tid; w < Wh; w += TH) {
             zrec_b[(size_t)last * Wh + w] = zb[cl * Wh + w];
             p.z_bits[(size_t)b * Wh + w] = zb[cl * Wh + w];
@@ -317,13 +315,29 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     }
 }
 
+// d^t = softmax(y^t) - onehot(label) for every recorded (trial, step), in place over the
+// y values the forward left in the d record.  Thread = one (trial, step).
+template <typename real>
+__global__ void k_softmax_d(real* __restrict__ d, const int32_t* __restrict__ labels, int n_classes,
+                            const int32_t* __restrict__ trial_T, int B, int T, int K, int t0, int n_steps) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)B * n_steps) return;
+    const int b = (int)(g / n_steps), t = t0 + (int)(g % n_steps);
+    if (trial_T && t >= trial_T[b]) return;
+    const int label = min(max(labels[b], 0), n_classes - 1);
+    real* y = d + ((size_t)b * T + t) * K;
+    real mx = y[0];
+    for (int k = 1; k < K; ++k) mx = y[k] > mx ? y[k] : mx;
+    real ssum = 0;
+    for (int k = 0; k < K; ++k) ssum += exp_real(y[k] - mx);
+    for (int k = 0; k < K; ++k) y[k] = exp_real(y[k] - mx) / ssum - (k == label ? real(1) : real(0));
+}
+
 // Packed forward rows: row r < n_in is input row r, row n_in + j is hidden row j; Cf
 // slots each.  A slot is bits 63..52 target accumulator, bits 51..0 the weight in fixed
-// point (40 fractional bits, two's complement): one 64-bit load per slot.  Hidden row j
-// holds its len_j synapses, then its readout column W_out[k][j] aimed at accumulators
-// N + 32 + k.  The forward adds the whole packed word to the target's accumulator: the
-// low 52 bits of the sum are the weight sum modulo 2^52 (read back sign-extended), the
-// target bits only pile up above them.  Slots past a row's length hold weight 0 aimed at
+// point (40 fractional bits, two's complement): one 64-bit load per slot, added with
+// acc_add.  Hidden row j holds its len_j synapses, then its readout column W_out[k][j]
+// aimed at accumulators N + 32 + k.  Slots past a row's length hold weight 0 aimed at
 // the per-lane spare N + (slot mod 32), so a warp adds a row's last 32-slot chunk whole,
 // with no per-lane test and no two lanes on one address.
 template <typename real>
@@ -683,7 +697,7 @@ __global__ void k_adam_dense(real* __restrict__ w, real* __restrict__ m, real* _
 
 // ------------------------------------------------------------------ host side
 static size_t fwd_smem(int n_in, int N, int Win, int Wh) {
-    return (size_t)(N + 64) * 8 + 32 * 8 + (size_t)(n_in + N + 1) * 4 + (size_t)(n_in + N) * 4 * 2 + 8 +
+    return (size_t)(N + 64) * 8 + (size_t)(n_in + N + 1) * 4 + (size_t)(n_in + N) * 4 * 2 + 8 +
            (size_t)(Win + 2 * Wh) * 4;
 }
 
@@ -795,15 +809,134 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     SNN_REQUIRE(smem <= 227 * 1024, "snn_step_neurons: n_in = %d, N = %d need %zu bytes of shared memory (max 227 KB)",
                 d.n_in, d.N, smem);
     switch (c->fwd_threads) {
-        case 128: return launch_forward_th<real, 128>(p, bt->B, smem, s);
-        case 512: return launch_forward_th<real, 512>(p, bt->B, smem, s);
-        default: return launch_forward_th<real, 256>(p, bt->B, smem, s);
+        case 128: st = launch_forward_th<real, 128>(p, bt->B, smem, s); break;
+        case 512: st = launch_forward_th<real, 512>(p, bt->B, smem, s); break;
+        default: st = launch_forward_th<real, 256>(p, bt->B, smem, s); break;
+    }
+    if (st != SNN_OK || !bt->d_rec) return st;
+    const long long n = (long long)bt->B * n_steps;
+    k_softmax_d<real><<<ceil_div(n, 256), 256, 0, s>>>((real*)bt->d_rec, bt->labels, d.n_classes, bt->trial_T, bt->B,
+                                                       bt->T, d.K, t0, n_steps);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+// Packed FP32 pairs (Blackwell f32x2 arithmetic; each half is rounded exactly like the
+// scalar operation).  Low half = first value.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float f2_lo(unsigned long long a) { return __uint_as_float((unsigned)a); }
+__device__ __forceinline__ float f2_hi(unsigned long long a) { return __uint_as_float((unsigned)(a >> 32)); }
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// FP32 adjoint scan with two neurons per thread (N even): the same recurrences as
+// k_backward on neuron pairs (2 jp, 2 jp + 1) in packed f32x2 arithmetic, psi and delta
+// moved as 8-byte pairs.  lam of each neuron is summed over readout pairs (k, k + 1)
+// with one packed FMA per pair: lam = (sum over even k) + (sum over odd k).
+constexpr int BWD2_TCH = 4;    // steps per chunk of the packed kernel
+
+template <int KV>
+__global__ void __launch_bounds__(BWD_THREADS)
+    k_backward_x2(const float* __restrict__ psi, const float* __restrict__ Dg, const float* __restrict__ W_out,
+                  float* __restrict__ delta, int T, int N, int K, float alpha, float rho, float beta) {
+    constexpr int KP = 4 * KV;
+    __shared__ __align__(16) float D_s[2][BWD2_TCH][KP];
+    const int tid = threadIdx.x;
+    const int jp = blockIdx.x * BWD_THREADS + tid;     // neuron pair
+    const int N2 = N >> 1;
+    const int b = blockIdx.y;
+    const bool ok = jp < N2;
+    unsigned long long wa[KP / 2], wb[KP / 2];         // (W[2m][j], W[2m+1][j]) for j = 2 jp, 2 jp + 1
+#pragma unroll
+    for (int m = 0; m < KP / 2; ++m) {
+        const int k0 = 2 * m, k1 = 2 * m + 1;
+        const float a0 = (k0 < K && ok) ? W_out[(size_t)k0 * N + 2 * jp] : 0.f;
+        const float a1 = (k1 < K && ok) ? W_out[(size_t)k1 * N + 2 * jp] : 0.f;
+        const float b0 = (k0 < K && ok) ? W_out[(size_t)k0 * N + 2 * jp + 1] : 0.f;
+        const float b1 = (k1 < K && ok) ? W_out[(size_t)k1 * N + 2 * jp + 1] : 0.f;
+        wa[m] = f2_pack(a0, a1);
+        wb[m] = f2_pack(b0, b1);
+    }
+    const unsigned long long* pb = (const unsigned long long*)psi + (size_t)b * T * N2 + (ok ? jp : 0);
+    const float* Db = Dg + (size_t)b * T * KP;
+    unsigned long long* db = (unsigned long long*)delta + (size_t)b * T * N2 + (ok ? jp : 0);
+    const int n_chunks = (T + BWD2_TCH - 1) / BWD2_TCH;
+    unsigned long long pcur[BWD2_TCH], pnext[BWD2_TCH];
+    auto load_chunk = [&](int ch, unsigned long long (&dst)[BWD2_TCH], int buf) {
+        const int tb = ch * BWD2_TCH, nt = min(BWD2_TCH, T - tb);
+#pragma unroll
+        for (int r = 0; r < BWD2_TCH; ++r) dst[r] = (r < nt && ok) ? pb[(size_t)(tb + r) * N2] : 0ull;
+        for (int idx = tid; idx < nt * KP; idx += BWD_THREADS) D_s[buf][idx / KP][idx % KP] = Db[(size_t)tb * KP + idx];
+    };
+    const unsigned long long alpha2 = f2_pack(alpha, alpha), beta2 = f2_pack(beta, beta);
+    const unsigned long long rho2 = f2_pack(rho, rho), nbeta2 = f2_pack(-beta, -beta);
+    load_chunk(n_chunks - 1, pcur, (n_chunks - 1) & 1);
+    __syncthreads();
+    unsigned long long lam_next = 0, psi_next = 0, mu = 0, h_next = 0, dl = 0;
+    for (int ch = n_chunks - 1; ch >= 0; --ch) {
+        const int tb = ch * BWD2_TCH, nt = min(BWD2_TCH, T - tb);
+        const int buf = ch & 1;
+        if (ch > 0) load_chunk(ch - 1, pnext, buf ^ 1);
+#pragma unroll
+        for (int r = BWD2_TCH - 1; r >= 0; --r) {
+            if (r < nt) {
+                const int t = tb + r;
+                const unsigned long long ps = pcur[r];
+                const unsigned long long* Dr = (const unsigned long long*)D_s[buf][r];
+                unsigned long long sa = 0, sb = 0;
+#pragma unroll
+                for (int m = 0; m < KP / 2; ++m) {
+                    const unsigned long long dk = Dr[m];           // (D_2m, D_2m+1)
+                    sa = f2_fma(wa[m], dk, sa);
+                    sb = f2_fma(wb[m], dk, sb);
+                }
+                const unsigned long long lam = f2_pack(f2_lo(sa) + f2_hi(sa), f2_lo(sb) + f2_hi(sb));
+                if (t == T - 1) {
+                    mu = 0;
+                    dl = 0;
+                } else {
+                    // mu = beta lam' psi' + (rho - beta psi') mu ;  delta = h' + alpha delta'
+                    mu = f2_fma(beta2, f2_mul(lam_next, psi_next), f2_mul(f2_fma(nbeta2, psi_next, rho2), mu));
+                    dl = f2_fma(alpha2, dl, h_next);
+                }
+                const unsigned long long h = f2_mul(ps, f2_sub(lam, mu));
+                if (ok) db[(size_t)t * N2] = dl;
+                h_next = h;
+                lam_next = lam;
+                psi_next = ps;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < BWD2_TCH; ++r) pcur[r] = pnext[r];
+        __syncthreads();
     }
 }
 
 template <typename real, int KV>
 static void launch_backward(const snn_classifier* c, const snn_batch* bt, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
+    if (std::is_same<real, float>::value && d.N % 2 == 0) {
+        dim3 g(ceil_div(d.N / 2, BWD_THREADS), bt->B);
+        k_backward_x2<KV><<<g, BWD_THREADS, 0, s>>>((const float*)bt->psi_rec, (const float*)bt->Dout,
+                                                     (const float*)d.W_out, (float*)bt->delta, bt->T, d.N, d.K,
+                                                     (float)c->alpha, (float)c->rho, (float)d.beta);
+        return;
+    }
     dim3 g(ceil_div(d.N, BWD_THREADS), bt->B);
     k_backward<real, KV><<<g, BWD_THREADS, 0, s>>>((const real*)bt->psi_rec, (const real*)bt->Dout,
                                                    (const real*)d.W_out, (real*)bt->delta, bt->T, d.N, d.K,
