@@ -30,10 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # library kernels per training batch: forward call 4 (k_input, k_pack, k_forward,
-# k_softmax_d), gradient 7 (k_readout_scan, k_reduce_gb, k_backward, k_gather,
-# k_reduce_ragged x2, k_reduce_out), Adam 4 (k_adam_ragged x2, k_adam_dense x2),
-# DEEP R 6 (eliminate, distribute, form per projection)
-LAUNCHES_PER_BATCH = 21
+# k_softmax_d), gradient 9 (k_readout_scan, k_backward_x2, k_reduce_gb, k_sort_rows x2,
+# k_gather, k_reduce_ragged x2, k_reduce_out), Adam 4 (k_adam_ragged x2, k_adam_dense
+# x2), DEEP R 6 (eliminate, distribute, form per projection)
+LAUNCHES_PER_BATCH = 23
 METRIC = "e-prop+DEEP R training samples/s"
 UNIT = "samples/s"
 WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}

@@ -498,6 +498,30 @@ __global__ void __launch_bounds__(BWD_THREADS)
     }
 }
 
+// Gather order of a ragged row: its live slots as keys (target << 11) | slot, sorted
+// ascending (targets are distinct within a row).  With sorted targets the 32 lanes of
+// one gather chunk read a narrow band of the adjoint row, so the chunks of one spike
+// event touch few 32-byte sectors more than once.  Warp per row, rank by counting;
+// blockDim.x / 32 warps per CTA, each with a C-word shared-memory row.
+__global__ void __launch_bounds__(256)
+    k_sort_rows(const int32_t* __restrict__ len, const int32_t* __restrict__ ind, int P, int C,
+                int32_t* __restrict__ keys) {
+    extern __shared__ int32_t sk[];                  // [warps][C]
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= P) return;
+    int32_t* row = sk + (size_t)warp * C;
+    const int n = len[i];
+    for (int s = lane; s < n; s += 32) row[s] = (ind[(size_t)i * C + s] << 11) | s;
+    __syncwarp();
+    for (int s = lane; s < n; s += 32) {
+        const int32_t key = row[s];
+        int rank = 0;
+        for (int e = 0; e < n; ++e) rank += row[e] < key ? 1 : 0;
+        keys[(size_t)i * C + rank] = key;
+    }
+}
+
 // Gather: grid (spike-word columns x 32 / ROWS, KS, slot groups).  CTA = ROWS presynaptic
 // rows of one bit word (input words first, then hidden words) for one group of 128 slots;
 // one warp per row, 4 slot chunks per lane.  The CTA stages the spike words of its whole
@@ -513,8 +537,8 @@ constexpr int GATHER_EV = 4;      // spike events whose loads are issued togethe
 template <typename real, int ROWS, int EV>
 __global__ void __launch_bounds__(ROWS * 32, 1)
     k_gather(const uint32_t* __restrict__ x_rec, const uint32_t* __restrict__ z_rec, int Win, int Wh,
-             const int32_t* __restrict__ in_len, const int32_t* __restrict__ in_ind, int in_C, int n_in,
-             const int32_t* __restrict__ rec_len, const int32_t* __restrict__ rec_ind, int rec_C, int N,
+             const int32_t* __restrict__ in_len, const int32_t* __restrict__ in_keys, int in_C, int n_in,
+             const int32_t* __restrict__ rec_len, const int32_t* __restrict__ rec_keys, int rec_C, int N,
              const real* __restrict__ delta, const real* __restrict__ D, int K, int Kp, long long BT,
              long long bt_per, real* __restrict__ part_in, real* __restrict__ part_rec,
              real* __restrict__ part_out) {
@@ -544,14 +568,14 @@ __global__ void __launch_bounds__(ROWS * 32, 1)
         const long long my = bt0 + k;
         words[k] = (my < bt1) ? bits[my * W + wi] : 0u;
     }
-    const int32_t* ri = (is_in ? in_ind : rec_ind) + (size_t)(row_ok ? i : 0) * C;
+    const int32_t* rk = (is_in ? in_keys : rec_keys) + (size_t)(row_ok ? i : 0) * C;
     const int nq = len > s_base ? min(4, (len - s_base + 31) >> 5) : 0;   // warp-uniform
-    int tgt[4];
+    int key[4];                                     // (target << 11) | slot, or -1
     real acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int s = s_base + q * 32 + lane;
-        tgt[q] = (q < nq && s < len) ? ri[s] : -1;
+        key[q] = (q < nq && s < len) ? rk[s] : -1;
         acc[q] = 0;
     }
     real acc_o = 0;
@@ -587,7 +611,7 @@ __global__ void __launch_bounds__(ROWS * 32, 1)
             const real* rowp = delta0 + (size_t)off[k] * N;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                v[k][q] = (k < nv && q < nq && tgt[q] >= 0) ? rowp[tgt[q]] : real(0);
+                v[k][q] = (k < nv && q < nq && key[q] >= 0) ? rowp[key[q] >> 11] : real(0);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -608,7 +632,7 @@ __global__ void __launch_bounds__(ROWS * 32, 1)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int s = s_base + q * 32 + lane;
-        if (q < nq && s < len) part[((size_t)ks * P + i) * C + s] = acc[q];
+        if (q < nq && s < len) part[((size_t)ks * P + i) * C + (key[q] & 2047)] = acc[q];
     }
     if (do_out) part_out[((size_t)ks * N + i) * K + lane] = acc_o;
 }
@@ -972,10 +996,19 @@ static snn_status grad_impl(snn_classifier* c, const snn_batch* bt, cudaStream_t
     const snn_ragged_desc& ri = d.w_in->d;
     const snn_ragged_desc& rr = d.w_rec->d;
     const int Cmax = ri.C > rr.C ? ri.C : rr.C;
+    int32_t* keys_in = c->gkeys;
+    int32_t* keys_rec = c->gkeys + (size_t)ri.P * ri.C;
+    for (int m = 0; m < 2; ++m) {
+        const snn_ragged_desc& rd = m == 0 ? ri : rr;
+        const int sw = rd.C <= 1536 ? 8 : 6;       // warps per CTA: at most 48 KB of rows
+        k_sort_rows<<<ceil_div(rd.P, sw), sw * 32, (size_t)sw * rd.C * 4, s>>>(rd.row_len, rd.ind, rd.P, rd.C,
+                                                                                  m == 0 ? keys_in : keys_rec);
+        SNN_LAUNCH_CHECK();
+    }
     dim3 gg((Win + Wh) * (32 / GATHER_ROWS), KS, (Cmax + 127) / 128);
     k_gather<real, GATHER_ROWS, GATHER_EV><<<gg, GATHER_ROWS * 32, 0, s>>>(
-        bt->x_rec, bt->z_rec, Win, Wh, ri.row_len, ri.ind, ri.C, d.n_in,
-        rr.row_len, rr.ind, rr.C, N, (const real*)bt->delta, (const real*)bt->Dout, K, Kp, BT, bt_per,
+        bt->x_rec, bt->z_rec, Win, Wh, ri.row_len, keys_in, ri.C, d.n_in,
+        rr.row_len, keys_rec, rr.C, N, (const real*)bt->delta, (const real*)bt->Dout, K, Kp, BT, bt_per,
         (real*)c->part_in, (real*)c->part_rec, (real*)c->part_out);
     SNN_LAUNCH_CHECK();
     k_reduce_ragged<real><<<ceil_div((long long)ri.P * ri.C, 256), 256, 0, s>>>((const real*)c->part_in, ri.row_len,
@@ -1060,6 +1093,8 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     if (e == cudaSuccess) e = cudaMalloc(&c->part_rec, n_rec_part);
     if (e == cudaSuccess) e = cudaMalloc(&c->part_out, n_out_part);
     if (e == cudaSuccess) e = cudaMalloc(&c->pk, (size_t)(d->n_in + d->N) * c->Cf * 8);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->gkeys, ((size_t)d->w_in->d.P * d->w_in->d.C + (size_t)d->w_rec->d.P * d->w_rec->d.C) * 4);
     if (e != cudaSuccess) {
         snn_destroy_classifier(c);
         set_error("snn_create_classifier: cudaMalloc failed: %s", cudaGetErrorString(e));
@@ -1085,6 +1120,7 @@ snn_status snn_destroy_classifier(snn_classifier* c) {
     cudaFree(c->part_rec);
     cudaFree(c->part_out);
     cudaFree(c->pk);
+    cudaFree(c->gkeys);
     free(c);
     return SNN_OK;
 }

@@ -206,5 +206,6 @@ struct snn_classifier {
     void* part_rec;          // [KS][N*C_rec]
     void* part_out;          // [KS][N][K]
     void* pk;                // [(n_in + N) * Cf] packed forward rows (refreshed per forward call)
+    int32_t* gkeys;          // [P_in*C_in + N*C_rec] gather order: (target << 11) | slot, ascending per row
     int32_t Cf;              // slots per packed row: max(C_in, C_rec + K) rounded up to 32
 };
