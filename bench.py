@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--sample-steps", type=int, default=600, help="oracle sample: steps of one trial")
     ap.add_argument("--batch", type=int, default=512, help="trials per batch (512 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
-    ap.add_argument("--workload", default="classifier", choices=["classifier", "batched", "serve", "topo"],
+    ap.add_argument("--workload", default="classifier", choices=["classifier", "batched", "serve", "topo", "kernels"],
                     help="classifier (default, the benchmark line); batched: 64 uneven instances, plain vs "
                          "graph-batched; serve: request loop latency; topo: topographic map steps/s")
     ap.add_argument("--scale", type=int, default=2, help="topo: grid side 16*scale")
@@ -480,15 +480,102 @@ def run_topo(args):
     stats_ff, stats_lat = s_ff.cpu().tolist(), s_lat.cpu().tolist()
     return {"workload": "topo", "metric": "simulated steps/s (1 ms steps)", "L": L, "neurons_per_sheet": N,
             "steps": n, "steps_per_s": round(n / (ms / 1e3), 1), "realtime_factor": round(n / (ms / 1e3) / 1000.0, 2),
-            "ms_per_1000_steps": round(ms / n * 1000, 3), "launches_per_step": 7 + 0.2,
+            "ms_per_1000_steps": round(ms / n * 1000, 3),
+            "path": "one cluster launch per 1000 steps" if N <= 4096 else "per-step launches (sheet larger than a cluster)",
             "rewire_ff": dict(zip(["removed", "formed", "overflow", "attempts"], stats_ff)),
             "rewire_lat": dict(zip(["removed", "formed", "overflow", "attempts"], stats_lat))}
+
+
+def run_kernels(args):
+    """DEEP R rewiring and standalone ragged propagation on a 65536 x 65536 projection
+    (~287 synapses per row, 18.8 M synapses; arrays and bitfields ~1.4 GB, far larger
+    than L2): mean CUDA-event time per call after warm-up, and the algorithmic bytes of
+    each call (the survey's per-unit byte model) per second against the measured HBM
+    copy bandwidth."""
+    import torch
+    import synth
+    from paper_2510_19764_gb300 import abi, build, net
+    build.build()
+    abi.load()
+    dev = "cuda"
+    P = Q = 65536
+    k, C = 288, 320
+    rag = synth.large_ragged(args.seed, P, Q, k, C)
+    r = net.DeviceRagged(rag.row_len, rag.ind, rag.w, Q, adam=True, deepr=True, seed=args.seed + 3)
+    pk = peaks()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed)
+    slot = torch.arange(C, device=dev)[None, :]
+    stats = torch.zeros(4, dtype=torch.int64, device=dev)
+    rw = []
+    for rep in range(8):
+        # a fixed fraction of live synapses turns against its sign bit, as after an
+        # optimiser step; DEEP R removes exactly those and regrows as many elsewhere
+        live = slot < r.row_len[:, None].long()
+        flip = live & (torch.rand((P, C), generator=gen, device=dev) < 0.02) & (r.w != 0)
+        r.w[flip] = -r.w[flip]
+        first = torch.where(flip.any(1), flip.int().argmax(1), torch.full((P,), C, device=dev))
+        moved = int((live & ~flip & (slot > first[:, None])).sum())
+        active, removed = int(live.sum()), int(flip.sum())
+        len_after_elim = r.row_len.long() - flip.sum(1)
+        stats.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        abi.snn_rewire_deepr(r.handle, rep, stats)
+        b.record()
+        b.synchronize()
+        formed = int(stats[1])
+        act_rows = int((r.row_len.long() > len_after_elim).sum())
+        # elimination: 8 B per active slot + 16 B per moved slot + one bitfield word per
+        # removal; formation: 16 B per new synapse + Q/8 B bitfield row per row with activations
+        by = 8 * active + 16 * moved + 4 * removed + 16 * formed + (Q // 8) * act_rows
+        if rep >= 3:
+            rw.append((a.elapsed_time(b), by, removed + formed))
+    ms = sum(x[0] for x in rw) / len(rw)
+    by = sum(x[1] for x in rw) / len(rw)
+    nrw = sum(x[2] for x in rw) / len(rw)
+    out = {"workload": "kernels", "matrix": {"P": P, "Q": Q, "C": C, "synapses": int(r.row_len.sum())},
+           "snn_rewire_deepr": {"ms": round(ms, 4), "rewired_synapses_per_s": round(nrw / (ms / 1e3), 1),
+                                "algorithmic_bytes": int(by),
+                                "roofline": {"bound": "hbm", "achieved": round(by / (ms / 1e3) / 1e9, 1),
+                                             "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                             "frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 4),
+                                             "peak_source": pk["source"]}}}
+    # standalone propagation of B spike vectors (10 % of rows spiking) with shared weights
+    B = 16
+    spk = torch.rand((B, P), generator=gen, device=dev) < 0.1
+    shifts = torch.arange(32, device=dev, dtype=torch.int64)
+    words = (spk.view(B, P // 32, 32).long() << shifts).sum(-1)
+    pre = torch.where(words >= 2 ** 31, words - 2 ** 32, words).int().contiguous()
+    acc = torch.zeros((B, Q), dtype=torch.int64, device=dev)
+    events = int((spk.long() * r.row_len.long()[None, :]).sum())
+    spikes = int(spk.sum())
+    times = []
+    for rep in range(8):
+        acc.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        abi.snn_propagate(r.handle, pre, B, acc)
+        b.record()
+        b.synchronize()
+        if rep >= 3:
+            times.append(a.elapsed_time(b))
+    ms = sum(times) / len(times)
+    by = 8 * events + 4 * spikes
+    out["snn_propagate"] = {"ms": round(ms, 4), "instances": B, "synaptic_events": events,
+                            "synaptic_events_per_s": round(events / (ms / 1e3), 1), "algorithmic_bytes": by,
+                            "roofline": {"bound": "hbm", "achieved": round(by / (ms / 1e3) / 1e9, 1),
+                                         "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                         "frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 4),
+                                         "peak_source": pk["source"]}}
+    return out
 
 
 def main():
     args = parse()
     if args.workload != "classifier":
-        fn = {"batched": run_batched, "serve": run_serve, "topo": run_topo}[args.workload]
+        fn = {"batched": run_batched, "serve": run_serve, "topo": run_topo, "kernels": run_kernels}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return 0
     WORKLOAD["B"] = args.batch

@@ -321,7 +321,10 @@ snn_status snn_rewire_topo(snn_ragged* r, const snn_topo_rewire* p, int64_t rewi
 /* Run steps t0 .. t0+n_steps-1 of the full topographic network: input, propagation of
  * the previous step's spikes (ff and lateral), neurons, STDP on both projections and,
  * after every step with (t+1) % rewire_every == 0, snn_rewire_topo on ff then lateral
- * with rewire index (t+1)/rewire_every - 1.  Kernel launches only; no host sync. */
+ * with rewire index (t+1)/rewire_every - 1.  Runs as one thread-block-cluster launch
+ * per (up to) 1000 steps, with results identical to that sequence of per-step calls;
+ * networks too large for one cluster use the per-step launches.  No host sync except
+ * when a projection's formation-threshold table has to be (re)built. */
 snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_ragged* ff,
                         snn_ragged* lat, const snn_topo_rewire* rw_ff, const snn_topo_rewire* rw_lat,
                         uint64_t input_seed, int32_t rewire_every, int64_t t0, int32_t n_steps,

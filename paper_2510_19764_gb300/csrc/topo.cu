@@ -41,35 +41,93 @@ static TopoK topo_consts(const snn_topo_params* p) {
     return k;
 }
 
+// ---- per-step arithmetic shared by the per-call kernels and the fused step loop
+
+// Stimulus focus of step t (the same for every source channel).
+__device__ __forceinline__ void topo_focus(const TopoK& k, uint64_t seed, long long t, int& fx, int& fy) {
+    const u64x4 f = philox(seed, PH_TOPO_FOCUS, (uint64_t)(t / k.t_stim), 0, 0, 0);
+    fx = (int)mulhi_index(f.x, (uint64_t)k.L_f);
+    fy = (int)mulhi_index(f.y, (uint64_t)k.L_f);
+}
+
+// Source channels 4g .. 4g+3 of step t (one Philox block): spike bits as a nibble;
+// xs[q] is channel 4g+q's trace, updated in place.
+__device__ __forceinline__ uint32_t topo_input_group(const TopoK& k, uint64_t seed, long long t, int g, int fx,
+                                                     int fy, float (&xs)[4]) {
+    uint32_t nib = 0;
+    const u64x4 u = philox(seed, PH_TOPO_INPUT, (uint64_t)t, (uint64_t)g, 0, 0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = 4 * g + q;
+        if (c < k.N) {
+            int dx = abs((c % k.L) % k.L_f - fx);
+            int dy = abs((c / k.L) % k.L_f - fy);
+            dx = min(dx, k.L_f - dx);
+            dy = min(dy, k.L_f - dy);
+            const uint64_t thr = (dx * dx + dy * dy <= k.radius2) ? k.thr_in : k.thr_base;
+            const bool s = u[q] < thr;
+            if (s) nib |= 1u << q;
+            xs[q] = xs[q] * k.dplus + (s ? 1.0f : 0.0f);
+        }
+    }
+    return nib;
+}
+
+// One conductance-LIF neuron step: g decays and takes the summed input I, then either a
+// refractory hold or exponential Euler with g held over the step; traces y (ydec = its
+// decayed value before the spike) and x.  Returns the spike.
+__device__ __forceinline__ bool topo_neuron(const TopoK& k, float I, float& gs, float& V, int& ref, float& y,
+                                            float& ydec, float& x) {
+    bool z = false;
+    const float g = gs * k.ds + I;
+    gs = g;
+    float v = V;
+    if (ref > 0) {
+        v = k.V_reset;
+        ref = ref - 1;
+    } else {
+        const float geff = g / k.g_leak;
+        const float vinf = (k.V_rest + geff * k.E_exc) / (1.0f + geff);
+        v = vinf + (v - vinf) * expf(-k.dt_over_tau_m * (1.0f + geff));
+        if (v >= k.V_theta) {
+            z = true;
+            v = k.V_reset;
+            ref = k.n_ref;
+        }
+    }
+    V = v;
+    ydec = y * k.dminus;
+    y = ydec + (z ? 1.0f : 0.0f);
+    x = x * k.dplus + (z ? 1.0f : 0.0f);
+    return z;
+}
+
+// STDP on one synapse: depression by the postsynaptic trace if the row's neuron spiked,
+// then potentiation by the presynaptic trace if the target spiked; clamped to [0, g_max].
+__device__ __forceinline__ float stdp_slot(float g, bool pre, bool post, float yd, float xp, float A_plus,
+                                           float A_minus, float g_max) {
+    if (pre) g = fmaxf(0.0f, g - A_minus * yd);
+    if (post) g = fminf(g_max, g + A_plus * xp);
+    return g;
+}
+
 // Thread = 4 source channels (one Philox block); nibbles of 8 lanes form one word.
 __global__ void k_topo_input(TopoK k, uint64_t seed, long long t, uint32_t* __restrict__ bits,
                              float* __restrict__ x_src) {
     __shared__ int focus[2];
-    if (threadIdx.x == 0) {
-        const u64x4 f = philox(seed, PH_TOPO_FOCUS, (uint64_t)(t / k.t_stim), 0, 0, 0);
-        focus[0] = (int)mulhi_index(f.x, (uint64_t)k.L_f);
-        focus[1] = (int)mulhi_index(f.y, (uint64_t)k.L_f);
-    }
+    if (threadIdx.x == 0) topo_focus(k, seed, t, focus[0], focus[1]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int n_groups = (k.N + 3) >> 2;
     uint32_t nib = 0;
     if (g < n_groups) {
-        const u64x4 u = philox(seed, PH_TOPO_INPUT, (uint64_t)t, (uint64_t)g, 0, 0);
+        float xs[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c = 4 * g + q;
-            if (c < k.N) {
-                int dx = abs((c % k.L) % k.L_f - focus[0]);
-                int dy = abs((c / k.L) % k.L_f - focus[1]);
-                dx = min(dx, k.L_f - dx);
-                dy = min(dy, k.L_f - dy);
-                const uint64_t thr = (dx * dx + dy * dy <= k.radius2) ? k.thr_in : k.thr_base;
-                const bool s = u[q] < thr;
-                if (s) nib |= 1u << q;
-                x_src[c] = x_src[c] * k.dplus + (s ? 1.0f : 0.0f);
-            }
-        }
+        for (int q = 0; q < 4; ++q) xs[q] = 4 * g + q < k.N ? x_src[4 * g + q] : 0.0f;
+        nib = topo_input_group(k, seed, t, g, focus[0], focus[1], xs);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * g + q < k.N) x_src[4 * g + q] = xs[q];
     }
     uint32_t word = nib << (4 * (g & 7));
     word |= __shfl_xor_sync(0xffffffffu, word, 1);
@@ -86,28 +144,15 @@ __global__ void k_topo_neurons(TopoK k, float* __restrict__ V, float* __restrict
     if (j < k.N) {
         const float I = from_fixed<float>(acc[j]);
         acc[j] = 0;
-        const float g = gs[j] * k.ds + I;
-        gs[j] = g;
-        float v = V[j];
+        float g = gs[j], v = V[j], yy = y[j], yd, x = x_tgt[j];
         int r = ref[j];
-        if (r > 0) {
-            v = k.V_reset;
-            ref[j] = r - 1;
-        } else {
-            const float geff = g / k.g_leak;
-            const float vinf = (k.V_rest + geff * k.E_exc) / (1.0f + geff);
-            v = vinf + (v - vinf) * expf(-k.dt_over_tau_m * (1.0f + geff));
-            if (v >= k.V_theta) {
-                z = true;
-                v = k.V_reset;
-                ref[j] = k.n_ref;
-            }
-        }
+        z = topo_neuron(k, I, g, v, r, yy, yd, x);
+        gs[j] = g;
         V[j] = v;
-        const float yd = y[j] * k.dminus;
+        ref[j] = r;
+        y[j] = yy;
         ydec[j] = yd;
-        y[j] = yd + (z ? 1.0f : 0.0f);
-        x_tgt[j] = x_tgt[j] * k.dplus + (z ? 1.0f : 0.0f);
+        x_tgt[j] = x;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, z);
     if ((threadIdx.x & 31) == 0 && (j >> 5) < k.Nw) bits[j >> 5] = m;
@@ -129,10 +174,7 @@ __global__ void k_stdp(const int32_t* __restrict__ len, const int32_t* __restric
         const int j = ind[o];
         const bool post = (post_bits[j >> 5] >> (j & 31)) & 1u;
         if (!pre && !post) continue;
-        float g = w[o];
-        if (pre) g = fmaxf(0.0f, g - A_minus * ydec[j]);
-        if (post) g = fminf(g_max, g + A_plus * xp);
-        w[o] = g;
+        w[o] = stdp_slot(w[o], pre, post, pre ? ydec[j] : 0.0f, xp, A_plus, A_minus, g_max);
     }
 }
 
@@ -153,11 +195,11 @@ __device__ __forceinline__ int torus_d2(int i, int j, int L) {
 // One CTA.  Histogram of attempt rows, then one warp per row with attempts: candidate
 // selection without replacement in a warp-private shared-memory bitfield, stable
 // elimination by ballot compaction, and formation of the remaining candidates in
-// ascending target order.
-__global__ void __launch_bounds__(1024)
-    k_topo_rewire(RewireK k, int32_t* __restrict__ len, int32_t* __restrict__ ind, float* __restrict__ w,
-                  const uint64_t* __restrict__ thr_form, int32_t* status, snn_rewire_stats* stats) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// ascending target order.  Row data are read through L2 (ld.global.cg): inside the
+// fused step loop other CTAs of the cluster write them between calls.
+__device__ void topo_rewire_cta(const RewireK& k, int32_t* __restrict__ len, int32_t* __restrict__ ind,
+                                float* __restrict__ w, const uint64_t* __restrict__ thr_form, int32_t* status,
+                                snn_rewire_stats* stats, unsigned char* smem) {
     int* att = (int*)smem;                       // [P]
     int* list = att + k.P;                       // [n_att]
     int* n_rows = list + k.n_att;                // [1]
@@ -215,7 +257,7 @@ __global__ void __launch_bounds__(1024)
             __syncwarp();
         }
         // elimination of existing synapses on candidates
-        const int n = len[i];
+        const int n = __ldcg(len + i);
         const size_t row = (size_t)i * k.C;
         int wp = 0;
         for (int base = 0; base < n; base += 32) {
@@ -225,8 +267,8 @@ __global__ void __launch_bounds__(1024)
             float g = 0.0f;
             bool is_c = false, rm = false;
             if (valid) {
-                j = ind[row + s];
-                g = w[row + s];
+                j = __ldcg(ind + row + s);
+                g = __ldcg(w + row + s);
                 is_c = (cand[j >> 5] >> (j & 31)) & 1u;
                 if (is_c) {
                     const u64x4 u = philox(k.seed, PH_TOPO_DRAW, k.rewire, (uint64_t)i, (uint64_t)j, 0);
@@ -291,6 +333,17 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+__global__ void __launch_bounds__(1024)
+    k_topo_rewire(RewireK k, int32_t* __restrict__ len, int32_t* __restrict__ ind, float* __restrict__ w,
+                  const uint64_t* __restrict__ thr_form, int32_t* status, snn_rewire_stats* stats) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    topo_rewire_cta(k, len, ind, w, thr_form, status, stats, smem);
+}
+
+static size_t rewire_smem(int P, int n_att, int Qw, int threads) {
+    return (size_t)(P + n_att + 1) * 4 + (size_t)(threads / 32) * Qw * 4;
+}
+
 static snn_status check_topo(const snn_topo_params* p) {
     SNN_REQUIRE(p, "topo: NULL parameters");
     SNN_REQUIRE(p->L > 0 && p->L_f > 0 && p->L % p->L_f == 0, "topo: need L > 0 and L a multiple of L_f");
@@ -299,8 +352,9 @@ static snn_status check_topo(const snn_topo_params* p) {
     return SNN_OK;
 }
 
-static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t rewire_idx, snn_rewire_stats* stats,
-                                cudaStream_t s) {
+// Validates one projection's rewiring parameters, refreshes its formation-threshold
+// table when they changed and fills the kernel constants (rewire index left at 0).
+static snn_status rewire_prepare(snn_ragged* r, const snn_topo_rewire* p, RewireK& k, cudaStream_t s) {
     const snn_ragged_desc& d = r->d;
     SNN_REQUIRE(d.dtype == SNN_F32, "snn_rewire_topo: F32 ragged matrices only");
     SNN_REQUIRE(p->L > 0 && (long long)p->L * p->L == d.Q && d.P == d.Q,
@@ -321,7 +375,6 @@ static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t
         r->thr_p = p->p_form;
         r->thr_sigma = p->sigma;
     }
-    RewireK k;
     k.P = d.P;
     k.Q = d.Q;
     k.C = d.C;
@@ -333,14 +386,276 @@ static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t
     k.thr_dep = prob_threshold(p->p_elim_dep);
     k.thr_pot = prob_threshold(p->p_elim_pot);
     k.seed = d.seed;
+    k.rewire = 0;
+    SNN_REQUIRE(rewire_smem(k.P, k.n_att, k.Qw, 1024) <= 227 * 1024, "snn_rewire_topo: P = %d too large for one CTA",
+                k.P);
+    return SNN_OK;
+}
+
+static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t rewire_idx, snn_rewire_stats* stats,
+                                cudaStream_t s) {
+    RewireK k;
+    const snn_status e = rewire_prepare(r, p, k, s);
+    if (e != SNN_OK) return e;
     k.rewire = (uint64_t)rewire_idx;
+    const snn_ragged_desc& d = r->d;
     const int threads = 1024;
-    size_t smem = (size_t)(k.P + k.n_att + 1) * 4 + (size_t)(threads / 32) * k.Qw * 4;
-    SNN_REQUIRE(smem <= 227 * 1024, "snn_rewire_topo: P = %d too large for one CTA", k.P);
+    const size_t smem = rewire_smem(k.P, k.n_att, k.Qw, threads);
     if (smem > 48 * 1024)
         SNN_CUDA(cudaFuncSetAttribute(k_topo_rewire, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_topo_rewire<<<1, threads, smem, s>>>(k, d.row_len, d.ind, (float*)d.w, r->thr_form, r->status, stats);
     SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+// ---- fused step loop: the whole network in one thread-block cluster
+//
+// One cluster of CS CTAs x FUSED_THREADS threads runs many steps in one launch.  Global
+// thread j owns target neuron j (and j + CS*FUSED_THREADS ...) with V, g, refractory count and y in
+// registers; thread g < ceil(N/4) owns source channels 4g..4g+3 and their traces.  Per
+// step, separated by cluster barriers (release/acquire; cross-CTA data are read through
+// L2 with ld.global.cg):
+//   A. input of step t; propagation of step t-1's source and target spikes (warp per
+//      bit word, exact int64 fixed-point atomics into acc)
+//   B. neurons of step t (acc consumed), spike words, traces x_tgt, ydec
+//   C. STDP on both projections (warp per row, the step's spike words staged in shared
+//      memory); after steps with (t+1) % every == 0, CTA 0 rewires ff and CTA 1 lateral.
+// The arithmetic is the per-call kernels' (shared device functions), so results are
+// identical to the sequence of per-call launches.
+struct TopoRun {
+    TopoK k;
+    int32_t* len[2];      // ff, lateral
+    int32_t* ind[2];
+    float* w[2];
+    int C[2];
+    float *V, *gs, *x_src, *x_tgt, *y, *ydec;
+    int32_t* ref;
+    unsigned long long* acc;
+    uint32_t *src_bits, *tgt_bits;
+    uint64_t in_seed;
+    long long t0;
+    int n_steps, rewire_every;
+    RewireK rk[2];
+    const uint64_t* thr[2];
+    int32_t* status[2];
+    snn_rewire_stats* stats[2];
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+constexpr int FUSED_THREADS = 512;
+
+template <int NPT>
+__global__ void __launch_bounds__(FUSED_THREADS, 1) k_topo_fused(TopoRun r) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TopoK& k = r.k;
+    const int N = k.N, Nw = k.Nw;
+    const int TT = gridDim.x * blockDim.x;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = gt >> 5, nwarps = TT >> 5;
+    uint32_t* sb_src = (uint32_t*)smem;           // [Nw] spike words of the step (STDP)
+    uint32_t* sb_tgt = sb_src + Nw;               // [Nw]
+    float V[NPT], gs[NPT], y[NPT], xt[NPT];
+    int ref[NPT];
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        const int j = gt + q * TT;
+        const bool ok = j < N;
+        V[q] = ok ? r.V[j] : 0.0f;
+        gs[q] = ok ? r.gs[j] : 0.0f;
+        y[q] = ok ? r.y[j] : 0.0f;
+        xt[q] = ok ? r.x_tgt[j] : 0.0f;
+        ref[q] = ok ? r.ref[j] : 0;
+    }
+    const int Ng = (N + 3) >> 2;
+    const bool has_group = gt < Ng;
+    float xs[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xs[q] = (has_group && 4 * gt + q < N) ? r.x_src[4 * gt + q] : 0.0f;
+    long long fper = -1;
+    int fx = 0, fy = 0;
+    for (long long t = r.t0; t < r.t0 + r.n_steps; ++t) {
+        const int cur = (int)(t & 1), prv = cur ^ 1;
+        // ---------------- A: input of step t, propagation of step t-1
+        {
+            uint32_t nib = 0;
+            if (has_group) {
+                if (t / k.t_stim != fper) {
+                    fper = t / k.t_stim;
+                    topo_focus(k, r.in_seed, t, fx, fy);
+                }
+                nib = topo_input_group(k, r.in_seed, t, gt, fx, fy, xs);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (4 * gt + q < N) r.x_src[4 * gt + q] = xs[q];
+            }
+            uint32_t word = nib << (4 * (gt & 7));
+            word |= __shfl_xor_sync(0xffffffffu, word, 1);
+            word |= __shfl_xor_sync(0xffffffffu, word, 2);
+            word |= __shfl_xor_sync(0xffffffffu, word, 4);
+            if ((gt & 7) == 0 && (gt >> 3) < Nw) r.src_bits[cur * Nw + (gt >> 3)] = word;
+        }
+        for (int wd = gwarp; wd < 2 * Nw; wd += nwarps) {
+            const int m = wd < Nw ? 0 : 1;            // 0: ff rows (source spikes), 1: lateral
+            const int wi = wd - m * Nw;
+            uint32_t bits = __ldcg((m == 0 ? r.src_bits : r.tgt_bits) + prv * Nw + wi);
+            const int32_t* ind = r.ind[m];
+            const float* wt = r.w[m];
+            const int C = r.C[m];
+            // lengths of all spiking rows of the word in one round trip
+            const int n_l = ((bits >> lane) & 1u) ? __ldcg(r.len[m] + wi * 32 + lane) : 0;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                const int i = wi * 32 + b;
+                bits &= bits - 1u;
+                const int n = __shfl_sync(0xffffffffu, n_l, b);
+                for (int s = lane; s < n; s += 32) {
+                    const size_t o = (size_t)i * C + s;
+                    atomicAdd(r.acc + __ldcg(ind + o), (unsigned long long)to_fixed(__ldcg(wt + o)));
+                }
+            }
+        }
+        cluster_barrier();
+        // ---------------- B: neurons of step t
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            const int j = gt + q * TT;
+            bool z = false;
+            if (j < N) {
+                const float I = from_fixed<float>((long long)__ldcg(r.acc + j));
+                r.acc[j] = 0ull;
+                float yd;
+                z = topo_neuron(k, I, gs[q], V[q], ref[q], y[q], yd, xt[q]);
+                r.ydec[j] = yd;
+                r.x_tgt[j] = xt[q];
+            }
+            const uint32_t zm = __ballot_sync(0xffffffffu, z);
+            const int j0 = j - lane;                  // the warp's first neuron
+            if (lane == 0 && (j0 >> 5) < Nw) r.tgt_bits[cur * Nw + (j0 >> 5)] = zm;
+        }
+        cluster_barrier();
+        // ---------------- C: STDP of step t, then rewiring
+        for (int wi = threadIdx.x; wi < Nw; wi += blockDim.x) {
+            sb_src[wi] = __ldcg(r.src_bits + cur * Nw + wi);
+            sb_tgt[wi] = __ldcg(r.tgt_bits + cur * Nw + wi);
+        }
+        __syncthreads();
+        // warp = batches of 8 rows whose loads are issued together (3 L2 round trips per
+        // 32-slot chunk of the batch instead of per row)
+        for (int rb = gwarp * 8; rb < 2 * N; rb += nwarps * 8) {
+            int n_l = 0;
+            float xp_l = 0.0f;
+            bool pre_l = false;
+            if (lane < 8 && rb + lane < 2 * N) {
+                const int row = rb + lane, m = row < N ? 0 : 1, i = row - m * N;
+                n_l = __ldcg(r.len[m] + i);
+                xp_l = __ldcg((m == 0 ? r.x_src : r.x_tgt) + i);
+                pre_l = ((m == 0 ? sb_src : sb_tgt)[i >> 5] >> (i & 31)) & 1u;
+            }
+            int nq[8], nmax = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                nq[q] = __shfl_sync(0xffffffffu, n_l, q);
+                nmax = max(nmax, nq[q]);
+            }
+            for (int s0 = 0; s0 < nmax; s0 += 32) {
+                int j[8];
+                size_t o[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int row = rb + q, m = row < N ? 0 : 1, i = row - m * N;
+                    o[q] = (size_t)i * r.C[m] + s0 + lane;
+                    j[q] = s0 + lane < nq[q] ? __ldcg(r.ind[m] + o[q]) : -1;
+                }
+                float g[8], yd[8];
+                bool pre[8], post[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int row = rb + q, m = row < N ? 0 : 1;
+                    pre[q] = __shfl_sync(0xffffffffu, pre_l, q);
+                    post[q] = j[q] >= 0 && ((sb_tgt[j[q] >> 5] >> (j[q] & 31)) & 1u);
+                    const bool upd = j[q] >= 0 && (pre[q] || post[q]);
+                    g[q] = upd ? __ldcg(r.w[m] + o[q]) : 0.0f;
+                    yd[q] = (upd && pre[q]) ? __ldcg(r.ydec + j[q]) : 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int row = rb + q, m = row < N ? 0 : 1;
+                    const float xp = __shfl_sync(0xffffffffu, xp_l, q);
+                    if (j[q] >= 0 && (pre[q] || post[q]))
+                        r.w[m][o[q]] = stdp_slot(g[q], pre[q], post[q], yd[q], xp, k.A_plus, k.A_minus, k.g_max);
+                }
+            }
+        }
+        if ((t + 1) % r.rewire_every == 0) {
+            cluster_barrier();
+            if (blockIdx.x < 2) {
+                const int m = blockIdx.x;
+                RewireK rk = r.rk[m];
+                rk.rewire = (uint64_t)((t + 1) / r.rewire_every - 1);
+                topo_rewire_cta(rk, r.len[m], r.ind[m], r.w[m], r.thr[m], r.status[m], r.stats[m], smem);
+            }
+        }
+        cluster_barrier();
+    }
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        const int j = gt + q * TT;
+        if (j < N) {
+            r.V[j] = V[q];
+            r.gs[j] = gs[q];
+            r.y[j] = y[q];
+            r.ref[j] = ref[q];
+        }
+    }
+}
+
+// Cluster size for the fused loop: the largest of 16 / 8 / 4 / 2 CTAs that can be
+// resident (0 if none).
+template <int NPT>
+static int fused_cluster_size(size_t smem, cudaStream_t s) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_topo_fused<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    cudaFuncSetAttribute(k_topo_fused<NPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cs = 16; cs >= 2; cs /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(FUSED_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_topo_fused<NPT>, &cfg) == cudaSuccess && n >= 1) return cs;
+    }
+    cudaGetLastError();
+    return 0;
+}
+
+template <int NPT>
+static snn_status launch_fused(const TopoRun& run, int cs, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(FUSED_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    SNN_CUDA(cudaLaunchKernelEx(&cfg, k_topo_fused<NPT>, run));
     return SNN_OK;
 }
 
@@ -410,6 +725,53 @@ snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_
     const int N = p->L * p->L, Nw = (N + 31) / 32;
     SNN_REQUIRE(ff->d.P == N && ff->d.Q == N && lat->d.P == N && lat->d.Q == N,
                 "snn_topo_run: projections must be N x N with N = L*L");
+    if (n_steps == 0) return SNN_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // fused path: one cluster launch per (up to) 1000 steps
+    if (ff->d.dtype == SNN_F32 && lat->d.dtype == SNN_F32 && st->V && st->gs && st->ref && st->x_src && st->x_tgt &&
+        st->y && st->ydec && st->acc && st->src_bits && st->tgt_bits) {
+        TopoRun run;
+        if ((e = rewire_prepare(ff, rw_ff, run.rk[0], s)) != SNN_OK) return e;
+        if ((e = rewire_prepare(lat, rw_lat, run.rk[1], s)) != SNN_OK) return e;
+        const int max_att = rw_ff->n_att > rw_lat->n_att ? rw_ff->n_att : rw_lat->n_att;
+        size_t smem = rewire_smem(N, max_att, ff->Qw > lat->Qw ? ff->Qw : lat->Qw, FUSED_THREADS);
+        if (smem < (size_t)2 * Nw * 4) smem = (size_t)2 * Nw * 4;
+        // one neuron per thread: beyond one cluster's threads the per-step launches spread
+        // STDP over the whole GPU and win
+        const int cs = smem <= 227 * 1024 ? fused_cluster_size<1>(smem, s) : 0;
+        if (cs >= 2 && N <= cs * FUSED_THREADS) {
+            run.k = topo_consts(p);
+            for (int m = 0; m < 2; ++m) {
+                snn_ragged* r = m == 0 ? ff : lat;
+                run.len[m] = r->d.row_len;
+                run.ind[m] = r->d.ind;
+                run.w[m] = (float*)r->d.w;
+                run.C[m] = r->d.C;
+                run.thr[m] = r->thr_form;
+                run.status[m] = r->status;
+            }
+            run.stats[0] = stats_ff;
+            run.stats[1] = stats_lat;
+            run.V = st->V;
+            run.gs = st->gs;
+            run.ref = st->ref;
+            run.x_src = st->x_src;
+            run.x_tgt = st->x_tgt;
+            run.y = st->y;
+            run.ydec = st->ydec;
+            run.acc = (unsigned long long*)st->acc;
+            run.src_bits = st->src_bits;
+            run.tgt_bits = st->tgt_bits;
+            run.in_seed = input_seed;
+            run.rewire_every = rewire_every;
+            for (int64_t t = t0; t < t0 + n_steps; t += 1000) {
+                run.t0 = t;
+                run.n_steps = (int)(t0 + n_steps - t < 1000 ? t0 + n_steps - t : 1000);
+                if ((e = launch_fused<1>(run, cs, smem, s)) != SNN_OK) return e;
+            }
+            return SNN_OK;
+        }
+    }
     for (int64_t t = t0; t < t0 + n_steps; ++t) {
         const int cur = (int)(t & 1), prv = cur ^ 1;
         if ((e = snn_topo_input(p, st, input_seed, t, stream)) != SNN_OK) return e;

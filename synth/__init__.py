@@ -54,7 +54,7 @@ def rates_to_thresholds(rates_hz: np.ndarray, dt_ms: float) -> np.ndarray:
 class ClassifierTask:
     """Rate templates [n_classes][n_bins][n_in] (Hz) and their spike thresholds."""
     rates_hz: np.ndarray
-    thr: np.ndarray          # uint64, same shape
+    thr: np.ndarray          # uint32 Bernoulli thresholds, same shape
     n_classes: int
     n_bins: int
     n_in: int
@@ -143,6 +143,26 @@ def random_ragged(seed: int, P: int, Q: int, p: float, C: int | None = None,
         row_len[i] = len(r)
         ind[i, :len(r)] = r
         w[i, :len(r)] = rng.normal(0.0, w_std, size=len(r))
+    return Ragged(P, Q, C, row_len, ind, w)
+
+
+def large_ragged(seed: int, P: int, Q: int, k: int, C: int, w_std: float = 1.0) -> Ragged:
+    """Large random ragged matrix for bandwidth measurements: each row draws k targets
+    uniformly with replacement and keeps the distinct ones (about k - k^2/(2Q)), in
+    ascending order; weights N(0, w_std) in float32-representable values."""
+    rng = np.random.default_rng([seed, 0x1A, P, Q, k])
+    t = np.sort(rng.integers(0, Q, size=(P, k), dtype=np.int64), axis=1)
+    keep = np.ones_like(t, dtype=bool)
+    keep[:, 1:] = t[:, 1:] != t[:, :-1]
+    row_len = keep.sum(axis=1).astype(np.int32)
+    assert int(row_len.max()) <= C
+    pos = np.cumsum(keep, axis=1) - 1
+    ind = np.full((P, C), -1, dtype=np.int32)
+    rows = np.nonzero(keep)
+    ind[rows[0], pos[rows]] = t[rows]
+    w = np.zeros((P, C), dtype=np.float64)
+    live = np.arange(C)[None, :] < row_len[:, None]
+    w[live] = rng.normal(0.0, w_std, size=int(live.sum())).astype(np.float32)
     return Ragged(P, Q, C, row_len, ind, w)
 
 

@@ -136,12 +136,13 @@ def test_steps_match_oracle_from_same_state():
     assert flips <= 2
 
 
-def test_topo_run_matches_granular_calls():
-    """snn_topo_run over 40 steps equals the same sequence of granular calls."""
+@pytest.mark.parametrize("L,C,T,n_att", [(16, 32, 40, 10), (32, 64, 200, 40), (112, 64, 30, 490)])
+def test_topo_run_matches_granular_calls(L, C, T, n_att):
+    """snn_topo_run (the fused cluster loop) equals the same sequence of granular calls,
+    bit for bit: connectivity, conductances, neuron state and traces."""
     from paper_2510_19764_gb300 import abi, net
-    L, C, T = 16, 32, 40
     N = L * L
-    p = ot.TopoParams(L=L, n_att=10)
+    p = ot.TopoParams(L=L, n_att=n_att)
     res = []
     for mode in ("run", "granular"):
         ff = synth.topo_initial(1, L, p.p_form_ff, p.sigma_ff, C, p.g_max)
@@ -167,8 +168,13 @@ def test_topo_run_matches_granular_calls():
                     abi.snn_rewire_topo(dff.handle, rw_ff, (t + 1) // 10 - 1)
                     abi.snn_rewire_topo(dlat.handle, rw_lat, (t + 1) // 10 - 1)
         torch.cuda.synchronize()
-        res.append((dff.host(), dlat.host(), st.V.cpu().numpy().copy()))
+        res.append((dff.host(), dlat.host(),
+                    {k: getattr(st, k).cpu().numpy().copy()
+                     for k in ("V", "gs", "ref", "x_src", "x_tgt", "y", "ydec", "acc", "src_bits", "tgt_bits")}))
     for a, b in zip(res[0][:2], res[1][:2]):
+        assert a["row_len"].sum() > 0
         for k in ("row_len", "ind", "w"):
             np.testing.assert_array_equal(a[k], b[k])
-    np.testing.assert_array_equal(res[0][2], res[1][2])
+    for k in res[0][2]:
+        np.testing.assert_array_equal(res[0][2][k], res[1][2][k], err_msg=k)
+    assert res[0][2]["tgt_bits"].any() or res[0][2]["y"].max() > 0
