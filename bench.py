@@ -297,16 +297,21 @@ def run_ours(args, world, rank, local):
     # dominant call and its algorithmic bytes
     dom = max(range(4), key=lambda c: per_call[c])
     N, n_in, K = W["N"], W["n_in"], W["K"]
-    alg = {
+    algs = {
         # forward: 8 B per synaptic event (ind + w) + 4 B per spike-bit list entry + 32 B per
         # ALIF neuron-step (v, a read/write; psi record)
         0: events * 8 + spikes * 4 + B * T * N * 32.0,
         # gradient: psi read + delta write/read + synaptic events gathered (4 B delta + 4 B ind)
         1: B * T * N * 4.0 * 3 + events * 8,
-        2: 28.0 * (in_rag.P * in_rag.C + rec_rag.P * rec_rag.C),
-        3: 24.0 * (in_rag.P * in_rag.C + rec_rag.P * rec_rag.C),
-    }[dom]
+        # Adam: 28 B per active slot; DEEP R: 8 B read per active slot (+ moves, formations)
+        2: 28.0 * active,
+        3: 8.0 * active,
+    }
+    alg = algs[dom]
     achieved = alg / (per_call[dom] / 1e3) / 1e9
+    by_call = {calls[c]: {"achieved_gbs": round(algs[c] / (per_call[c] / 1e3) / 1e9, 1),
+                          "frac": round(algs[c] / (per_call[c] / 1e3) / 1e9 / pk["hbm_gbs"], 4)}
+               for c in range(4) if per_call[c] > 0}
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -327,6 +332,7 @@ def run_ours(args, world, rank, local):
         "roofline": {"kernel": calls[dom], "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
                      "traffic": None, "peak_source": pk["source"]},
+        "roofline_by_call": by_call,
         "e2e": {"value": round(B * args.steps * world / (e2e_ms / 1e3), 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": LAUNCHES_PER_BATCH * args.steps,

@@ -135,7 +135,7 @@ __global__ void k_input(InputParams p) {
 // parity and built where the spikes appear: hidden spikes are appended with one
 // warp-aggregated shared-memory atomic per warp during the neuron update, the input
 // spikes of step t (drawn ahead of time by k_input) are listed by warp 0.  Per step t:
-//  (A) warps take every nwarps-th row of the lists of step t-1, two rows at a time; each
+//  (A) warps take every nwarps-th row of the lists of step t-1, FWD_ROWS at a time; each
 //      slot is one packed 64-bit load (target index | fixed-point weight) and one
 //      pair of 32-bit shared-memory atomics (padding slots of a row's last chunk add 0
 //      to per-lane spare accumulators).  Hidden rows carry their readout column as K
@@ -145,6 +145,8 @@ __global__ void k_input(InputParams p) {
 //  (B) each thread updates its NPT neurons (state in registers) and writes psi; warp 1
 //      advances the leaky readout y^t = alpha y^{t-1} + W_out z^{t-1} + b (one lane per
 //      output, sequential in t) and records y^t into the d record (softmax comes later).
+constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time
+
 template <typename real, int NPT, int TH>
 __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -218,26 +220,30 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             zcur[w] = 0u;
         }
         if (tid == 32) lcnt[cur] = 0;
-        for (int k = warp; k < n_rows; k += 2 * nwarps) {
-            const int rA = lprv[k];
-            const int rB = (k + nwarps < n_rows) ? lprv[k + nwarps] : R;   // R: empty row
-            const int nA = lens[rA], nB = lens[rB];
-            const unsigned long long* pkA = p.pk + (size_t)rA * p.Cf;
-            const unsigned long long* pkB = p.pk + (size_t)(rB < R ? rB : 0) * p.Cf;
-            const int nmax = nA > nB ? nA : nB;
+        for (int k = warp; k < n_rows; k += FWD_ROWS * nwarps) {
+            // FWD_ROWS rows per warp at a time, their packed chunks loaded together
+            int nr[FWD_ROWS];
+            const unsigned long long* pr[FWD_ROWS];
+            int nmax = 0;
+#pragma unroll
+            for (int u = 0; u < FWD_ROWS; ++u) {
+                const int r = (k + u * nwarps < n_rows) ? lprv[k + u * nwarps] : R;   // R: empty row
+                nr[u] = lens[r];
+                pr[u] = p.pk + (size_t)(r < R ? r : 0) * p.Cf;
+                nmax = nr[u] > nmax ? nr[u] : nmax;
+            }
             for (int s0 = 0; s0 < nmax; s0 += 128) {
-                unsigned long long wA[4], wB[4];
+                unsigned long long wv[FWD_ROWS][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    // warp-uniform chunk tests; chunk slots past the length are padding
-                    wA[q] = s0 + q * 32 < nA ? pkA[s0 + q * 32 + lane] : 0ull;
-                    wB[q] = s0 + q * 32 < nB ? pkB[s0 + q * 32 + lane] : 0ull;
-                }
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (s0 + q * 32 < nA) acc_add(acc, wA[q]);
-                    if (s0 + q * 32 < nB) acc_add(acc, wB[q]);
-                }
+                    for (int u = 0; u < FWD_ROWS; ++u)   // warp-uniform chunk tests; slots past a
+                        wv[u][q] = s0 + q * 32 < nr[u] ? pr[u][s0 + q * 32 + lane] : 0ull;   // length are padding
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int u = 0; u < FWD_ROWS; ++u)
+                        if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q]);
             }
         }
         __syncthreads();

@@ -4,13 +4,16 @@
 //  k_deepr_eliminate  : one warp per row; a synapse is dormant when its weight's sign is
 //                       strictly opposite to its fixed sign bit; survivors are compacted
 //                       stably with a warp ballot + prefix count (w, m, v move along),
-//                       connectivity bits of removed synapses are cleared.
-//  k_deepr_distribute : one CTA; sums the dormant counts on the device and spreads them
-//                       over rows in rounds (per-round histogram with integer atomics,
-//                       so the result does not depend on thread order).
+//                       connectivity bits of removed synapses are cleared; the dormant
+//                       total D is summed on the device.
+//  k_deepr_round0     : the whole grid draws round 0 of the redistribution (D rows)
+//                       into a per-row histogram with integer atomics.
+//  k_deepr_distribute : one CTA; accepts round 0 up to each row's room and runs the
+//                       remaining rounds on the leftovers (order-independent counts).
 //  k_deepr_form       : one warp per row with activations; each activation appends the
-//                       m-th free target found with a warp popcount scan over the row's
-//                       connectivity bitfield.
+//                       m-th free target: a scan over per-chunk free counts (chunks of
+//                       1024 targets, kept in shared memory) finds the chunk, one
+//                       32-word scan finds the bit.
 #include "common.cuh"
 
 #include <mutex>
@@ -18,11 +21,11 @@
 namespace snn {
 
 template <typename real>
-__global__ void k_deepr_eliminate(int32_t* __restrict__ len, int32_t* __restrict__ ind, real* __restrict__ w,
-                                  real* __restrict__ m, real* __restrict__ v, const uint32_t* __restrict__ sign,
-                                  uint32_t* __restrict__ conn, int32_t* __restrict__ dormant, int P, int C, int Qw) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= P) return;
+__device__ __forceinline__ void eliminate_row(int32_t* __restrict__ len, int32_t* __restrict__ ind,
+                                              real* __restrict__ w, real* __restrict__ m, real* __restrict__ v,
+                                              const uint32_t* __restrict__ sign, uint32_t* __restrict__ conn,
+                                              int32_t* __restrict__ dormant, int32_t* __restrict__ cnt, int i, int C,
+                                              int Qw) {
     const int lane = lane_id();
     const int n = len[i];
     const size_t row = (size_t)i * C;
@@ -58,6 +61,45 @@ __global__ void k_deepr_eliminate(int32_t* __restrict__ len, int32_t* __restrict
     if (lane == 0) {
         len[i] = wp;
         dormant[i] = n - wp;
+        cnt[i] = 0;
+    }
+    __syncwarp();
+}
+
+constexpr int DEEPR_THREADS = 256;
+
+template <typename real>
+__global__ void __launch_bounds__(DEEPR_THREADS)
+    k_deepr_eliminate(int32_t* __restrict__ len, int32_t* __restrict__ ind, real* __restrict__ w,
+                      real* __restrict__ m, real* __restrict__ v, const uint32_t* __restrict__ sign,
+                      uint32_t* __restrict__ conn, int32_t* __restrict__ dormant, int32_t* __restrict__ cnt,
+                      unsigned long long* __restrict__ dsum, int P, int C, int Qw) {
+    __shared__ int removed_w[DEEPR_THREADS / 32];
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (i < P) eliminate_row(len, ind, w, m, v, sign, conn, dormant, cnt, i, C, Qw);
+    if (lane == 0) removed_w[threadIdx.x >> 5] = i < P ? dormant[i] : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += removed_w[k];
+        if (t) atomicAdd(dsum, (unsigned long long)t);
+    }
+}
+
+// Round 0 of the redistribution over the whole grid: activation k draws row mulhi(u, P)
+// with u = Philox(DEEPR_DIST; (rewire, 0, k/4, 0)) word k%4.
+__global__ void k_deepr_round0(const unsigned long long* __restrict__ dsum, int32_t* __restrict__ cnt, int P,
+                               uint64_t seed, uint64_t rewire, const long long* ridx_dev) {
+    if (ridx_dev) rewire = (uint64_t)*ridx_dev;
+    const long long D = (long long)*dsum;
+    const long long groups = (D + 3) >> 2;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const u64x4 u = philox(seed, PH_DEEPR_DIST, rewire, 0, (uint64_t)g, 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * g + q < D) atomicAdd(&cnt[(int)mulhi_index(u[q], (uint64_t)P)], 1);
     }
 }
 
@@ -80,6 +122,8 @@ __global__ void __launch_bounds__(1024)
     __shared__ long long red[32];
     if (ridx_dev) rewire = (uint64_t)*ridx_dev;
     long long dsum = 0;
+    // one CTA walks all rows: unrolled so that several rows' loads are in flight
+#pragma unroll 8
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int forb = (no_autapse && i < Q) ? 1 : 0;
         const int l = len[i];
@@ -91,18 +135,21 @@ __global__ void __launch_bounds__(1024)
     const long long D = block_sum_ll(dsum, red);
     long long remaining = D;
     for (int r = 0; r < 64 && remaining > 0; ++r) {
-        for (int i = threadIdx.x; i < P; i += blockDim.x) cnt[i] = 0;
-        __syncthreads();
-        const long long groups = (remaining + 3) >> 2;
-        for (long long g = threadIdx.x; g < groups; g += blockDim.x) {
-            const u64x4 u = philox(seed, PH_DEEPR_DIST, rewire, (uint64_t)r, (uint64_t)g, 0);
+        if (r > 0) {   // round 0 was drawn by k_deepr_round0 over the whole grid
+            for (int i = threadIdx.x; i < P; i += blockDim.x) cnt[i] = 0;
+            __syncthreads();
+            const long long groups = (remaining + 3) >> 2;
+            for (long long g = threadIdx.x; g < groups; g += blockDim.x) {
+                const u64x4 u = philox(seed, PH_DEEPR_DIST, rewire, (uint64_t)r, (uint64_t)g, 0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (4 * g + q < remaining) atomicAdd(&cnt[(int)mulhi_index(u[q], (uint64_t)P)], 1);
+                for (int q = 0; q < 4; ++q) {
+                    if (4 * g + q < remaining) atomicAdd(&cnt[(int)mulhi_index(u[q], (uint64_t)P)], 1);
+                }
             }
         }
         __syncthreads();
         long long rej = 0;
+#pragma unroll 8
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const int c = cnt[i];
             if (c) {
@@ -123,22 +170,59 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// Free-target counts per chunk of 32 bitfield words of a row (the self target of a
+// recurrent projection and the bits beyond Q count as taken).
+__device__ __forceinline__ uint32_t conn_word(const uint32_t* crow, int wi, int Qw, int i, int forb,
+                                              uint32_t tail_mask) {
+    uint32_t word = 0xffffffffu;
+    if (wi < Qw) {
+        word = crow[wi];
+        if (forb && (i >> 5) == wi) word |= 1u << (i & 31);
+        if (wi == Qw - 1) word |= tail_mask;
+    }
+    return word;
+}
+
 template <typename real>
-__global__ void k_deepr_form(int32_t* __restrict__ len, int32_t* __restrict__ ind, real* __restrict__ w,
-                             real* __restrict__ m, real* __restrict__ v, uint32_t* __restrict__ conn,
-                             const int32_t* __restrict__ taken, int P, int C, int Q, int Qw, int no_autapse,
-                             uint64_t seed, uint64_t rewire, const long long* ridx_dev, int32_t* status,
-                             snn_rewire_stats* stats) {
+__global__ void __launch_bounds__(DEEPR_THREADS)
+    k_deepr_form(int32_t* __restrict__ len, int32_t* __restrict__ ind, real* __restrict__ w, real* __restrict__ m,
+                 real* __restrict__ v, uint32_t* __restrict__ conn, const int32_t* __restrict__ taken, int P, int C,
+                 int Q, int Qw, int no_autapse, uint64_t seed, uint64_t rewire, const long long* ridx_dev,
+                 int32_t* status, snn_rewire_stats* stats) {
+    extern __shared__ int32_t chunk_free_all[];      // [warps][NC]
+    const int NC = (Qw + 31) >> 5;                   // chunks of 32 words (1024 targets)
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (ridx_dev) rewire = (uint64_t)*ridx_dev;
     if (i >= P) return;
     const int nt = taken[i];
     if (nt == 0) return;
     const int lane = lane_id();
+    int32_t* F = chunk_free_all + (size_t)(threadIdx.x >> 5) * NC;
     const int forb = (no_autapse && i < Q) ? 1 : 0;
     const uint32_t tail_mask = (Q & 31) ? ~((1u << (Q & 31)) - 1u) : 0u;   // bits beyond Q in the last word
     uint32_t* crow = conn + (size_t)i * Qw;
     const size_t row = (size_t)i * C;
+    // chunk c is counted by lane c % 32: its 32 words as eight 16-byte loads (a row's
+    // bitfield starts 16-byte aligned when Qw is a multiple of 4)
+    const bool vec = (Qw & 3) == 0;
+    for (int c = lane; c < NC; c += 32) {
+        int z = 0;
+        if (vec && c * 32 + 32 <= Qw) {
+            const uint4* p4 = (const uint4*)(crow + c * 32);
+            uint4 q[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) q[h] = p4[h];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) z += __popc(~q[h].x) + __popc(~q[h].y) + __popc(~q[h].z) + __popc(~q[h].w);
+            // self target and the bits beyond Q fall in this chunk only if its words hold them
+            if (forb && (i >> 10) == c) z -= ((crow[i >> 5] >> (i & 31)) & 1u) ? 0 : 1;
+            if (tail_mask && (Qw - 1) >> 5 == c) z -= __popc(~crow[Qw - 1] & tail_mask);
+        } else {
+            for (int h = 0; h < 32; ++h) z += __popc(~conn_word(crow, c * 32 + h, Qw, i, forb, tail_mask));
+        }
+        F[c] = z;
+    }
+    __syncwarp();
     int n = len[i];
     int formed = 0;
     for (int k = 0; k < nt; ++k) {
@@ -149,27 +233,36 @@ __global__ void k_deepr_form(int32_t* __restrict__ len, int32_t* __restrict__ in
         }
         const u64x4 u = philox(seed, PH_DEEPR_FORM, rewire, (uint64_t)i, (uint64_t)k, 0);
         const int mth = (int)mulhi_index(u.x, (uint64_t)n_free);
-        int target = -1, seen = 0;
-        for (int wb = 0; wb < Qw && target < 0; wb += 32) {
-            const int wi = wb + lane;
-            uint32_t word = 0xffffffffu;
-            if (wi < Qw) {
-                word = crow[wi];
-                if (forb && (i >> 5) == wi) word |= 1u << (i & 31);
-                if (wi == Qw - 1) word |= tail_mask;
+        // chunk holding the mth free target (ascending), then its word and bit
+        int chunk = -1, before = 0, seen = 0;
+        for (int cb = 0; cb < NC && chunk < 0; cb += 32) {
+            const int c = cb + lane;
+            const int f = c < NC ? F[c] : 0;
+            const int incl = warp_incl_scan(f);
+            const int excl = incl - f;
+            const uint32_t hm = __ballot_sync(0xffffffffu, c < NC && mth >= seen + excl && mth < seen + incl);
+            if (hm) {
+                const int src = __ffs(hm) - 1;
+                chunk = cb + src;
+                before = seen + __shfl_sync(0xffffffffu, excl, src);
             }
+            seen += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        int target = -1;
+        if (chunk >= 0) {
+            const int wi = chunk * 32 + lane;
+            const uint32_t word = conn_word(crow, wi, Qw, i, forb, tail_mask);
             const int zeros = __popc(~word);
             const int incl = warp_incl_scan(zeros);
             const int excl = incl - zeros;
-            const bool hit = mth >= seen + excl && mth < seen + incl;
-            const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+            const int want = mth - before;
+            const uint32_t hm = __ballot_sync(0xffffffffu, want >= excl && want < incl);
             if (hm) {
                 const int src = __ffs(hm) - 1;
                 int tg = -1;
-                if (lane == src) tg = wi * 32 + nth_set_bit(~word, mth - seen - excl);
+                if (lane == src) tg = wi * 32 + nth_set_bit(~word, want - excl);
                 target = __shfl_sync(0xffffffffu, tg, src);
             }
-            seen += __shfl_sync(0xffffffffu, incl, 31);
         }
         if (target < 0) {
             if (lane == 0) atomicOr(status, ST_STATE);
@@ -181,6 +274,7 @@ __global__ void k_deepr_form(int32_t* __restrict__ len, int32_t* __restrict__ in
             m[row + n] = real(0);
             v[row + n] = real(0);
             crow[target >> 5] |= 1u << (target & 31);
+            F[chunk] -= 1;
         }
         __syncwarp();
         ++n;
@@ -192,27 +286,43 @@ __global__ void k_deepr_form(int32_t* __restrict__ len, int32_t* __restrict__ in
     }
 }
 
+// Launch sequence of one rewiring (dsum: device uint64 scratch for the dormant total).
 template <typename real>
-static snn_status rewire_impl(snn_ragged* r, uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
-                              cudaStream_t s) {
-    const snn_ragged_desc& d = r->d;
-    const int blocks = ceil_div((long long)d.P * 32, 256);
-    k_deepr_eliminate<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
-                                                    d.sign_bits, d.conn_bits, r->dormant, d.P, d.C, r->Qw);
+static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* dormant, int32_t* taken,
+                                    int32_t* room, int32_t* cnt, unsigned long long* dsum, int32_t* status,
+                                    uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
+                                    cudaStream_t s) {
+    const int blocks = ceil_div((long long)d.P * 32, DEEPR_THREADS);
+    SNN_CUDA(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), s));
+    k_deepr_eliminate<real><<<blocks, DEEPR_THREADS, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
+                                                              d.sign_bits, d.conn_bits, dormant, cnt, dsum, d.P, d.C,
+                                                              Qw);
     SNN_LAUNCH_CHECK();
-    k_deepr_distribute<<<1, 1024, 0, s>>>(d.row_len, r->dormant, r->room, r->taken, r->cnt, d.P, d.C, d.Q,
-                                          d.no_autapse, d.seed, rewire, ridx_dev, r->status, stats);
+    k_deepr_round0<<<2 * 152, 256, 0, s>>>(dsum, cnt, d.P, d.seed, rewire, ridx_dev);
     SNN_LAUNCH_CHECK();
-    k_deepr_form<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v, d.conn_bits,
-                                               r->taken, d.P, d.C, d.Q, r->Qw, d.no_autapse, d.seed, rewire,
-                                               ridx_dev, r->status, stats);
+    k_deepr_distribute<<<1, 1024, 0, s>>>(d.row_len, dormant, room, taken, cnt, d.P, d.C, d.Q, d.no_autapse, d.seed,
+                                          rewire, ridx_dev, status, stats);
+    SNN_LAUNCH_CHECK();
+    const size_t smem = (size_t)(DEEPR_THREADS / 32) * ((Qw + 31) / 32) * sizeof(int32_t);
+    SNN_REQUIRE(smem <= 48 * 1024, "snn_rewire_deepr: Q = %d too large for the formation chunk table", d.Q);
+    k_deepr_form<real><<<blocks, DEEPR_THREADS, smem, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
+                                                            d.conn_bits, taken, d.P, d.C, d.Q, Qw, d.no_autapse,
+                                                            d.seed, rewire, ridx_dev, status, stats);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
 
+template <typename real>
+static snn_status rewire_impl(snn_ragged* r, uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
+                              cudaStream_t s) {
+    return rewire_launch_all<real>(r->d, r->Qw, r->dormant, r->taken, r->room, r->cnt,
+                                   (unsigned long long*)r->scal, r->status, rewire, ridx_dev, stats, s);
+}
+
 // ------------------------------------------------------------------ no-allocation variant
 // Fixed scratch for snn_rewire_deepr_noalloc: four int32 arrays of NOALLOC_MAX_ROWS rows
-// (dormant counts, taken, room, per-round histogram) and one status word.  It lives in
+// (dormant counts, taken, room, per-round histogram), one status word and (at word 8
+// of the tail) the uint64 dormant total.  It lives in
 // every device that loads the library until the process exits.
 constexpr int NOALLOC_MAX_ROWS = 16384;
 static __device__ __align__(256) int32_t g_noalloc_scratch[4 * NOALLOC_MAX_ROWS + 32];
@@ -249,19 +359,9 @@ static snn_status rewire_noalloc_impl(const snn_ragged_desc& d, int32_t* scratch
     int32_t* taken = scratch + NOALLOC_MAX_ROWS;
     int32_t* room = scratch + 2 * NOALLOC_MAX_ROWS;
     int32_t* cnt = scratch + 3 * NOALLOC_MAX_ROWS;
+    unsigned long long* dsum = (unsigned long long*)(scratch + 4 * NOALLOC_MAX_ROWS + 8);
     if (!status) status = scratch + 4 * NOALLOC_MAX_ROWS;
-    const int blocks = ceil_div((long long)d.P * 32, 256);
-    k_deepr_eliminate<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
-                                                    d.sign_bits, d.conn_bits, dormant, d.P, d.C, Qw);
-    SNN_LAUNCH_CHECK();
-    k_deepr_distribute<<<1, 1024, 0, s>>>(d.row_len, dormant, room, taken, cnt, d.P, d.C, d.Q, d.no_autapse, d.seed,
-                                          rewire, nullptr, status, stats);
-    SNN_LAUNCH_CHECK();
-    k_deepr_form<real><<<blocks, 256, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v, d.conn_bits,
-                                               taken, d.P, d.C, d.Q, Qw, d.no_autapse, d.seed, rewire, nullptr, status,
-                                               stats);
-    SNN_LAUNCH_CHECK();
-    return SNN_OK;
+    return rewire_launch_all<real>(d, Qw, dormant, taken, room, cnt, dsum, status, rewire, nullptr, stats, s);
 }
 
 }  // namespace snn

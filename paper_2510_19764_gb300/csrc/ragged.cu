@@ -90,8 +90,20 @@ __global__ void k_propagate(const int32_t* __restrict__ row_len, const int32_t* 
         int len = row_len[i];
         const int32_t* ri = ind + (size_t)i * C;
         const real* rw = w + (size_t)i * C;
-        for (int s = lane_id(); s < len; s += 32)
-            atomicAdd(a + ri[s], (unsigned long long)to_fixed(rw[s]));
+        // four 32-slot chunks per iteration: their loads are issued before the adds
+        for (int s0 = 0; s0 < len; s0 += 128) {
+            int j[4];
+            real x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = s0 + 32 * q + lane_id();
+                j[q] = s < len ? ri[s] : -1;
+                x[q] = s < len ? rw[s] : real(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j[q] >= 0) atomicAdd(a + j[q], (unsigned long long)to_fixed(x[q]));
+        }
     }
 }
 
