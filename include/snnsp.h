@@ -26,7 +26,9 @@
  *    is bit (j & 31) of word (j >> 5).
  *  - Random numbers: Philox4x64-10 (Salmon et al., SC'11) keyed by (seed, purpose),
  *    with purpose-specific counters; Bernoulli(p) is "word < floor(p * 2^64)" and a
- *    uniform index in [0, n) is the high 64 bits of word * n.
+ *    uniform index in [0, n) is the high 64 bits of word * n.  The classifier's
+ *    Poisson input is the one exception: 32-bit halves of the words against
+ *    floor(p * 2^32) (see snn_step_neurons).
  *  - Spike accumulators (snn_propagate) are int64 fixed point with 40 fractional bits,
  *    so their sums do not depend on the order of the atomic additions.
  */
@@ -224,8 +226,11 @@ typedef struct {
 #define SNN_EPROP_GRAD  0
 #define SNN_EPROP_APPLY 1
 
-/* Create a classifier handle; validates sizes and allocates fixed scratch for the
- * e-prop gradient partial sums (sized from max_B, max_T and the two ragged handles). */
+/* Create a classifier handle; validates sizes (0 < K <= 32, N <= 2048, n_in <= 1024,
+ * row capacities <= 2048) and allocates fixed scratch: the e-prop gradient partial sums
+ * (sized from max_B, max_T and the two ragged handles), the packed forward rows and the
+ * gather order of each row.  The forward sums each neuron's synaptic input of a step
+ * exactly in fixed point while its magnitude stays below 2^11 (2048 in weight units). */
 snn_status snn_create_classifier(const snn_classifier_desc* desc, snn_classifier** out);
 /* Row schedule of snn_step_neurons: how many warps (4, 8 or 16) share one trial's
  * spiking rows and neurons (default 8).  Results do not depend on it (integer
@@ -315,7 +320,10 @@ snn_status snn_stdp_update(snn_ragged* r, const snn_topo_params* p, const uint32
  * candidates with a synapse are eliminated iff R < thr(p_elim_dep if g < g_theta else
  * p_elim_pot), the others formed iff R < thr(p_form exp(-d^2/2 sigma^2)) with g = g_new,
  * R = Philox(TOPO_DRAW; (rewire_idx, i, j, 0)) word 0; rows compact stably; formations are
- * appended in ascending target order; a full row counts overflow.  F32 only. */
+ * appended in ascending target order; a full row counts overflow.  F32 only.  The first
+ * call with a new (L, p_form, sigma) builds the handle's formation-threshold table on
+ * the host and copies it synchronously; later calls with the same parameters do not
+ * synchronise. */
 snn_status snn_rewire_topo(snn_ragged* r, const snn_topo_rewire* p, int64_t rewire_idx,
                            snn_rewire_stats* stats, snn_stream stream);
 /* Run steps t0 .. t0+n_steps-1 of the full topographic network: input, propagation of
