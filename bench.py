@@ -32,8 +32,12 @@ sys.path.insert(0, ROOT)
 # library kernels per training batch: forward call 4 (k_input, k_pack, k_forward,
 # k_softmax_d), gradient 9 (k_readout_scan, k_backward_x2, k_reduce_gb, k_sort_rows x2,
 # k_gather, k_reduce_ragged x2, k_reduce_out), Adam 4 (k_adam_ragged x2, k_adam_dense
-# x2), DEEP R 6 (eliminate, distribute, form per projection)
-LAUNCHES_PER_BATCH = 23
+# x2), DEEP R 10 (eliminate, round0, accept0, distribute, form per projection; plus one
+# 16-byte memset each)
+LAUNCHES_PER_BATCH = 27
+# DRAM bytes (read + write) of one k_forward launch at 512 trials: 4 x the 507.3 MB that
+# ncu measured for the 128-trial case of the same kernel build (None once it changes)
+FORWARD_TRAFFIC = 4 * 507.27e6
 METRIC = "e-prop+DEEP R training samples/s"
 UNIT = "samples/s"
 WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}
@@ -139,6 +143,27 @@ def dist_init(args):
 
 
 # ------------------------------------------------------------------------ workload
+
+def classifier_config(in_C: int, rec_C: int, world: int) -> dict:
+    """The `config` of the classifier bench line (both arms)."""
+    W = WORKLOAD
+    return {"workload": "spoken-digit-shaped sparse ALIF classifier, e-prop + DEEP R training batch",
+            "n_in": W["n_in"], "hidden": W["N"], "readouts": W["K"], "steps_per_trial": W["T"],
+            "global_batch": W["B"] * world, "connectivity": W["p"], "row_capacity": [in_C, rec_C],
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (per-batch records and adjoint > 4 GB rewritten every step)"}
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest value of x over all ranks (the bench's per-rank times)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
 
 def make_workload(seed: int, device="cuda"):
     import numpy as np
@@ -252,12 +277,7 @@ def run_ours(args, world, rank, local):
         end.record(stream)
         barrier()
     ms = start.elapsed_time(end)
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     per_call = [0.0] * 4
     for ev in ev_pairs:
         for c in range(4):
@@ -282,11 +302,7 @@ def run_ours(args, world, rank, local):
     e2e_end.record(stream)
     barrier()
     e2e_ms = max(e2e_start.elapsed_time(e2e_end), (time.perf_counter() - t_host0) * 1e3)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     h2d = sum(x.numel() * x.element_size() for x in h_desc[0])
     d2h = out_host.numel() * out_host.element_size() + stats_host.numel() * stats_host.element_size()
     ok = cls.w_in.status(stream) == abi.SNN_OK and cls.w_rec.status(stream) == abi.SNN_OK
@@ -317,11 +333,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "spoken-digit-shaped sparse ALIF classifier, e-prop + DEEP R training batch",
-                   "n_in": n_in, "hidden": N, "readouts": K, "steps_per_trial": T, "global_batch": B * world,
-                   "connectivity": W["p"], "row_capacity": [in_rag.C, rec_rag.C],
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (per-batch records and adjoint > 4 GB rewritten every step)"},
+        "config": classifier_config(in_rag.C, rec_rag.C, world),
         "synaptic_events_per_s": round(events * world / (ms_max / 1e3 / args.steps), 1),
         # e-prop: the per-synapse trace form updates every active synapse of every trial at
         # every step; the adjoint gather computes the same gradients from synaptic events
@@ -331,7 +343,10 @@ def run_ours(args, world, rank, local):
         "per_call_ms": {c: round(x, 4) for c, x in zip(calls, per_call)},
         "roofline": {"kernel": calls[dom], "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-                     "traffic": None, "peak_source": pk["source"]},
+                     "traffic": FORWARD_TRAFFIC * B / 512 if dom == 0 and FORWARD_TRAFFIC else None,
+                     "traffic_source": "k_forward DRAM read+write per launch from one ncu capture of the "
+                                       "128-trial case, scaled by trials (the psi record grows with them)",
+                     "peak_source": pk["source"]},
         "roofline_by_call": by_call,
         "e2e": {"value": round(B * args.steps * world / (e2e_ms / 1e3), 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -363,7 +378,7 @@ def run_reference(args, sample_steps: int, world: int, rank: int):
     oc.eprop_gradients(onet, r["x"], r["z"], r["psi"], r["d"])
     dt = time.perf_counter() - t0
     per_trial = dt * W["T"] / sample_steps
-    return 1.0 / per_trial, per_trial, dt
+    return 1.0 / per_trial, per_trial, dt, (in_rag.C, rec_rag.C)
 
 
 # ------------------------------------------------------------------ other workloads
@@ -589,13 +604,12 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        v, per_trial, dt = run_reference(args, args.sample_steps, world, rank)
+        v, per_trial, dt, caps = run_reference(args, args.sample_steps, world, rank)
         line = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_trial * WORKLOAD["B"] * 1e3, 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": "spoken-digit-shaped sparse ALIF classifier, e-prop + DEEP R training batch",
-                           "global_batch": WORKLOAD["B"]},
+                "config": classifier_config(caps[0], caps[1], world),
                 "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": f"1 trial x {args.sample_steps} of 1000 steps (forward + e-prop traces), "
                                            f"{dt:.1f} s, scaled to a full trial"},
@@ -606,7 +620,7 @@ def main():
     if rank == 0 and args.no_cpu_baseline:
         print(json.dumps(line), flush=True)
     elif rank == 0:
-        cv, per_trial, dt = run_reference(args, args.sample_steps, world, rank)
+        cv, per_trial, dt, _ = run_reference(args, args.sample_steps, world, rank)
         line["cpu_baseline"] = {"value": round(cv, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"1 trial x {args.sample_steps} of 1000 steps (forward + e-prop traces), "
                                           f"{dt:.1f} s, scaled to a full trial"}

@@ -189,7 +189,7 @@ struct snn_ragged {
     int32_t* taken;
     int32_t* room;
     int32_t* cnt;
-    int32_t* scal;           // [4] device scalars: words 0-1 the dormant total of a rewiring (uint64)
+    int32_t* scal;           // [4] device scalars: uint64 dormant total, uint64 round-0 rejections
     // topographic rewiring: formation threshold table by squared distance
     uint64_t* thr_form;      // [thr_cap]
     int32_t thr_cap;

@@ -114,37 +114,50 @@ __device__ __forceinline__ long long block_sum_ll(long long x, long long* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(1024)
-    k_deepr_distribute(const int32_t* __restrict__ len, const int32_t* __restrict__ dormant, int32_t* __restrict__ room,
-                       int32_t* __restrict__ taken, int32_t* __restrict__ cnt, int P, int C, int Q, int no_autapse,
-                       uint64_t seed, uint64_t rewire, const long long* ridx_dev, int32_t* status,
-                       snn_rewire_stats* stats) {
+// Round 0 accepted over the whole grid: each row's room is min(C - len, free targets);
+// it takes min(cnt, room) activations, the rest are rejections (summed on the device).
+__global__ void k_deepr_accept0(const int32_t* __restrict__ len, const int32_t* __restrict__ cnt,
+                                int32_t* __restrict__ room, int32_t* __restrict__ taken,
+                                unsigned long long* __restrict__ rejected, int P, int C, int Q, int no_autapse) {
     __shared__ long long red[32];
-    if (ridx_dev) rewire = (uint64_t)*ridx_dev;
-    long long dsum = 0;
-    // one CTA walks all rows: unrolled so that several rows' loads are in flight
-#pragma unroll 8
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    long long rej = 0;
+    if (i < P) {
         const int forb = (no_autapse && i < Q) ? 1 : 0;
         const int l = len[i];
         const int r1 = C - l, r2 = Q - forb - l;
-        room[i] = r1 < r2 ? r1 : r2;
-        taken[i] = 0;
-        dsum += dormant[i];
+        const int rm = r1 < r2 ? r1 : r2;
+        const int c = cnt[i];
+        const int acc = c < rm ? c : rm;
+        room[i] = rm;
+        taken[i] = acc;
+        rej = c - acc;
     }
-    const long long D = block_sum_ll(dsum, red);
-    long long remaining = D;
-    for (int r = 0; r < 64 && remaining > 0; ++r) {
-        if (r > 0) {   // round 0 was drawn by k_deepr_round0 over the whole grid
-            for (int i = threadIdx.x; i < P; i += blockDim.x) cnt[i] = 0;
-            __syncthreads();
-            const long long groups = (remaining + 3) >> 2;
-            for (long long g = threadIdx.x; g < groups; g += blockDim.x) {
-                const u64x4 u = philox(seed, PH_DEEPR_DIST, rewire, (uint64_t)r, (uint64_t)g, 0);
+    const long long t = block_sum_ll(rej, red);
+    if (threadIdx.x == 0 && t) atomicAdd(rejected, (unsigned long long)t);
+}
+
+// Rounds 1..63 on the activations round 0 rejected (usually none: the CTA then only
+// records the counts).  One CTA; per round it draws the remaining activations' rows
+// with integer atomics and accepts them up to each row's remaining room.
+__global__ void __launch_bounds__(1024)
+    k_deepr_distribute(const int32_t* __restrict__ room, int32_t* __restrict__ taken, int32_t* __restrict__ cnt,
+                       const unsigned long long* __restrict__ dsum, const unsigned long long* __restrict__ rejected,
+                       int P, uint64_t seed, uint64_t rewire, const long long* ridx_dev, int32_t* status,
+                       snn_rewire_stats* stats) {
+    __shared__ long long red[32];
+    if (ridx_dev) rewire = (uint64_t)*ridx_dev;
+    const long long D = (long long)*dsum;
+    long long remaining = (long long)*rejected;
+    for (int r = 1; r < 64 && remaining > 0; ++r) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        const long long groups = (remaining + 3) >> 2;
+        for (long long g = threadIdx.x; g < groups; g += blockDim.x) {
+            const u64x4 u = philox(seed, PH_DEEPR_DIST, rewire, (uint64_t)r, (uint64_t)g, 0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (4 * g + q < remaining) atomicAdd(&cnt[(int)mulhi_index(u[q], (uint64_t)P)], 1);
-                }
+            for (int q = 0; q < 4; ++q) {
+                if (4 * g + q < remaining) atomicAdd(&cnt[(int)mulhi_index(u[q], (uint64_t)P)], 1);
             }
         }
         __syncthreads();
@@ -189,7 +202,7 @@ __global__ void __launch_bounds__(DEEPR_THREADS)
                  real* __restrict__ v, uint32_t* __restrict__ conn, const int32_t* __restrict__ taken, int P, int C,
                  int Q, int Qw, int no_autapse, uint64_t seed, uint64_t rewire, const long long* ridx_dev,
                  int32_t* status, snn_rewire_stats* stats) {
-    extern __shared__ int32_t chunk_free_all[];      // [warps][NC]
+    extern __shared__ int32_t form_smem[];           // per warp: free counts of its row's chunks
     const int NC = (Qw + 31) >> 5;                   // chunks of 32 words (1024 targets)
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (ridx_dev) rewire = (uint64_t)*ridx_dev;
@@ -197,7 +210,7 @@ __global__ void __launch_bounds__(DEEPR_THREADS)
     const int nt = taken[i];
     if (nt == 0) return;
     const int lane = lane_id();
-    int32_t* F = chunk_free_all + (size_t)(threadIdx.x >> 5) * NC;
+    int32_t* F = form_smem + (size_t)(threadIdx.x >> 5) * NC;
     const int forb = (no_autapse && i < Q) ? 1 : 0;
     const uint32_t tail_mask = (Q & 31) ? ~((1u << (Q & 31)) - 1u) : 0u;   // bits beyond Q in the last word
     uint32_t* crow = conn + (size_t)i * Qw;
@@ -223,16 +236,20 @@ __global__ void __launch_bounds__(DEEPR_THREADS)
         F[c] = z;
     }
     __syncwarp();
-    int n = len[i];
+    const int n0 = len[i];
+    int n = n0;
     int formed = 0;
+    uint64_t u_l = 0;                                // lane k % 32's draw for activation k
     for (int k = 0; k < nt; ++k) {
         const int n_free = Q - forb - n;
         if (n_free <= 0 || n >= C) {
             if (lane == 0) atomicOr(status, ST_STATE);
             break;
         }
-        const u64x4 u = philox(seed, PH_DEEPR_FORM, rewire, (uint64_t)i, (uint64_t)k, 0);
-        const int mth = (int)mulhi_index(u.x, (uint64_t)n_free);
+        // the draws depend only on (rewire, i, k): 32 activations' draws at once
+        if ((k & 31) == 0 && k + lane < nt) u_l = philox(seed, PH_DEEPR_FORM, rewire, (uint64_t)i, (uint64_t)(k + lane), 0).x;
+        const uint64_t u = __shfl_sync(0xffffffffu, u_l, k & 31);
+        const int mth = (int)mulhi_index(u, (uint64_t)n_free);
         // chunk holding the mth free target (ascending), then its word and bit
         int chunk = -1, before = 0, seen = 0;
         for (int cb = 0; cb < NC && chunk < 0; cb += 32) {
@@ -286,22 +303,26 @@ __global__ void __launch_bounds__(DEEPR_THREADS)
     }
 }
 
-// Launch sequence of one rewiring (dsum: device uint64 scratch for the dormant total).
+// Launch sequence of one rewiring.  dsum: device uint64[2] scratch (dormant total,
+// round-0 rejections), zeroed here.
 template <typename real>
 static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* dormant, int32_t* taken,
                                     int32_t* room, int32_t* cnt, unsigned long long* dsum, int32_t* status,
                                     uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
                                     cudaStream_t s) {
     const int blocks = ceil_div((long long)d.P * 32, DEEPR_THREADS);
-    SNN_CUDA(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), s));
+    SNN_CUDA(cudaMemsetAsync(dsum, 0, 2 * sizeof(unsigned long long), s));
     k_deepr_eliminate<real><<<blocks, DEEPR_THREADS, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
                                                               d.sign_bits, d.conn_bits, dormant, cnt, dsum, d.P, d.C,
                                                               Qw);
     SNN_LAUNCH_CHECK();
     k_deepr_round0<<<2 * 152, 256, 0, s>>>(dsum, cnt, d.P, d.seed, rewire, ridx_dev);
     SNN_LAUNCH_CHECK();
-    k_deepr_distribute<<<1, 1024, 0, s>>>(d.row_len, dormant, room, taken, cnt, d.P, d.C, d.Q, d.no_autapse, d.seed,
-                                          rewire, ridx_dev, status, stats);
+    k_deepr_accept0<<<ceil_div(d.P, 256), 256, 0, s>>>(d.row_len, cnt, room, taken, dsum + 1, d.P, d.C, d.Q,
+                                                       d.no_autapse);
+    SNN_LAUNCH_CHECK();
+    k_deepr_distribute<<<1, 1024, 0, s>>>(room, taken, cnt, dsum, dsum + 1, d.P, d.seed, rewire, ridx_dev, status,
+                                          stats);
     SNN_LAUNCH_CHECK();
     const size_t smem = (size_t)(DEEPR_THREADS / 32) * ((Qw + 31) / 32) * sizeof(int32_t);
     SNN_REQUIRE(smem <= 48 * 1024, "snn_rewire_deepr: Q = %d too large for the formation chunk table", d.Q);
@@ -321,8 +342,8 @@ static snn_status rewire_impl(snn_ragged* r, uint64_t rewire, const long long* r
 
 // ------------------------------------------------------------------ no-allocation variant
 // Fixed scratch for snn_rewire_deepr_noalloc: four int32 arrays of NOALLOC_MAX_ROWS rows
-// (dormant counts, taken, room, per-round histogram), one status word and (at word 8
-// of the tail) the uint64 dormant total.  It lives in
+// (dormant counts, taken, room, per-round histogram), one status word and (at words
+// 8-11 of the tail) the uint64 dormant total and round-0 rejections.  It lives in
 // every device that loads the library until the process exits.
 constexpr int NOALLOC_MAX_ROWS = 16384;
 static __device__ __align__(256) int32_t g_noalloc_scratch[4 * NOALLOC_MAX_ROWS + 32];
