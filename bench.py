@@ -214,39 +214,59 @@ def run_ours(args, world, rank, local):
     B, T = W["B"], W["T"]
     task, in_rag, rec_rag, cls = make_workload(args.seed + 1000 * rank, dev)
     n_total = args.warmup + args.steps
-    batches = [synth.trial_batch(task, args.seed + rank, i, B) for i in range(2 * n_total)]
+    batches = [synth.trial_batch(task, args.seed + rank, i, B) for i in range(2 * n_total + 2)]
     # device copies of every batch's trial descriptors (the device-resident leg)
     d_desc = [(torch.as_tensor(tb.labels, device=dev), torch.as_tensor(tb.bin_len, device=dev),
                torch.as_tensor(tb.trial_ids, device=dev)) for tb in batches]
     # pinned host copies (the end-to-end leg)
     h_desc = [(torch.as_tensor(tb.labels).pin_memory(), torch.as_tensor(tb.bin_len).pin_memory(),
                torch.as_tensor(tb.trial_ids).pin_memory()) for tb in batches]
-    batch = net.DeviceBatch(cls, batches[0].labels, batches[0].bin_len, batches[0].trial_ids, T, device=dev)
+    # two batch buffers: the next batch's input spikes are drawn on a side stream into
+    # one while the other trains (inputs depend only on trial, step and channel)
+    bufs = [net.DeviceBatch(cls, batches[0].labels, batches[0].bin_len, batches[0].trial_ids, T, device=dev)
+            for _ in range(2)]
     if args.schedule:
         abi.snn_classifier_set_schedule(cls.handle, args.schedule)
-    stream = torch.cuda.current_stream()
+    # the training steps run on a high-priority stream, the input draws on a low-priority
+    # one: the block scheduler then fills only the slots the training kernels leave free
+    stream = torch.cuda.Stream(device=dev, priority=-5)    # mapped to the highest priority
+    side = torch.cuda.Stream(device=dev, priority=0)       # the default, lowest priority
+    torch.cuda.set_stream(stream)
+    ev_free = [torch.cuda.Event() for _ in range(2)]     # buffer's last training step done
+    ev_drawn = [torch.cuda.Event() for _ in range(2)]    # buffer's inputs drawn
+    for e in ev_free:
+        e.record(stream)
     stats = torch.zeros((2, 4), dtype=torch.int64, device=dev)
     lr, l1 = 1e-3, 1e-5
     calls = ["snn_step_neurons", "snn_eprop_update(GRAD)", "snn_eprop_update(APPLY)", "snn_rewire_deepr"]
     ev_pairs = []
 
-    def one_step(i, desc, timed):
+    def draw(i, desc):
+        X = bufs[i % 2]
         lab, bl, tid = desc
-        batch.labels.copy_(lab, non_blocking=True)
-        batch.bin_len.copy_(bl, non_blocking=True)
-        batch.trial_ids.copy_(tid, non_blocking=True)
-        for t_ in (batch.v, batch.a, batch.y, batch.ysum, batch.x_bits, batch.z_bits):
+        side.wait_event(ev_free[i % 2])
+        with torch.cuda.stream(side):
+            X.labels.copy_(lab, non_blocking=True)
+            X.bin_len.copy_(bl, non_blocking=True)
+            X.trial_ids.copy_(tid, non_blocking=True)
+            abi.snn_draw_inputs(cls.handle, X.desc, 0, T, side)
+        ev_drawn[i % 2].record(side)
+
+    def train(i, timed):
+        X = bufs[i % 2]
+        stream.wait_event(ev_drawn[i % 2])
+        for t_ in (X.v, X.a, X.y, X.ysum, X.x_bits, X.z_bits):
             t_.zero_()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if timed else None
         if ev:
             ev[0].record(stream)
-        abi.snn_step_neurons(cls.handle, batch.desc, 0, T, stream)
+        abi.snn_step_neurons_ex(cls.handle, X.desc, 0, T, abi.SNN_STEP_INPUTS_READY, stream)
         if ev:
             ev[1].record(stream)
-        abi.snn_eprop_update(cls.handle, batch.desc, abi.SNN_EPROP_GRAD, None, stream)
+        abi.snn_eprop_update(cls.handle, X.desc, abi.SNN_EPROP_GRAD, None, stream)
         if ev:
             ev[2].record(stream)
-        abi.snn_eprop_update(cls.handle, batch.desc, abi.SNN_EPROP_APPLY, net.adam_params(lr, i + 1, l1=l1), stream)
+        abi.snn_eprop_update(cls.handle, X.desc, abi.SNN_EPROP_APPLY, net.adam_params(lr, i + 1, l1=l1), stream)
         if ev:
             ev[3].record(stream)
         abi.snn_rewire_deepr(cls.w_in.handle, i, stats[0], stream)
@@ -254,6 +274,16 @@ def run_ours(args, world, rank, local):
         if ev:
             ev[4].record(stream)
             ev_pairs.append(ev)
+        ev_free[i % 2].record(stream)
+
+    def run(lo, hi, desc, timed, after=None):
+        # steps lo .. hi-1; the inputs of step lo were drawn before, those of hi are drawn here
+        for i in range(lo, hi):
+            train(i, timed)
+            draw(i + 1, desc[i + 1])
+            if after:
+                after(i)
+        stream.wait_stream(side)
 
     def barrier():
         if world > 1:
@@ -262,8 +292,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
 
     # warm-up
-    for i in range(args.warmup):
-        one_step(i, d_desc[i], False)
+    draw(0, d_desc[0])
+    run(0, args.warmup, d_desc, False)
     barrier()
     # ---- device-resident timed region
     stats.zero_()
@@ -271,9 +301,7 @@ def run_ours(args, world, rank, local):
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         start.record(stream)
-        for k in range(args.steps):
-            i = args.warmup + k
-            one_step(i, d_desc[i], True)
+        run(args.warmup, n_total, d_desc, True)
         end.record(stream)
         barrier()
     ms = start.elapsed_time(end)
@@ -283,22 +311,25 @@ def run_ours(args, world, rank, local):
         for c in range(4):
             per_call[c] += ev[c].elapsed_time(ev[c + 1])
     per_call = [x / len(ev_pairs) for x in per_call]
+    batch = bufs[(n_total - 1) % 2]
     events, spikes = count_events(batch, cls, dev)
     rewired = int(stats[:, 0].sum().item() + stats[:, 1].sum().item())     # removed + formed, timed batches
     active = int(cls.w_in.row_len.sum().item() + cls.w_rec.row_len.sum().item())
     # ---- end-to-end leg through the public calls, host buffers each step
     out_host = torch.empty((B, W["K"]), dtype=torch.float32).pin_memory()
     stats_host = torch.empty((2, 4), dtype=torch.int64).pin_memory()
+    draw(n_total, h_desc[n_total])
     barrier()
+
+    def read_back(i):
+        out_host.copy_(bufs[i % 2].ysum, non_blocking=True)
+        stats_host.copy_(stats, non_blocking=True)
+        stream.synchronize()
+
     e2e_start, e2e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_start.record(stream)
     t_host0 = time.perf_counter()
-    for k in range(args.steps):
-        i = n_total + k
-        one_step(i, h_desc[i], False)
-        out_host.copy_(batch.ysum, non_blocking=True)
-        stats_host.copy_(stats, non_blocking=True)
-        stream.synchronize()
+    run(n_total, n_total + args.steps, h_desc, False, after=read_back)
     e2e_end.record(stream)
     barrier()
     e2e_ms = max(e2e_start.elapsed_time(e2e_end), (time.perf_counter() - t_host0) * 1e3)

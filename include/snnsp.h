@@ -60,7 +60,7 @@ typedef void* snn_stream;        /* cudaStream_t */
 /* Message for the most recent failing call on this host thread ("" if none). */
 const char* snn_last_error(void);
 /* ABI version of this header (bumped on any incompatible change). */
-int32_t snn_abi_version(void);   /* 4 */
+int32_t snn_abi_version(void);   /* 5 */
 
 /* ==================================================================================
  * Ragged sparse matrix (Sec. 2.1, Fig. 1; DEEP R bitfields Sec. 2.1.2, Fig. 2)
@@ -254,6 +254,21 @@ snn_status snn_destroy_classifier(snn_classifier* c);
  * runs with the value clamped into range. */
 snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
                             snn_stream stream);
+
+/* Draw the input spikes x^t of steps t0 .. t0+n_steps-1 into b->x_rec (the first part
+ * of snn_step_neurons, as its own launch).  Needs labels, bin_len, trial_ids (and
+ * trial_T when set) of b; touches nothing else.  A caller can draw the next batch's
+ * inputs on another stream while the current batch trains, since they depend on
+ * (trial, step, channel) only. */
+snn_status snn_draw_inputs(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
+                           snn_stream stream);
+
+#define SNN_STEP_INPUTS_READY 1   /* x_rec already holds the steps' inputs (snn_draw_inputs) */
+/* snn_step_neurons with flags: SNN_STEP_INPUTS_READY skips the input draw; every other
+ * flag bit is SNN_EINVAL.  Results are identical to snn_step_neurons when x_rec holds
+ * what snn_draw_inputs wrote for the same batch and steps. */
+snn_status snn_step_neurons_ex(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
+                               int32_t flags, snn_stream stream);
 
 /* e-prop learning (Sec. 2.2.1 eligibility-trace equations, summed over trials).
  * SNN_EPROP_GRAD: from the records of a finished batch (all T steps) computes

@@ -18,12 +18,14 @@ SNN_OK, SNN_EINVAL, SNN_ENOMEM, SNN_ECAPACITY, SNN_ECUDA, SNN_ETIMEOUT, SNN_ESTA
 SNN_F32, SNN_F64 = 0, 1
 SNN_EPROP_GRAD, SNN_EPROP_APPLY = 0, 1
 SNN_FIXED_FRAC_BITS = 40
+SNN_STEP_INPUTS_READY = 1
 
 EXPORTED = [
     "snn_last_error", "snn_abi_version", "snn_create_ragged", "snn_destroy_ragged", "snn_ragged_status",
     "snn_propagate", "snn_rewire_deepr", "snn_create_classifier", "snn_destroy_classifier", "snn_step_neurons",
     "snn_eprop_update", "snn_topo_input", "snn_topo_neurons", "snn_stdp_update", "snn_rewire_topo", "snn_topo_run",
     "snn_philox", "snn_rewire_deepr_noalloc", "snn_classifier_set_schedule", "snn_rewire_deepr_dev",
+    "snn_draw_inputs", "snn_step_neurons_ex",
 ]
 
 
@@ -122,6 +124,8 @@ def load() -> C.CDLL:
         "snn_rewire_deepr_noalloc": (i32, [P(RaggedDesc), i64, vp, vp, vp]),
         "snn_classifier_set_schedule": (i32, [vp, i32]),
         "snn_rewire_deepr_dev": (i32, [vp, vp, vp, vp]),
+        "snn_draw_inputs": (i32, [vp, P(Batch), i32, i32, vp]),
+        "snn_step_neurons_ex": (i32, [vp, P(Batch), i32, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +209,14 @@ def snn_destroy_classifier(h: int) -> None:
 
 def snn_step_neurons(h: int, batch: Batch, t0: int, n_steps: int, stream=None) -> None:
     check(load().snn_step_neurons(h, C.byref(batch), t0, n_steps, stream_ptr(stream)))
+
+
+def snn_draw_inputs(h: int, batch: Batch, t0: int, n_steps: int, stream=None) -> None:
+    check(load().snn_draw_inputs(h, C.byref(batch), t0, n_steps, stream_ptr(stream)))
+
+
+def snn_step_neurons_ex(h: int, batch: Batch, t0: int, n_steps: int, flags: int, stream=None) -> None:
+    check(load().snn_step_neurons_ex(h, C.byref(batch), t0, n_steps, flags, stream_ptr(stream)))
 
 
 def snn_eprop_update(h: int, batch: Batch | None, phase: int, adam: Adam | None, stream=None) -> None:

@@ -770,10 +770,9 @@ static snn_status refresh_fixed(snn_classifier* c, cudaStream_t s) {
     return SNN_OK;
 }
 
-template <typename real>
-static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int n_steps, cudaStream_t s) {
+static snn_status draw_impl(snn_classifier* c, const snn_batch* bt, int t0, int n_steps, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
-    const int Win = (d.n_in + 31) / 32, Wh = (d.N + 31) / 32;
+    const int Win = (d.n_in + 31) / 32;
     InputParams ip;
     ip.n_in = d.n_in;
     ip.Win = Win;
@@ -794,6 +793,18 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     const long long groups = (long long)bt->B * n_steps * Win * 4;
     k_input<<<ceil_div(groups, 256), 256, 0, s>>>(ip);
     SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+template <typename real>
+static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int n_steps, bool inputs_ready,
+                            cudaStream_t s) {
+    const snn_classifier_desc& d = c->d;
+    const int Win = (d.n_in + 31) / 32, Wh = (d.N + 31) / 32;
+    if (!inputs_ready) {
+        const snn_status st = draw_impl(c, bt, t0, n_steps, s);
+        if (st != SNN_OK) return st;
+    }
 
     FwdParams<real> p;
     p.n_in = d.n_in;
@@ -957,9 +968,162 @@ __global__ void __launch_bounds__(BWD_THREADS)
     }
 }
 
+// ---- bulk-copy staging of the adjoint scan (TMA 1-D copies into shared memory)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the barrier's phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+    uint32_t done = 0;
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+    return done != 0;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) that
+// completes its byte count on the barrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// FP32 adjoint scan, two neurons per thread, psi and D staged by bulk copies: CTA =
+// (trial, 256 neurons); steps walked backwards in chunks of BB_S, BB_NST chunks in
+// flight.  Thread 0 issues, per chunk, one bulk copy per step row of the CTA's psi slice
+// (up to 1 KB) and one for the chunk's D rows, all completing on that stage's mbarrier;
+// every thread reads its neuron pair's psi from shared memory.  The same recurrences
+// and arithmetic as k_backward_x2 (bit-identical results).  Needs N % 4 == 0.  A wait
+// that gives up sets SNN_ETIMEOUT's flag, lets the copies in flight land (bounded) and
+// ends the CTA.
+constexpr bool BWD_BULK = true;
+constexpr int BB_THREADS = 128;
+constexpr int BB_S = 8;
+constexpr int BB_NST = 3;
+constexpr int BB_WAIT = 1 << 22;
+
+template <int KV>
+__global__ void __launch_bounds__(BB_THREADS)
+    k_backward_bulk(const float* __restrict__ psi, const float* __restrict__ Dg, const float* __restrict__ W_out,
+                    float* __restrict__ delta, int T, int N, int K, float alpha, float rho, float beta,
+                    int32_t* status) {
+    constexpr int KP = 4 * KV;
+    __shared__ __align__(128) float ps_s[BB_NST][BB_S][2 * BB_THREADS];
+    __shared__ __align__(16) float D_s[BB_NST][BB_S][KP];
+    __shared__ __align__(8) uint64_t bar[BB_NST];
+    const int tid = threadIdx.x;
+    const int j0 = blockIdx.x * 2 * BB_THREADS;             // first neuron of the CTA
+    const int ncols = min(2 * BB_THREADS, N - j0);          // multiple of 4 (N % 4 == 0)
+    const int jp = blockIdx.x * BB_THREADS + tid;            // neuron pair
+    const int N2 = N >> 1;
+    const int b = blockIdx.y;
+    const bool ok = jp < N2;
+    unsigned long long wa[KP / 2], wb[KP / 2];
+#pragma unroll
+    for (int m = 0; m < KP / 2; ++m) {
+        const int k0 = 2 * m, k1 = 2 * m + 1;
+        const float a0 = (k0 < K && ok) ? W_out[(size_t)k0 * N + 2 * jp] : 0.f;
+        const float a1 = (k1 < K && ok) ? W_out[(size_t)k1 * N + 2 * jp] : 0.f;
+        const float b0 = (k0 < K && ok) ? W_out[(size_t)k0 * N + 2 * jp + 1] : 0.f;
+        const float b1 = (k1 < K && ok) ? W_out[(size_t)k1 * N + 2 * jp + 1] : 0.f;
+        wa[m] = f2_pack(a0, a1);
+        wb[m] = f2_pack(b0, b1);
+    }
+    const float* pb = psi + (size_t)b * T * N + j0;
+    const float* Db = Dg + (size_t)b * T * KP;
+    unsigned long long* db = (unsigned long long*)delta + (size_t)b * T * N2 + (ok ? jp : 0);
+    const int n_chunks = (T + BB_S - 1) / BB_S;
+    if (tid == 0) {
+        for (int st = 0; st < BB_NST; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // chunk q (0 = last in time) -> chunk index n_chunks-1-q, stage q % BB_NST
+    auto issue = [&](int q) {
+        const int ch = n_chunks - 1 - q, st = q % BB_NST;
+        const int tb = ch * BB_S, nt = min(BB_S, T - tb);
+        mbar_expect_tx(&bar[st], (uint32_t)(nt * ncols * 4 + nt * KP * 4));
+        for (int r = 0; r < nt; ++r)
+            bulk_g2s(ps_s[st][r], pb + (size_t)(tb + r) * N, (uint32_t)(ncols * 4), &bar[st]);
+        bulk_g2s(D_s[st][0], Db + (size_t)tb * KP, (uint32_t)(nt * KP * 4), &bar[st]);
+    };
+    if (tid == 0)
+        for (int q = 0; q < BB_NST && q < n_chunks; ++q) issue(q);
+    const unsigned long long alpha2 = f2_pack(alpha, alpha), beta2 = f2_pack(beta, beta);
+    const unsigned long long rho2 = f2_pack(rho, rho), nbeta2 = f2_pack(-beta, -beta);
+    unsigned long long lam_next = 0, psi_next = 0, mu = 0, h_next = 0, dl = 0;
+    for (int q = 0; q < n_chunks; ++q) {
+        const int ch = n_chunks - 1 - q, st = q % BB_NST;
+        const int tb = ch * BB_S, nt = min(BB_S, T - tb);
+        const bool got = mbar_wait(&bar[st], (uint32_t)((q / BB_NST) & 1), BB_WAIT);
+        if (__syncthreads_or(!got)) {
+            // give up: record it, let every copy still in flight land, end the CTA
+            if (tid == 0) {
+                atomicOr(status, ST_TIMEOUT);
+                for (int q2 = q; q2 < n_chunks && q2 < q + BB_NST; ++q2)
+                    mbar_wait(&bar[q2 % BB_NST], (uint32_t)((q2 / BB_NST) & 1), BB_WAIT);
+            }
+            __syncthreads();
+            return;
+        }
+#pragma unroll
+        for (int r = BB_S - 1; r >= 0; --r) {
+            if (r < nt) {
+                const int t = tb + r;
+                const unsigned long long ps = ((const unsigned long long*)ps_s[st][r])[tid];
+                const unsigned long long* Dr = (const unsigned long long*)D_s[st][r];
+                unsigned long long sa = 0, sb = 0;
+#pragma unroll
+                for (int m = 0; m < KP / 2; ++m) {
+                    const unsigned long long dk = Dr[m];
+                    sa = f2_fma(wa[m], dk, sa);
+                    sb = f2_fma(wb[m], dk, sb);
+                }
+                const unsigned long long lam = f2_pack(f2_lo(sa) + f2_hi(sa), f2_lo(sb) + f2_hi(sb));
+                if (t == T - 1) {
+                    mu = 0;
+                    dl = 0;
+                } else {
+                    mu = f2_fma(beta2, f2_mul(lam_next, psi_next), f2_mul(f2_fma(nbeta2, psi_next, rho2), mu));
+                    dl = f2_fma(alpha2, dl, h_next);
+                }
+                const unsigned long long h = f2_mul(ps, f2_sub(lam, mu));
+                if (ok) db[(size_t)t * N2] = dl;
+                h_next = h;
+                lam_next = lam;
+                psi_next = ps;
+            }
+        }
+        __syncthreads();                                     // stage st fully read
+        if (tid == 0 && q + BB_NST < n_chunks) issue(q + BB_NST);
+    }
+}
+
 template <typename real, int KV>
 static void launch_backward(const snn_classifier* c, const snn_batch* bt, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
+    if (std::is_same<real, float>::value && d.N % 4 == 0 && BWD_BULK) {
+        dim3 g(ceil_div(d.N, 2 * BB_THREADS), bt->B);
+        k_backward_bulk<KV><<<g, BB_THREADS, 0, s>>>((const float*)bt->psi_rec, (const float*)bt->Dout,
+                                                      (const float*)d.W_out, (float*)bt->delta, bt->T, d.N, d.K,
+                                                      (float)c->alpha, (float)c->rho, (float)d.beta,
+                                                      d.w_rec->status);
+        return;
+    }
     if (std::is_same<real, float>::value && d.N % 2 == 0) {
         dim3 g(ceil_div(d.N / 2, BWD_THREADS), bt->B);
         k_backward_x2<KV><<<g, BWD_THREADS, 0, s>>>((const float*)bt->psi_rec, (const float*)bt->Dout,
@@ -1142,16 +1306,35 @@ static snn_status check_batch(const snn_classifier* c, const snn_batch* b) {
     return SNN_OK;
 }
 
-snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps, snn_stream stream) {
+snn_status snn_step_neurons_ex(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps, int32_t flags,
+                               snn_stream stream) {
     clear_error();
     SNN_REQUIRE(c, "snn_step_neurons: NULL classifier");
     snn_status st = check_batch(c, b);
     if (st != SNN_OK) return st;
     SNN_REQUIRE(t0 >= 0 && n_steps >= 0 && t0 + n_steps <= b->T, "snn_step_neurons: steps [%d, %d) outside [0, %d)",
                 t0, t0 + n_steps, b->T);
+    SNN_REQUIRE((flags & ~SNN_STEP_INPUTS_READY) == 0, "snn_step_neurons_ex: unknown flags 0x%x", flags);
     if (n_steps == 0) return SNN_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    return c->d.dtype == SNN_F32 ? step_impl<float>(c, b, t0, n_steps, s) : step_impl<double>(c, b, t0, n_steps, s);
+    const bool ready = (flags & SNN_STEP_INPUTS_READY) != 0;
+    return c->d.dtype == SNN_F32 ? step_impl<float>(c, b, t0, n_steps, ready, s)
+                                 : step_impl<double>(c, b, t0, n_steps, ready, s);
+}
+
+snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps, snn_stream stream) {
+    return snn_step_neurons_ex(c, b, t0, n_steps, 0, stream);
+}
+
+snn_status snn_draw_inputs(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(c, "snn_draw_inputs: NULL classifier");
+    snn_status st = check_batch(c, b);
+    if (st != SNN_OK) return st;
+    SNN_REQUIRE(t0 >= 0 && n_steps >= 0 && t0 + n_steps <= b->T, "snn_draw_inputs: steps [%d, %d) outside [0, %d)",
+                t0, t0 + n_steps, b->T);
+    if (n_steps == 0) return SNN_OK;
+    return draw_impl(c, b, t0, n_steps, (cudaStream_t)stream);
 }
 
 snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase, const snn_adam* adam,

@@ -246,3 +246,28 @@ def test_training_run_tiny_config(dtype):
         assert agree >= 0.999
     assert abs(np.mean(np.array(g_preds) == np.array([tb.labels[0] for tb in batches]))
                - np.mean(np.array(preds) == np.array([tb.labels[0] for tb in batches]))) <= 0.005 + 1e-12
+
+
+def test_predrawn_inputs_give_identical_records():
+    """snn_draw_inputs (on another stream) + snn_step_neurons_ex(INPUTS_READY) give the
+    same records, bit for bit, as snn_step_neurons drawing its own inputs; unknown flag
+    bits are rejected."""
+    from paper_2510_19764_gb300 import abi, net
+    T, B = 300, 6
+    s = _setups.classifier(seed=3, n_in=64, N=128, K=4, lif=False, v_thr=0.6, T=T, max_B=B, spoken=True,
+                           n_bins=5, n_classes=4)
+    tb = synth.trial_batch(s.task, 3, 0, B)
+    ref = net.DeviceBatch(s.dev, tb.labels, tb.bin_len, tb.trial_ids, T, record_state=True)
+    abi.snn_step_neurons(s.dev.handle, ref.desc, 0, T)
+    got = net.DeviceBatch(s.dev, tb.labels, tb.bin_len, tb.trial_ids, T, record_state=True)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    abi.snn_draw_inputs(s.dev.handle, got.desc, 0, T, side)
+    side.synchronize()
+    abi.snn_step_neurons_ex(s.dev.handle, got.desc, 0, T, abi.SNN_STEP_INPUTS_READY)
+    torch.cuda.synchronize()
+    for k in ("x_rec", "z_rec", "psi_rec", "d_rec", "v_rec", "a_rec", "y_rec", "ysum", "v", "a"):
+        assert torch.equal(getattr(ref, k), getattr(got, k)), k
+    assert int(net.spikes_from_bits(net.u32_to_numpy(got.z_rec), 128).sum()) > 0
+    with pytest.raises(abi.SnnError):
+        abi.snn_step_neurons_ex(s.dev.handle, got.desc, 0, T, 2)
