@@ -30,10 +30,8 @@ namespace snn {
 
 template <typename real>
 struct FwdParams {
-    int n_in, N, K, Win, Wh, T, t0, n_steps, n_classes;
+    int n_in, N, K, Win, Wh, T, t0, n_steps;
     real alpha, rho, beta, v_thr, psi_scale, inv_vthr;
-    int32_t* status;
-    const int32_t* labels;
     const int32_t* in_len;
     const int32_t* rec_len;
     const unsigned long long* pk;   // packed rows (see k_pack), Cf slots each
@@ -815,15 +813,12 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.T = bt->T;
     p.t0 = t0;
     p.n_steps = n_steps;
-    p.n_classes = d.n_classes;
     p.alpha = (real)c->alpha;
     p.rho = (real)c->rho;
     p.beta = (real)d.beta;
     p.v_thr = (real)d.v_thr;
     p.psi_scale = (real)(0.3 / d.v_thr);
     p.inv_vthr = (real)(1.0 / d.v_thr);
-    p.status = d.w_in->status;
-    p.labels = bt->labels;
     p.in_len = d.w_in->d.row_len;
     p.rec_len = d.w_rec->d.row_len;
     p.pk = (const unsigned long long*)c->pk;
