@@ -446,6 +446,7 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 constexpr int FUSED_THREADS = 512;
+constexpr int TOPO_FUSED_MAX_NPT = 1;   // neurons per thread the fused loop accepts (1, 2 or 4)
 
 template <int NPT>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) k_topo_fused(TopoRun r) {
@@ -738,8 +739,11 @@ snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_
         if (smem < (size_t)2 * Nw * 4) smem = (size_t)2 * Nw * 4;
         // one neuron per thread: beyond one cluster's threads the per-step launches spread
         // STDP over the whole GPU and win
+        // neurons per thread: one while the cluster has a thread per neuron, else up to
+        // TOPO_FUSED_MAX_NPT (beyond that the per-step launches spread STDP wider)
         const int cs = smem <= 227 * 1024 ? fused_cluster_size<1>(smem, s) : 0;
-        if (cs >= 2 && N <= cs * FUSED_THREADS) {
+        const int npt = cs >= 2 ? (N + cs * FUSED_THREADS - 1) / (cs * FUSED_THREADS) : 0;
+        if (cs >= 2 && npt <= TOPO_FUSED_MAX_NPT) {
             run.k = topo_consts(p);
             for (int m = 0; m < 2; ++m) {
                 snn_ragged* r = m == 0 ? ff : lat;
@@ -767,7 +771,9 @@ snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_
             for (int64_t t = t0; t < t0 + n_steps; t += 1000) {
                 run.t0 = t;
                 run.n_steps = (int)(t0 + n_steps - t < 1000 ? t0 + n_steps - t : 1000);
-                if ((e = launch_fused<1>(run, cs, smem, s)) != SNN_OK) return e;
+                e = npt == 1 ? launch_fused<1>(run, cs, smem, s)
+                             : npt == 2 ? launch_fused<2>(run, cs, smem, s) : launch_fused<4>(run, cs, smem, s);
+                if (e != SNN_OK) return e;
             }
             return SNN_OK;
         }
