@@ -533,7 +533,7 @@ def run_topo(args):
     return {"workload": "topo", "metric": "simulated steps/s (1 ms steps)", "L": L, "neurons_per_sheet": N,
             "steps": n, "steps_per_s": round(n / (ms / 1e3), 1), "realtime_factor": round(n / (ms / 1e3) / 1000.0, 2),
             "ms_per_1000_steps": round(ms / n * 1000, 3),
-            "path": "one cluster launch per 1000 steps" if N <= 4096 else "per-step launches (sheet larger than a cluster)",
+            "path": "one thread-block-cluster launch per 1000 steps (up to 4 neurons per thread)",
             "rewire_ff": dict(zip(["removed", "formed", "overflow", "attempts"], stats_ff)),
             "rewire_lat": dict(zip(["removed", "formed", "overflow", "attempts"], stats_lat))}
 

@@ -446,7 +446,7 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 constexpr int FUSED_THREADS = 512;
-constexpr int TOPO_FUSED_MAX_NPT = 1;   // neurons per thread the fused loop accepts (1, 2 or 4)
+constexpr int TOPO_FUSED_MAX_NPT = 4;   // neurons per thread the fused loop accepts (1, 2 or 4)
 
 template <int NPT>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) k_topo_fused(TopoRun r) {
@@ -741,9 +741,12 @@ snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_
         // STDP over the whole GPU and win
         // neurons per thread: one while the cluster has a thread per neuron, else up to
         // TOPO_FUSED_MAX_NPT (beyond that the per-step launches spread STDP wider)
-        const int cs = smem <= 227 * 1024 ? fused_cluster_size<1>(smem, s) : 0;
+        int cs = smem <= 227 * 1024 ? fused_cluster_size<1>(smem, s) : 0;
         const int npt = cs >= 2 ? (N + cs * FUSED_THREADS - 1) / (cs * FUSED_THREADS) : 0;
-        if (cs >= 2 && npt <= TOPO_FUSED_MAX_NPT) {
+        // the chosen instantiation gets its own launch attributes and cluster size
+        if (npt == 2) cs = fused_cluster_size<2>(smem, s);
+        if (npt > 2 && npt <= 4) cs = fused_cluster_size<4>(smem, s);
+        if (cs >= 2 && npt <= TOPO_FUSED_MAX_NPT && N <= (npt > 2 ? 4 : npt) * cs * FUSED_THREADS) {
             run.k = topo_consts(p);
             for (int m = 0; m < 2; ++m) {
                 snn_ragged* r = m == 0 ? ff : lat;
