@@ -34,6 +34,10 @@ from . import abi, net
 N_IN, K_OUT, N_CLASSES, N_BINS, T_MAX = 700, 20, 20, 10, 1000
 
 
+class AdmissionError(RuntimeError):
+    """A request can never be admitted (its slot or fine-tuning copy exceeds the budget)."""
+
+
 @dataclass
 class Request:
     rid: int
@@ -241,6 +245,11 @@ class Engine:
                         self.stats["launches"] += 1
                         self.stats["max_batch_seen"] = max(self.stats["max_batch_seen"], len(take))
                 pending = rest
+                if pending and not flights:
+                    # nothing in flight will free a slot or memory: these requests can never start
+                    need = max((64 << 20) if r.finetune else self.slots[r.model][0].bytes for r in pending)
+                    raise AdmissionError(f"{len(pending)} request(s) cannot be admitted: one needs {need} bytes "
+                                         f"of device memory, the budget is {self.mem_budget} bytes")
             self.stats["max_in_flight"] = max(self.stats["max_in_flight"], len(flights))
             if not flights and qi < len(queue) and not pending and realtime:
                 wait = queue[qi].arrival - (time.perf_counter() - t_start)

@@ -46,3 +46,21 @@ def test_realtime_loop_reports_latency():
     res = eng.run(reqs, realtime=True)
     s = serve.latency_summary(res, max(r.latency for r in res) + reqs[-1].arrival)
     assert s["requests"] == 60 and 0 < s["p50_ms"] <= s["p99_ms"]
+
+
+def test_admission_failure_is_reported_not_hung():
+    """Host-side fault: a memory budget too small for any slot or fine-tuning copy.  The
+    loop raises AdmissionError at once instead of waiting for memory nothing will free;
+    a budget that fits one slot at a time still serves everything, one launch at a time."""
+    from paper_2510_19764_gb300 import serve
+    task = synth.spoken_digit_task(5, n_in=serve.N_IN, n_classes=serve.N_CLASSES, T=serve.T_MAX, n_bins=serve.N_BINS)
+    models = [serve.Model(0, 64, task, max_batch=4)]
+    reqs = serve.poisson_requests(6, 1000.0, 1, seed=4, finetune_frac=0.0, t_range=(20, 40))
+    with pytest.raises(serve.AdmissionError):
+        serve.Engine(models, max_batch=4, slots_per_model=1, n_streams=1, mem_budget=1024).run(reqs, realtime=False)
+    eng = serve.Engine(models, max_batch=4, slots_per_model=2, n_streams=2, mem_budget=1024)
+    one_slot = eng.slots[0][0].bytes
+    eng.mem_budget = one_slot
+    res = eng.run(reqs, realtime=False)
+    assert [r.rid for r in res] == list(range(len(reqs)))
+    assert eng.stats["max_in_flight"] == 1
