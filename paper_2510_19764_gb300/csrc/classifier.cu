@@ -81,9 +81,13 @@ __device__ __forceinline__ void acc_add(unsigned* acc, unsigned long long w) {
     atomicAdd(a, __funnelshift_r(lo, hi, 20));            // bits 51..20
     atomicAdd(a + 1, lo & 0xFFFFFu);                      // bits 19..0
 }
-__device__ __forceinline__ long long acc_value(const long long* acc) {
+// The accumulated sum 2^20 H + L in real units (40 fractional bits): H 2^-20 + L 2^-40,
+// each product exact, one rounding in the sum (for double the same value as converting
+// the 64-bit integer first).
+template <typename real>
+__device__ __forceinline__ real acc_real(const long long* acc) {
     const unsigned* a = (const unsigned*)acc;
-    return (long long)(int)a[0] * (1ll << 20) + (long long)a[1];
+    return (real)(int)a[0] * (real)9.5367431640625e-07 + (real)a[1] * (real)9.094947017729282e-13;
 }
 
 // Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             xw[lane] = 0u;
         }
         if (warp == RO_WARP && lane < K) {         // y^t from the readout sums W_out z^{t-1}
-            yk = p.alpha * yk + from_fixed<real>(acc_value(Iacc + N + 32 + lane)) + bk;
+            yk = p.alpha * yk + acc_real<real>(Iacc + N + 32 + lane) + bk;
             Iacc[N + 32 + lane] = 0;
             ysk += yk;
             if (d_b) d_b[(size_t)t * K + lane] = yk;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
             const int j = tid + q * TH;
             bool spk = false;
             if (j < N) {
-                const real I = from_fixed<real>(acc_value(Iacc + j));
+                const real I = acc_real<real>(Iacc + j);
                 Iacc[j] = 0;
                 const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
                 const real v = p.alpha * (zp ? vr[q] - p.v_thr : vr[q]) + I;
