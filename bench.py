@@ -53,13 +53,20 @@ def parse():
     ap.add_argument("--sample-steps", type=int, default=600, help="oracle sample: steps of one trial")
     ap.add_argument("--batch", type=int, default=512, help="trials per batch (512 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
-    ap.add_argument("--workload", default="classifier", choices=["classifier", "batched", "serve", "topo", "kernels"],
+    ap.add_argument("--workload", default="classifier",
+                    choices=["classifier", "batched", "serve", "topo", "topo-evolution", "kernels"],
                     help="classifier (default, the benchmark line); batched: 64 uneven instances, plain vs "
-                         "graph-batched; serve: request loop latency; topo: topographic map steps/s")
+                         "graph-batched; serve: request loop latency; topo: topographic map steps/s; "
+                         "topo-evolution: connectivity evolution of the map over a long run")
     ap.add_argument("--scale", type=int, default=2, help="topo: grid side 16*scale")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 4, 8, 16],
                     help="forward row schedule (warps per trial); 0 = the library default")
     ap.add_argument("--topo-steps", type=int, default=10000)
+    ap.add_argument("--evolution-steps", type=int, default=100000,
+                    help="topo-evolution: steps (time bins of 200 ms)")
+    ap.add_argument("--topo-setting", default="disc", choices=["disc", "paper"],
+                    help="topo / topo-evolution: disc = 1 ms steps with the disc input; paper = the printed "
+                         "setting, h = 0.1 ms, Gaussian input, 20 ms stimulus interval, rewiring every 1 ms")
     return ap.parse_args()
 
 
@@ -238,7 +245,7 @@ def run_ours(args, world, rank, local):
     ev_drawn = [torch.cuda.Event() for _ in range(NB)]    # buffer's inputs drawn
     for e in ev_free:
         e.record(stream)
-    stats = torch.zeros((2, 4), dtype=torch.int64, device=dev)
+    stats = torch.zeros((n_total, 2, 4), dtype=torch.int64, device=dev)   # DEEP R counts per batch
     lr, l1 = 1e-3, 1e-5
     calls = ["snn_step_neurons", "snn_eprop_update(GRAD)", "snn_eprop_update(APPLY)", "snn_rewire_deepr"]
     ev_pairs = []
@@ -271,8 +278,8 @@ def run_ours(args, world, rank, local):
         abi.snn_eprop_update(cls.handle, X.desc, abi.SNN_EPROP_APPLY, net.adam_params(lr, i + 1, l1=l1), stream)
         if ev:
             ev[3].record(stream)
-        abi.snn_rewire_deepr(cls.w_in.handle, i, stats[0], stream)
-        abi.snn_rewire_deepr(cls.w_rec.handle, i, stats[1], stream)
+        abi.snn_rewire_deepr(cls.w_in.handle, i, stats[i, 0], stream)
+        abi.snn_rewire_deepr(cls.w_rec.handle, i, stats[i, 1], stream)
         if ev:
             ev[4].record(stream)
             ev_pairs.append(ev)
@@ -326,8 +333,11 @@ def run_ours(args, world, rank, local):
     last_call = [ev_pairs[-1][c].elapsed_time(ev_pairs[-1][c + 1]) for c in range(4)]
     batch = bufs[(n_total - 1) % NB]
     events, spikes = count_events(batch, cls, dev)
-    rewired = int(stats[:, 0].sum().item() + stats[:, 1].sum().item())     # removed + formed, timed batches
+    timed_stats = stats[args.warmup:n_total].cpu()
+    rewired = int(timed_stats[:, :, :2].sum())                              # removed + formed, timed batches
     active = int(cls.w_in.row_len.sum().item() + cls.w_rec.row_len.sum().item())
+    # fraction of the sparse synapses DEEP R replaced in each timed batch (Fig. 6's curve)
+    rewired_fraction = [round(float(x) / active, 6) for x in timed_stats[:, :, 0].sum(1).tolist()]
     # ---- end-to-end leg through the public calls, host buffers each step: the same
     # batches from the same state as the timed region
     out_host = torch.empty((B, W["K"]), dtype=torch.float32).pin_memory()
@@ -340,7 +350,7 @@ def run_ours(args, world, rank, local):
 
     def read_back(i):
         out_host.copy_(bufs[i % NB].ysum, non_blocking=True)
-        stats_host.copy_(stats, non_blocking=True)
+        stats_host.copy_(stats[i], non_blocking=True)
         stream.synchronize()
 
     e2e_start, e2e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -389,6 +399,8 @@ def run_ours(args, world, rank, local):
         "synapse_updates_per_s": round(active * B * T * world / (ms_max / 1e3 / args.steps), 1),
         # DEEP R: (removed + formed) over the rewiring calls' own time
         "rewired_synapses_per_s": round(rewired / (per_call[3] * args.steps / 1e3), 1) if per_call[3] > 0 else None,
+        "deepr_rewired_fraction": {"per_batch": rewired_fraction,
+                                   "mean": round(sum(rewired_fraction) / len(rewired_fraction), 6)},
         "per_call_ms": {c: round(x, 4) for c, x in zip(calls, per_call)},
         "roofline": {"kernel": calls[dom], "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
@@ -515,15 +527,13 @@ def run_serve(args):
     return out
 
 
-def run_topo(args):
-    """Topographic map (two L x L sheets, L = 16 * scale): steps/s of the full step
-    sequence (input, propagation, conductance LIF, STDP on both projections, rewiring
-    every 10 steps with 10 s^2 attempts per projection)."""
-    import torch
+def topo_setup(args):
+    """The topographic map of the topo workloads: two L x L sheets (L = 16 * scale),
+    capacity 64, pairwise-Bernoulli initial connectivity, 10 s^2 attempts per projection
+    per rewiring.  Returns (L, N, dt_ms, device projections, params, rewiring params,
+    state)."""
     import synth
-    from paper_2510_19764_gb300 import abi, build, net
-    build.build()
-    abi.load()
+    from paper_2510_19764_gb300 import net
     L = 16 * args.scale
     N = L * L
     C = 64
@@ -531,29 +541,133 @@ def run_topo(args):
     lat = synth.topo_initial(args.seed + 2, L, 1.0, 1.0, C, 0.2)
     dff = net.DeviceRagged(ff.row_len, ff.ind, ff.w, N, seed=11)
     dlat = net.DeviceRagged(lat.row_len, lat.ind, lat.w, N, seed=12)
-    tp = net.topo_params(L=L, L_f=16 if args.scale > 2 else L)
+    L_f = 16 if args.scale > 2 else L
+    if args.topo_setting == "paper":
+        dt = 0.1
+        tp = net.topo_params(L=L, L_f=L_f, dt=dt, t_stim=200, f_base=5.0, f_in=152.8, sigma_stim=2.0)
+    else:
+        dt = 1.0
+        tp = net.topo_params(L=L, L_f=L_f)
     n_att = 10 * args.scale * args.scale
-    rw_ff = net.topo_rewire(L, 0.16, 2.5, n_att)
-    rw_lat = net.topo_rewire(L, 1.0, 1.0, n_att)
+    rw = {"ff": net.topo_rewire(L, 0.16, 2.5, n_att), "lat": net.topo_rewire(L, 1.0, 1.0, n_att)}
     st = net.DeviceTopoState(N, -70.0)
+    return L, N, dt, {"ff": dff, "lat": dlat}, tp, rw, st
+
+
+def run_topo(args):
+    """Topographic map (two L x L sheets, L = 16 * scale): steps/s of the full step
+    sequence (input, propagation, conductance LIF, STDP on both projections, rewiring
+    every 10 steps with 10 s^2 attempts per projection)."""
+    import torch
+    from paper_2510_19764_gb300 import abi, build
+    build.build()
+    abi.load()
+    L, N, dt, dev, tp, rw, st = topo_setup(args)
     s_ff = torch.zeros(4, dtype=torch.int64, device="cuda")
     s_lat = torch.zeros(4, dtype=torch.int64, device="cuda")
-    abi.snn_topo_run(tp, st.desc, dff.handle, dlat.handle, rw_ff, rw_lat, 5, 10, 0, 200, s_ff, s_lat)
+    abi.snn_topo_run(tp, st.desc, dev["ff"].handle, dev["lat"].handle, rw["ff"], rw["lat"], 5, 10, 0, 200, s_ff,
+                     s_lat)
     torch.cuda.synchronize()
     n = args.topo_steps
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    abi.snn_topo_run(tp, st.desc, dff.handle, dlat.handle, rw_ff, rw_lat, 5, 10, 200, n, s_ff, s_lat)
+    abi.snn_topo_run(tp, st.desc, dev["ff"].handle, dev["lat"].handle, rw["ff"], rw["lat"], 5, 10, 200, n, s_ff,
+                     s_lat)
     b.record()
     b.synchronize()
     ms = a.elapsed_time(b)
     stats_ff, stats_lat = s_ff.cpu().tolist(), s_lat.cpu().tolist()
-    return {"workload": "topo", "metric": "simulated steps/s (1 ms steps)", "L": L, "neurons_per_sheet": N,
-            "steps": n, "steps_per_s": round(n / (ms / 1e3), 1), "realtime_factor": round(n / (ms / 1e3) / 1000.0, 2),
-            "ms_per_1000_steps": round(ms / n * 1000, 3),
+    return {"workload": "topo", "metric": f"simulated steps/s ({dt:g} ms steps)", "setting": args.topo_setting,
+            "L": L, "neurons_per_sheet": N, "steps": n, "steps_per_s": round(n / (ms / 1e3), 1),
+            "realtime_factor": round(n * dt / ms, 2), "ms_per_1000_steps": round(ms / n * 1000, 3),
             "path": "one thread-block-cluster launch per 1000 steps (up to 4 neurons per thread)",
             "rewire_ff": dict(zip(["removed", "formed", "overflow", "attempts"], stats_ff)),
             "rewire_lat": dict(zip(["removed", "formed", "overflow", "attempts"], stats_lat))}
+
+
+def run_topo_evolution(args):
+    """Connectivity evolution of the topographic map over a long run (the analysis of
+    Sec. 3.2, Figs. 8-9): the map of run_topo simulated in time bins of 200 steps; per
+    bin the rewiring's elimination and formation histograms (by squared distance) and
+    the in-/out-degrees of both projections; at the start and the end the connection
+    probability and mean weight by displacement.  All recording is done by the
+    library's kernels on the device; the host reads the records once at the end."""
+    import math
+    import torch
+    from paper_2510_19764_gb300 import abi, build, net
+    build.build()
+    abi.load()
+    L, N, dt, dev, tp, rw, st = topo_setup(args)
+    BIN = int(round(200.0 / dt))                  # 200 ms time bins
+    n_bins = max(1, args.evolution_steps // BIN)
+    projs = ("ff", "lat")
+    hist = {k: net.attach_event_histograms(rw[k], L) for k in projs}
+    nb = hist["ff"][0].numel()
+    # device records: [bin][elim, form][d2] and [bin][in, out][neuron]
+    rec_ev = {k: torch.zeros((n_bins, 2, nb), dtype=torch.int64, device="cuda") for k in projs}
+    rec_deg = {k: torch.zeros((n_bins + 1, 2, N), dtype=torch.int32, device="cuda") for k in projs}
+    prof = {}
+
+    def snapshot(b):
+        for k in projs:
+            count, wsum, indeg = net.topo_connectivity(dev[k], L)
+            rec_deg[k][b, 0].copy_(indeg)
+            rec_deg[k][b, 1].copy_(dev[k].row_len)
+            if b in (0, n_bins):
+                prof[(k, b)] = (count, wsum)
+
+    snapshot(0)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for b in range(n_bins):
+        abi.snn_topo_run(tp, st.desc, dev["ff"].handle, dev["lat"].handle, rw["ff"], rw["lat"], 5, 10, b * BIN, BIN)
+        for k in projs:
+            rec_ev[k][b, 0].copy_(hist[k][0])
+            rec_ev[k][b, 1].copy_(hist[k][1])
+            hist[k][0].zero_()
+            hist[k][1].zero_()
+        snapshot(b + 1)
+    e.record()
+    e.synchronize()
+    ms = a.elapsed_time(e)
+    unit_bin = [math.isqrt(d2) for d2 in range(nb)]
+    n_unit = unit_bin[-1] + 1
+
+    def unit(h):                       # squared-distance bins -> unit-distance bins
+        out = [0] * n_unit
+        for d2, c in enumerate(h):
+            out[unit_bin[d2]] += int(c)
+        return out
+
+    fifths = [(n_bins * q // 5, max(n_bins * (q + 1) // 5, n_bins * q // 5 + 1)) for q in range(5)]
+    out = {"workload": "topo-evolution", "setting": args.topo_setting, "L": L, "neurons_per_sheet": N,
+           "dt_ms": dt, "steps": n_bins * BIN, "bin_steps": BIN, "model_s": round(n_bins * BIN * dt / 1e3, 1),
+           "steps_per_s_with_analysis": round(n_bins * BIN / (ms / 1e3), 1),
+           "initial_degree_theory": round(2 * math.pi * 0.16 * 2.5 ** 2, 3),
+           "rates": "events per 200 ms bin, averaged over each fifth of the run"}
+    for k in projs:
+        ev = rec_ev[k].cpu().numpy()
+        deg = rec_deg[k].cpu().numpy().astype(float)
+        head, tail = max(1, n_bins // 10), max(1, n_bins // 10)
+        cnt0, w0 = (x.cpu().numpy() for x in prof[(k, 0)])
+        cnt1, w1 = (x.cpu().numpy() for x in prof[(k, n_bins)])
+        dy = list(range(L // 2 + 1))
+        out[k] = {
+            "elim_rate": [round(float(ev[lo:hi, 0].sum(1).mean()), 2) for lo, hi in fifths],
+            "form_rate": [round(float(ev[lo:hi, 1].sum(1).mean()), 2) for lo, hi in fifths],
+            "elim_by_distance_first_tenth": unit(ev[:head, 0].sum(0)),
+            "elim_by_distance_last_tenth": unit(ev[-tail:, 0].sum(0)),
+            "form_by_distance_first_tenth": unit(ev[:head, 1].sum(0)),
+            "form_by_distance_last_tenth": unit(ev[-tail:, 1].sum(0)),
+            "in_degree_mean": [round(float(deg[b, 0].mean()), 3) for b in (0, *[hi for _, hi in fifths])],
+            "in_degree_std": [round(float(deg[b, 0].std()), 3) for b in (0, *[hi for _, hi in fifths])],
+            "out_degree_mean": [round(float(deg[b, 1].mean()), 3) for b in (0, *[hi for _, hi in fifths])],
+            "out_degree_std": [round(float(deg[b, 1].std()), 3) for b in (0, *[hi for _, hi in fifths])],
+            "p_conn_dx0_start": [round(float(cnt0[d * L] / N), 4) for d in dy],
+            "p_conn_dx0_end": [round(float(cnt1[d * L] / N), 4) for d in dy],
+            "w_mean_dx0_end": [round(float(w1[d * L] / cnt1[d * L]), 4) if cnt1[d * L] else None for d in dy],
+        }
+    return out
 
 
 def run_kernels(args):
@@ -639,13 +753,60 @@ def run_kernels(args):
                                          "peak": pk["hbm_gbs"], "unit": "GB/s",
                                          "frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 4),
                                          "peak_source": pk["source"]}}
+    out["deepr_guided_vs_uniform"] = deepr_guided_timing(args, dev)
     return out
+
+
+def deepr_guided_timing(args, dev):
+    """DEEP R on the classifier's recurrent projection shape (1024 x 1024, 10 %, no
+    autapses; 2 % of the synapses turned against their sign per rewiring) with uniform
+    and with distance-guided formation (neurons on a 32 x 32 torus, sigma 2): mean
+    CUDA-event time per rewiring."""
+    import torch
+    import synth
+    from paper_2510_19764_gb300 import abi, net
+    N, L = 1024, 32
+    res = {}
+    for mode in ("uniform", "guided"):
+        rag = synth.random_ragged(args.seed + 5, N, N, 0.1, no_autapse=True)
+        r = net.DeviceRagged(rag.row_len, rag.ind, rag.w, N, no_autapse=True, adam=True, deepr=True, seed=5)
+        keep = None
+        if mode == "guided":
+            g = abi.DeeprGuide()
+            g.L, g.reserved, g.sigma = L, 0, 2.0
+            keep = torch.arange(N, dtype=torch.int32, device=dev)
+            g.pre_site = g.post_site = abi.ptr(keep)
+            abi.snn_ragged_set_deepr_guide(r.handle, g)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(args.seed)
+        slot = torch.arange(r.C, device=dev)[None, :]
+        stats = torch.zeros(4, dtype=torch.int64, device=dev)
+        times, formed = [], 0
+        for rep in range(8):
+            live = slot < r.row_len[:, None].long()
+            flip = live & (torch.rand(r.w.shape, generator=gen, device=dev) < 0.02) & (r.w != 0)
+            r.w[flip] = -r.w[flip]
+            stats.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            abi.snn_rewire_deepr(r.handle, rep, stats)
+            b.record()
+            b.synchronize()
+            if rep >= 3:
+                times.append(a.elapsed_time(b))
+                formed += int(stats[1])
+        assert r.status() == abi.SNN_OK
+        res[mode] = {"ms": round(sum(times) / len(times), 4), "formed_per_rewire": formed // len(times)}
+        del keep
+    return res
 
 
 def main():
     args = parse()
     if args.workload != "classifier":
-        fn = {"batched": run_batched, "serve": run_serve, "topo": run_topo, "kernels": run_kernels}[args.workload]
+        fn = {"batched": run_batched, "serve": run_serve, "topo": run_topo, "topo-evolution": run_topo_evolution,
+              "kernels": run_kernels}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return 0
     WORKLOAD["B"] = args.batch

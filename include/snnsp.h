@@ -60,7 +60,7 @@ typedef void* snn_stream;        /* cudaStream_t */
 /* Message for the most recent failing call on this host thread ("" if none). */
 const char* snn_last_error(void);
 /* ABI version of this header (bumped on any incompatible change). */
-int32_t snn_abi_version(void);   /* 5 */
+int32_t snn_abi_version(void);   /* 6 */
 
 /* ==================================================================================
  * Ragged sparse matrix (Sec. 2.1, Fig. 1; DEEP R bitfields Sec. 2.1.2, Fig. 2)
@@ -137,6 +137,34 @@ snn_status snn_rewire_deepr(snn_ragged* r, int64_t rewire_idx, snn_rewire_stats*
  * kernels run (rewire_idx_dev: device int64), so a captured CUDA graph can advance it. */
 snn_status snn_rewire_deepr_dev(snn_ragged* r, const int64_t* rewire_idx_dev, snn_rewire_stats* stats,
                                 snn_stream stream);
+
+/* Distance-guided DEEP R formation.  The paper's Discussion proposes guiding DEEP R's
+ * regrowth by the distance-dependent formation rule of the topographic map (Tab. 1-2)
+ * instead of choosing new targets uniformly.  Neurons of both populations sit on sites
+ * of an L x L torus; the k-th activation of row i picks free target j with probability
+ * proportional to the integer weight q[d^2] = floor(2^24 exp(-d^2 / (2 sigma^2))), d the
+ * torus distance between the sites of i and j (q computed on the host in double
+ * precision): with S the weight total over the row's free targets and u the uniform
+ * rule's draw, r = mulhi(u, S) picks the first free target in ascending order whose
+ * running weight sum exceeds r.  A row whose free targets all weigh 0 falls back to the
+ * uniform rule.  Elimination and the redistribution of activations over rows are
+ * unchanged. */
+typedef struct {
+    int32_t L;                  /* side of the site grid (sites 0 .. L*L - 1) */
+    int32_t reserved;           /* must be 0 */
+    double sigma;               /* Gaussian width in grid units, > 0 */
+    const int32_t* pre_site;    /* device [P]: site of each presynaptic neuron (row) */
+    const int32_t* post_site;   /* device [Q]: site of each postsynaptic neuron (target) */
+} snn_deepr_guide;
+/* Attach a guide to a handle; g = NULL detaches it (uniform formation again).  Builds
+ * the weight table in device memory that the handle allocates on the first call (its
+ * only allocation after snn_create_ragged), checks every site on the device and waits
+ * for the result: SNN_ESTATE if a site lies outside [0, L*L) (the guide stays off).  The
+ * site arrays remain the caller's and must stay valid while attached.  snn_rewire_deepr
+ * and snn_rewire_deepr_dev then form with the guide; snn_rewire_deepr_noalloc (no
+ * handle) always forms uniformly.  Cost: two passes over a row's bitfield per
+ * activation (the uniform rule needs one chunk scan). */
+snn_status snn_ragged_set_deepr_guide(snn_ragged* r, const snn_deepr_guide* g, snn_stream stream);
 
 /* DEEP R rewiring that allocates nothing (the paper has no counterpart; this entry
  * exists for callers that cannot allocate device memory).  Some callers cannot call
@@ -221,6 +249,18 @@ typedef struct {
     const double* bias_dev;   /* optional device {beta1^t, beta2^t}: read by the kernels
                                  instead of b1t, b2t (lets a captured CUDA graph advance
                                  the step count on the device); NULL: use b1t, b2t */
+    /* DEEP R noise term (Bellec et al. 2018; Sec. 2.1.2 notes that the paper leaves it
+     * out, as Bellec et al. 2020 did): temperature > 0 adds sqrt(2 lr temperature) nu to
+     * every active ragged weight after its Adam step (not to the dense readout), with
+     * nu ~ N(0, 1) from the Box-Muller transform of Philox (purpose DEEPR_NOISE, key =
+     * the matrix's seed, counter (noise_idx, row, slot, 0)):
+     *   u1 = ((word0 >> 11) + 1) 2^-53 in (0, 1],  u2 = (word1 >> 11) 2^-53 in [0, 1),
+     *   nu = sqrt(-2 ln u1) cos(2 pi u2)   (evaluated in double precision).
+     * temperature = 0: off (the paper's setting). */
+    double temperature;
+    int64_t noise_idx;            /* counter field of this step's draws (e.g. the batch index) */
+    const int64_t* noise_idx_dev; /* optional device copy of noise_idx, read by the kernel
+                                     (graph replay); NULL: use noise_idx */
 } snn_adam;
 
 #define SNN_EPROP_GRAD  0
@@ -295,8 +335,19 @@ typedef struct {
     int32_t n_ref;        /* refractory steps */
     int32_t reserved;
     double dt, tau_m, V_rest, E_exc, V_theta, V_reset, tau_s, g_leak;
-    double f_base, f_in;             /* Hz outside / inside the focus */
+    double f_base, f_in;             /* Hz outside / inside the focus (disc profile); with
+                                        sigma_stim > 0: base and peak rate */
     double g_max, tau_plus, tau_minus, A_plus, A_minus;
+    /* Input profile.  sigma_stim = 0: disc, channel rate f_in within squared torus
+     * distance radius2 of its tile's focus, f_base outside.  sigma_stim > 0: the Gaussian
+     * of Tab. 1 "Input", rate f_base + f_in exp(-d^2 / (2 sigma_stim^2)) (f_in is f_peak).
+     * Either way a channel fires iff its Philox word is below thr(d^2) =
+     * floor(rate dt 1e-3 2^64), computed on the host in double precision from the
+     * expression in that order.  The thresholds of d^2 >= 1024 must all equal
+     * thr(1023) (true for the disc with radius2 < 1023 and for any Gaussian whose
+     * tail has fallen below the rounding of f_base by then, e.g. sigma_stim = 2);
+     * otherwise the calls return SNN_EINVAL. */
+    double sigma_stim;
 } snn_topo_params;
 
 typedef struct {
@@ -305,6 +356,16 @@ typedef struct {
     double g_theta, g_new;           /* depression threshold, weight of new synapses */
     int32_t L;                       /* torus side used for distances */
     int32_t n_att;                   /* attempts per call */
+    /* Optional event histograms for the connectivity-evolution analysis of Sec. 3.2
+     * (eliminations and formations by spatial separation, Figs. 8-9 A-B): device int64
+     * arrays of 2*(L/2)^2 + 1 bins, bin = squared torus distance d^2 between the
+     * source and target grid positions.  Each elimination adds 1 to elim_d2[d^2], each
+     * synapse created (not the overflowed ones) 1 to form_d2[d^2].  The library only
+     * adds: the caller zeroes them and reads them (e.g. once per time bin).  NULL: not
+     * recorded.  Squared distances keep the bins exact; unit-width distance bins are
+     * floor(sqrt(d^2)) on the host. */
+    int64_t* elim_d2;
+    int64_t* form_d2;
 } snn_topo_rewire;
 
 /* Topographic network state (caller-owned device memory), N = L*L, Nw = ceil(N/32). */
@@ -352,6 +413,21 @@ snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_
                         snn_ragged* lat, const snn_topo_rewire* rw_ff, const snn_topo_rewire* rw_lat,
                         uint64_t input_seed, int32_t rewire_every, int64_t t0, int32_t n_steps,
                         snn_rewire_stats* stats_ff, snn_rewire_stats* stats_lat, snn_stream stream);
+
+/* Connectivity profile of a topographic projection (the state analysed in Sec. 3.2,
+ * Figs. 8-9 C-D): for every synapse i -> j of the L*L x L*L matrix, its displacement on
+ * the torus dx = (x_j - x_i) mod L, dy = (y_j - y_i) mod L (x = index % L, y = index / L)
+ * and its target.  Outputs (device arrays, each optional, zeroed by the call and then
+ * filled):
+ *   disp_count [L*L] int64: synapses with displacement (dx, dy) at dy*L + dx; divided by
+ *              L*L it is the connection probability at that displacement (panel D);
+ *   disp_wsum  [L*L] double: sum of their weights (mean weight = wsum / count; summed
+ *              with atomics, so the rounding order varies between runs);
+ *   in_degree  [L*L] int32: synapses onto each target (panel C; the out-degree of row i
+ *              is row_len[i]).
+ * F32 matrices with P = Q = L*L.  Asynchronous on `stream`; no allocation. */
+snn_status snn_topo_connectivity(const snn_ragged* r, int32_t L, int64_t* disp_count, double* disp_wsum,
+                                 int32_t* in_degree, snn_stream stream);
 
 /* ==================================================================================
  * Test hook

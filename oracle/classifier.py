@@ -261,8 +261,12 @@ def adam(w, m, v, g, lr: float, b1t: float, b2t: float, beta1=0.9, beta2=0.999, 
     return w, m, v
 
 
-def adam_ragged(w, m, v, g, row_len, lr, b1t, b2t, **kw):
-    """Adam on the active slots (s < row_len) of a ragged matrix; padding untouched."""
+def adam_ragged(w, m, v, g, row_len, lr, b1t, b2t, temperature: float = 0.0, nu=None, **kw):
+    """Adam on the active slots (s < row_len) of a ragged matrix; padding untouched.
+    temperature > 0: DEEP R's noise term, w += sqrt(2 lr T) nu after the Adam step
+    (nu: standard normals per slot, from oracle.deepr.langevin_normals)."""
     mask = _slot_mask(row_len, w.shape[1])
     w2, m2, v2 = adam(w, m, v, g, lr, b1t, b2t, **kw)
+    if temperature > 0.0:
+        w2 = w2 + math.sqrt(2.0 * lr * temperature) * nu
     return np.where(mask, w2, w), np.where(mask, m2, m), np.where(mask, v2, v)

@@ -42,6 +42,7 @@ TOPO_CAND = 6      # topo candidate targets: counter (rewire, row, k, 0), word 0
 TOPO_DRAW = 7      # topo elimination/formation R: counter (rewire, row, target, 0), word 0
 TOPO_FOCUS = 8     # topo stimulus centre: counter (period, 0, 0, 0), words 0 (x), 1 (y)
 TOPO_INPUT = 9     # topo Poisson input: counter (t, ch // 4, 0, 0), word ch % 4
+DEEPR_NOISE = 10   # DEEP R noise term: counter (noise_idx, row, slot, 0), words 0 and 1
 
 _U64 = np.uint64
 _LO32 = _U64(0xFFFFFFFF)

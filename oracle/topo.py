@@ -3,12 +3,13 @@
 Sec. 2.1.3 (rewiring algorithm, Fig. 3) and Sec. 2.2.2 (model, Tab. 1-2) of the paper.
 
 Per step t (dt = h):
- 1. source layer: Poisson spikes; channel c fires with probability rate(c) dt where the
-    rate is f_in inside a disc of radius r around the stimulus centre (torus distance)
-    and f_base outside; the centre is re-drawn every t_stim steps (Tab. 1 "Input"; the
-    disc replaces the Gaussian profile for the 32 x 32 workload, the Gaussian is a
-    variant).  Replicated foci: the centre lives on a tile of side L_f and repeats on
-    every tile (Sec. 2.2.2, s^2 stimulus locations when scaling).
+ 1. source layer: Poisson spikes; channel c fires with probability rate(c) dt where,
+    with d the torus distance to the stimulus centre, the rate is either Tab. 1's
+    Gaussian f_base + f_peak exp(-d^2 / (2 sigma_stim^2)) (sigma_stim > 0, f_in = f_peak)
+    or a disc: f_in for d <= r, f_base outside (the 32 x 32 workload's profile); the
+    centre is re-drawn every t_stim steps.  Replicated foci: the centre lives on a tile
+    of side L_f and repeats on every tile (Sec. 2.2.2, s^2 stimulus locations when
+    scaling).
  2. conductance: g_i <- g_i exp(-dt/tau_s) + sum of weights of spikes of step t-1
     (delay = one step, Tab. 2 t_d = h).
  3. conductance LIF (Tab. 1): in refractory steps V is held at V_reset; otherwise
@@ -69,6 +70,7 @@ class TopoParams:
     radius: int = 3
     t_stim: int = 20
     L_f: int | None = None      # focus tile side (None -> L: a single focus)
+    sigma_stim: float = 0.0     # > 0: Gaussian profile f_base + f_in exp(-d^2/2 sigma^2) (Tab. 1 "Input")
     # STDP (Tab. 2F)
     g_max: float = 0.2
     tau_plus: float = 20.0
@@ -105,6 +107,19 @@ class TopoParams:
         return int(round(self.tau_ref / self.dt))
 
 
+def paper_setting(L: int = 16, **kw) -> TopoParams:
+    """The model as Tab. 1-2 print it: time step h = 0.1 ms (so the 0.1 ms delay is one
+    step), Gaussian input f_base 5 Hz + f_peak 152.8 Hz exp(-d^2 / (2 * 2^2)), stimulus
+    interval 20 ms, rewiring every 1 ms with 10 attempts per 16 x 16 tile.  Conductances
+    stay in units of g_leak (the one reading kept)."""
+    dt = 0.1
+    s = L // 16
+    base = dict(L=L, dt=dt, f_base=5.0, f_in=152.8, sigma_stim=2.0, t_stim=int(round(20.0 / dt)),
+                rewire_every=int(round(1.0 / dt)), n_att=10 * s * s, L_f=16 if s > 1 else None)
+    base.update(kw)
+    return TopoParams(**base)
+
+
 def torus_d2(i: int, j: int, L: int) -> int:
     xi, yi, xj, yj = i % L, i // L, j % L, j // L
     dx = abs(xi - xj)
@@ -137,10 +152,17 @@ def input_spikes(seed: int, t: int, p: TopoParams) -> np.ndarray:
     dy = np.abs((c // L) % L_f - fy)
     dx = np.minimum(dx, L_f - dx)
     dy = np.minimum(dy, L_f - dy)
-    inside = dx * dx + dy * dy <= p.radius * p.radius
-    thr_in = np.uint64(philox.threshold(p.f_in * p.dt * 1e-3))
-    thr_base = np.uint64(philox.threshold(p.f_base * p.dt * 1e-3))
-    thr = np.where(inside, thr_in, thr_base).astype(np.uint64)
+    d2 = dx * dx + dy * dy
+    if p.sigma_stim > 0.0:
+        # Tab. 1 "Input": rate f_base + f_peak exp(-d^2 / (2 sigma_stim^2)), f_in = f_peak
+        thr = np.array([philox.threshold((p.f_base + p.f_in * math.exp(-int(q) / (2.0 * p.sigma_stim
+                                                                                  * p.sigma_stim))) * p.dt * 1e-3)
+                        for q in d2], dtype=np.uint64)
+    else:
+        inside = d2 <= p.radius * p.radius
+        thr_in = np.uint64(philox.threshold(p.f_in * p.dt * 1e-3))
+        thr_base = np.uint64(philox.threshold(p.f_base * p.dt * 1e-3))
+        thr = np.where(inside, thr_in, thr_base).astype(np.uint64)
     cu = c.astype(np.uint64)
     u = philox.draw(seed, philox.TOPO_INPUT, np.uint64(t), cu // np.uint64(4), 0, 0,
                     word=(cu % np.uint64(4)).astype(np.int64))
@@ -274,6 +296,49 @@ def rewire(row_len, ind, g, C: int, Q: int, L: int, seed: int, rewire_idx: int, 
             cand[j] = False
     return {"row_len": row_len, "ind": ind, "g": g, "removed": removed, "formed": formed,
             "overflow": overflow, "attempts": att, "removed_d2": removed_d2, "formed_d2": formed_d2}
+
+
+# ---------------------------------------------------------------------------- analysis
+#
+# Connectivity-evolution analysis of Sec. 3.2 (Figs. 8-9): eliminations and formations
+# counted by the spatial separation of source and target (panels A-B), in- and
+# out-degrees (panel C), connection probability and mean weight by displacement (panel D).
+
+def d2_histogram(d2_list, L: int) -> np.ndarray:
+    """Counts of squared torus distances, bins 0 .. 2 (L//2)^2."""
+    h = np.zeros(2 * (L // 2) ** 2 + 1, dtype=np.int64)
+    for d2 in d2_list:
+        h[int(d2)] += 1
+    return h
+
+
+def unit_distance_bins(h_d2: np.ndarray) -> np.ndarray:
+    """Regroup a squared-distance histogram into unit-width distance bins:
+    bin b holds the d with b <= d < b + 1, i.e. the d^2 with floor(sqrt(d^2)) = b."""
+    b = np.array([math.isqrt(d2) for d2 in range(len(h_d2))], dtype=np.int64)
+    out = np.zeros(int(b[-1]) + 1, dtype=np.int64)
+    np.add.at(out, b, np.asarray(h_d2, dtype=np.int64))
+    return out
+
+
+def connectivity_profile(row_len, ind, g, L: int):
+    """For every synapse i -> j: displacement (dx, dy) = ((x_j - x_i) mod L,
+    (y_j - y_i) mod L) with x = index mod L, y = index div L.  Returns
+    count[dy*L + dx], wsum[dy*L + dx] (sum of the weights) and in_degree[j]; the
+    out-degree of row i is row_len[i]."""
+    N = L * L
+    count = np.zeros(N, dtype=np.int64)
+    wsum = np.zeros(N, dtype=np.float64)
+    indeg = np.zeros(N, dtype=np.int64)
+    for i in range(len(row_len)):
+        for s in range(int(row_len[i])):
+            j = int(ind[i, s])
+            dx = (j % L - i % L) % L
+            dy = (j // L - i // L) % L
+            count[dy * L + dx] += 1
+            wsum[dy * L + dx] += float(g[i, s])
+            indeg[j] += 1
+    return count, wsum, indeg
 
 
 # ------------------------------------------------------------------------------- run

@@ -25,7 +25,7 @@ EXPORTED = [
     "snn_propagate", "snn_rewire_deepr", "snn_create_classifier", "snn_destroy_classifier", "snn_step_neurons",
     "snn_eprop_update", "snn_topo_input", "snn_topo_neurons", "snn_stdp_update", "snn_rewire_topo", "snn_topo_run",
     "snn_philox", "snn_rewire_deepr_noalloc", "snn_classifier_set_schedule", "snn_rewire_deepr_dev",
-    "snn_draw_inputs", "snn_step_neurons_ex",
+    "snn_draw_inputs", "snn_step_neurons_ex", "snn_topo_connectivity", "snn_ragged_set_deepr_guide",
 ]
 
 
@@ -69,19 +69,23 @@ class Batch(C.Structure):
 
 class Adam(C.Structure):
     _fields_ = [("lr", f64), ("beta1", f64), ("beta2", f64), ("eps", f64), ("b1t", f64), ("b2t", f64), ("l1", f64),
-                ("bias_dev", vp)]
+                ("bias_dev", vp), ("temperature", f64), ("noise_idx", i64), ("noise_idx_dev", vp)]
+
+
+class DeeprGuide(C.Structure):
+    _fields_ = [("L", i32), ("reserved", i32), ("sigma", f64), ("pre_site", vp), ("post_site", vp)]
 
 
 class TopoParams(C.Structure):
     _fields_ = [("L", i32), ("L_f", i32), ("radius2", i32), ("t_stim", i32), ("n_ref", i32), ("reserved", i32),
                 ("dt", f64), ("tau_m", f64), ("V_rest", f64), ("E_exc", f64), ("V_theta", f64), ("V_reset", f64),
                 ("tau_s", f64), ("g_leak", f64), ("f_base", f64), ("f_in", f64), ("g_max", f64), ("tau_plus", f64),
-                ("tau_minus", f64), ("A_plus", f64), ("A_minus", f64)]
+                ("tau_minus", f64), ("A_plus", f64), ("A_minus", f64), ("sigma_stim", f64)]
 
 
 class TopoRewire(C.Structure):
     _fields_ = [("p_form", f64), ("sigma", f64), ("p_elim_dep", f64), ("p_elim_pot", f64), ("g_theta", f64),
-                ("g_new", f64), ("L", i32), ("n_att", i32)]
+                ("g_new", f64), ("L", i32), ("n_att", i32), ("elim_d2", vp), ("form_d2", vp)]
 
 
 class TopoState(C.Structure):
@@ -126,6 +130,8 @@ def load() -> C.CDLL:
         "snn_rewire_deepr_dev": (i32, [vp, vp, vp, vp]),
         "snn_draw_inputs": (i32, [vp, P(Batch), i32, i32, vp]),
         "snn_step_neurons_ex": (i32, [vp, P(Batch), i32, i32, i32, vp]),
+        "snn_topo_connectivity": (i32, [vp, i32, vp, vp, vp, vp]),
+        "snn_ragged_set_deepr_guide": (i32, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -246,6 +252,14 @@ def snn_topo_run(p: TopoParams, st: TopoState, ff: int, lat: int, rw_ff: TopoRew
                  stream=None) -> None:
     check(load().snn_topo_run(C.byref(p), C.byref(st), ff, lat, C.byref(rw_ff), C.byref(rw_lat), input_seed,
                               rewire_every, t0, n_steps, ptr(stats_ff), ptr(stats_lat), stream_ptr(stream)))
+
+
+def snn_ragged_set_deepr_guide(h: int, g: "DeeprGuide | None", stream=None) -> None:
+    check(load().snn_ragged_set_deepr_guide(h, C.byref(g) if g is not None else None, stream_ptr(stream)))
+
+
+def snn_topo_connectivity(h: int, L: int, disp_count=None, disp_wsum=None, in_degree=None, stream=None) -> None:
+    check(load().snn_topo_connectivity(h, L, ptr(disp_count), ptr(disp_wsum), ptr(in_degree), stream_ptr(stream)))
 
 
 def snn_philox(seed: int, purpose: int, ctr, n: int, out, stream=None) -> None:

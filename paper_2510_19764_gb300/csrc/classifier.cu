@@ -689,12 +689,27 @@ __device__ __forceinline__ void bias_from_device(const double* bias_dev, real& b
     }
 }
 
+// DEEP R noise of slot (i, s): standard normal by the Box-Muller transform of two
+// Philox words, in double precision.
+__device__ __forceinline__ double deepr_noise(uint64_t seed, uint64_t noise_idx, int i, int s) {
+    const u64x4 u = philox(seed, PH_DEEPR_NOISE, noise_idx, (uint64_t)i, (uint64_t)s, 0);
+    const double u1 = (double)((u.x >> 11) + 1) * 0x1p-53;      // (0, 1], exact: the log stays finite
+    const double u2 = (double)(u.y >> 11) * 0x1p-53;            // [0, 1)
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+struct NoiseK {
+    double amp;                    // sqrt(2 lr temperature); 0 = off
+    uint64_t seed, idx;
+    const int64_t* idx_dev;
+};
+
 template <typename real>
 __global__ void k_adam_ragged(const int32_t* __restrict__ len, const int32_t* __restrict__ ind, int P, int C, int Qw,
                               real* __restrict__ w, real* __restrict__ m, real* __restrict__ v,
                               const real* __restrict__ grad, const uint32_t* __restrict__ sign, real l1, real lr,
                               real b1, real b2, real omb1, real omb2, real eps, real bc1, real bc2,
-                              const double* __restrict__ bias_dev) {
+                              const double* __restrict__ bias_dev, NoiseK nz) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)P * C) return;
     bias_from_device(bias_dev, bc1, bc2);
@@ -708,6 +723,10 @@ __global__ void k_adam_ragged(const int32_t* __restrict__ len, const int32_t* __
     }
     real ww = w[idx], mm = m[idx], vv = v[idx];
     adam_update(ww, mm, vv, g, lr, b1, b2, omb1, omb2, eps, bc1, bc2);
+    if (nz.amp > 0.0) {
+        const uint64_t k = nz.idx_dev ? (uint64_t)*nz.idx_dev : nz.idx;
+        ww = (real)((double)ww + nz.amp * deepr_noise(nz.seed, k, i, s));
+    }
     w[idx] = ww;
     m[idx] = mm;
     v[idx] = vv;
@@ -1200,9 +1219,14 @@ static snn_status apply_impl(snn_classifier* c, const snn_adam* ad, cudaStream_t
     for (snn_ragged* r : {d.w_in, d.w_rec}) {
         const snn_ragged_desc& rd = r->d;
         const uint32_t* sign = (ad->l1 != 0.0) ? rd.sign_bits : nullptr;
+        NoiseK nz;
+        nz.amp = ad->temperature > 0.0 ? std::sqrt(2.0 * ad->lr * ad->temperature) : 0.0;
+        nz.seed = rd.seed;
+        nz.idx = (uint64_t)ad->noise_idx;
+        nz.idx_dev = ad->noise_idx_dev;
         k_adam_ragged<real><<<ceil_div((long long)rd.P * rd.C, 256), 256, 0, s>>>(
             rd.row_len, rd.ind, rd.P, rd.C, r->Qw, (real*)rd.w, (real*)rd.m, (real*)rd.v, (const real*)rd.grad, sign,
-            (real)ad->l1, lr, b1, b2, omb1, omb2, eps, bc1, bc2, ad->bias_dev);
+            (real)ad->l1, lr, b1, b2, omb1, omb2, eps, bc1, bc2, ad->bias_dev, nz);
         SNN_LAUNCH_CHECK();
     }
     k_adam_dense<real><<<ceil_div(d.K * d.N, 256), 256, 0, s>>>((real*)d.W_out, (real*)d.W_out_m, (real*)d.W_out_v,
@@ -1357,6 +1381,8 @@ snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase
         SNN_REQUIRE(c->d.W_out_m && c->d.W_out_v && c->d.b_m && c->d.b_v, "snn_eprop_update: readout moments missing");
         SNN_REQUIRE(adam->bias_dev || (adam->b1t < 1.0 && adam->b2t < 1.0),
                     "snn_eprop_update: b1t, b2t must be beta^t with t >= 1");
+        SNN_REQUIRE(adam->temperature >= 0.0 && (adam->temperature == 0.0 || adam->noise_idx >= 0),
+                    "snn_eprop_update: temperature must be >= 0 (and noise_idx >= 0 when it is > 0)");
         return c->d.dtype == SNN_F32 ? apply_impl<float>(c, adam, s) : apply_impl<double>(c, adam, s);
     }
     SNN_REQUIRE(false, "snn_eprop_update: unknown phase %d", phase);

@@ -50,7 +50,7 @@ enum : int32_t {
 // and bumps the key by two Weyl constants.
 enum : uint64_t {
     PH_INPUT = 1, PH_SIGN = 2, PH_DEEPR_DIST = 3, PH_DEEPR_FORM = 4, PH_TOPO_ATT = 5,
-    PH_TOPO_CAND = 6, PH_TOPO_DRAW = 7, PH_TOPO_FOCUS = 8, PH_TOPO_INPUT = 9,
+    PH_TOPO_CAND = 6, PH_TOPO_DRAW = 7, PH_TOPO_FOCUS = 8, PH_TOPO_INPUT = 9, PH_DEEPR_NOISE = 10,
 };
 
 struct u64x4 {
@@ -195,6 +195,13 @@ struct snn_ragged {
     int32_t thr_cap;
     double thr_p, thr_sigma; // parameters the table was built for
     int32_t thr_L;
+    // distance-guided DEEP R formation (snn_ragged_set_deepr_guide)
+    int32_t guide_on;
+    int32_t guide_L;
+    const int32_t* guide_pre;    // caller's site arrays
+    const int32_t* guide_post;
+    uint32_t* guide_q;           // [guide_qcap] weights by squared distance
+    int32_t guide_qcap;
 };
 
 struct snn_classifier {

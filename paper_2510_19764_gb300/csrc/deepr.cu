@@ -16,7 +16,9 @@
 //                       32-word scan finds the bit.
 #include "common.cuh"
 
+#include <cmath>
 #include <mutex>
+#include <vector>
 
 namespace snn {
 
@@ -303,13 +305,143 @@ __global__ void __launch_bounds__(DEEPR_THREADS)
     }
 }
 
+// ---- distance-guided formation
+struct GuideK {
+    const int32_t* pre_site;
+    const int32_t* post_site;
+    const uint32_t* q;           // weight by squared torus distance of the two sites
+    int L;
+};
+
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t guide_weight(const GuideK& g, int sx, int sy, int j) {
+    const int t = g.post_site[j];
+    int dx = abs(t % g.L - sx), dy = abs(t / g.L - sy);
+    dx = min(dx, g.L - dx);
+    dy = min(dy, g.L - dy);
+    return g.q[dx * dx + dy * dy];
+}
+
+// Weight of the free targets in one bitfield word (free: its zero bits, inverted).
+__device__ __forceinline__ unsigned long long word_weight(const GuideK& g, int sx, int sy, uint32_t free_bits,
+                                                          int wi) {
+    unsigned long long s = 0;
+    for (uint32_t rest = free_bits; rest; rest &= rest - 1u) s += guide_weight(g, sx, sy, wi * 32 + __ffs(rest) - 1);
+    return s;
+}
+
+// One warp per row with activations; activation k draws u as the uniform rule does and
+// picks the free target where the running weight sum (ascending targets) first exceeds
+// r = mulhi(u, S), S the weight total; with S = 0 every free target weighs 1 (the
+// uniform rule).  Two passes over the row's bitfield per activation: the total, then
+// the word holding r, whose owner lane walks its free bits.
+template <typename real>
+__global__ void __launch_bounds__(DEEPR_THREADS)
+    k_deepr_form_guided(int32_t* __restrict__ len, int32_t* __restrict__ ind, real* __restrict__ w,
+                        real* __restrict__ m, real* __restrict__ v, uint32_t* __restrict__ conn,
+                        const int32_t* __restrict__ taken, int P, int C, int Q, int Qw, int no_autapse, uint64_t seed,
+                        uint64_t rewire, const long long* ridx_dev, int32_t* status, snn_rewire_stats* stats,
+                        GuideK g) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (ridx_dev) rewire = (uint64_t)*ridx_dev;
+    if (i >= P) return;
+    const int nt = taken[i];
+    if (nt == 0) return;
+    const int lane = lane_id();
+    const int forb = (no_autapse && i < Q) ? 1 : 0;
+    const uint32_t tail_mask = (Q & 31) ? ~((1u << (Q & 31)) - 1u) : 0u;
+    uint32_t* crow = conn + (size_t)i * Qw;
+    const size_t row = (size_t)i * C;
+    const int si = g.pre_site[i];
+    const int sx = si % g.L, sy = si / g.L;
+    int n = len[i];
+    int formed = 0;
+    uint64_t u_l = 0;
+    for (int k = 0; k < nt; ++k) {
+        const int n_free = Q - forb - n;
+        if (n_free <= 0 || n >= C) {
+            if (lane == 0) atomicOr(status, ST_STATE);
+            break;
+        }
+        if ((k & 31) == 0 && k + lane < nt) u_l = philox(seed, PH_DEEPR_FORM, rewire, (uint64_t)i, (uint64_t)(k + lane), 0).x;
+        const uint64_t u = __shfl_sync(0xffffffffu, u_l, k & 31);
+        unsigned long long S = 0;
+        for (int wb = 0; wb < Qw; wb += 32) {
+            const int wi = wb + lane;
+            S += word_weight(g, sx, sy, ~conn_word(crow, wi, Qw, i, forb, tail_mask), wi);
+        }
+        S = warp_sum(S);
+        const bool flat = S == 0;
+        const unsigned long long r = mulhi_index(u, flat ? (uint64_t)n_free : (uint64_t)S);
+        unsigned long long seen = 0;
+        int target = -1;
+        for (int wb = 0; wb < Qw && target < 0; wb += 32) {
+            const int wi = wb + lane;
+            const uint32_t fb = ~conn_word(crow, wi, Qw, i, forb, tail_mask);
+            const unsigned long long ww = flat ? (unsigned long long)__popc(fb) : word_weight(g, sx, sy, fb, wi);
+            const unsigned long long incl = warp_incl_scan_u64(ww);
+            const unsigned long long excl = incl - ww;
+            const uint32_t hm = __ballot_sync(0xffffffffu, r >= seen + excl && r < seen + incl);
+            if (hm) {
+                const int src = __ffs(hm) - 1;
+                int tg = -1;
+                if (lane == src) {
+                    unsigned long long acc = seen + excl;
+                    for (uint32_t rest = fb; rest; rest &= rest - 1u) {
+                        const int j = wi * 32 + __ffs(rest) - 1;
+                        acc += flat ? 1ull : guide_weight(g, sx, sy, j);
+                        if (acc > r) {
+                            tg = j;
+                            break;
+                        }
+                    }
+                }
+                target = __shfl_sync(0xffffffffu, tg, src);
+            }
+            seen += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (target < 0) {
+            if (lane == 0) atomicOr(status, ST_STATE);
+            break;
+        }
+        if (lane == 0) {
+            ind[row + n] = target;
+            w[row + n] = real(0);
+            m[row + n] = real(0);
+            v[row + n] = real(0);
+            crow[target >> 5] |= 1u << (target & 31);
+        }
+        __syncwarp();
+        ++n;
+        ++formed;
+    }
+    if (lane == 0) {
+        len[i] = n;
+        if (stats) atomicAdd((unsigned long long*)&stats->formed, (unsigned long long)formed);
+    }
+}
+
+__global__ void k_check_sites(const int32_t* __restrict__ site, int n, int lim, int32_t* status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n && (site[k] < 0 || site[k] >= lim)) atomicOr(status, ST_STATE);
+}
+
 // Launch sequence of one rewiring.  dsum: device uint64[2] scratch (dormant total,
 // round-0 rejections), zeroed here.
 template <typename real>
 static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* dormant, int32_t* taken,
                                     int32_t* room, int32_t* cnt, unsigned long long* dsum, int32_t* status,
                                     uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, const GuideK* guide = nullptr) {
     const int blocks = ceil_div((long long)d.P * 32, DEEPR_THREADS);
     SNN_CUDA(cudaMemsetAsync(dsum, 0, 2 * sizeof(unsigned long long), s));
     k_deepr_eliminate<real><<<blocks, DEEPR_THREADS, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
@@ -324,6 +456,13 @@ static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* d
     k_deepr_distribute<<<1, 1024, 0, s>>>(room, taken, cnt, dsum, dsum + 1, d.P, d.seed, rewire, ridx_dev, status,
                                           stats);
     SNN_LAUNCH_CHECK();
+    if (guide) {
+        k_deepr_form_guided<real><<<blocks, DEEPR_THREADS, 0, s>>>(
+            d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v, d.conn_bits, taken, d.P, d.C, d.Q, Qw, d.no_autapse,
+            d.seed, rewire, ridx_dev, status, stats, *guide);
+        SNN_LAUNCH_CHECK();
+        return SNN_OK;
+    }
     const size_t smem = (size_t)(DEEPR_THREADS / 32) * ((Qw + 31) / 32) * sizeof(int32_t);
     SNN_REQUIRE(smem <= 48 * 1024, "snn_rewire_deepr: Q = %d too large for the formation chunk table", d.Q);
     k_deepr_form<real><<<blocks, DEEPR_THREADS, smem, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
@@ -336,8 +475,16 @@ static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* d
 template <typename real>
 static snn_status rewire_impl(snn_ragged* r, uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
                               cudaStream_t s) {
+    GuideK g;
+    if (r->guide_on) {
+        g.pre_site = r->guide_pre;
+        g.post_site = r->guide_post;
+        g.q = r->guide_q;
+        g.L = r->guide_L;
+    }
     return rewire_launch_all<real>(r->d, r->Qw, r->dormant, r->taken, r->room, r->cnt,
-                                   (unsigned long long*)r->scal, r->status, rewire, ridx_dev, stats, s);
+                                   (unsigned long long*)r->scal, r->status, rewire, ridx_dev, stats, s,
+                                   r->guide_on ? &g : nullptr);
 }
 
 // ------------------------------------------------------------------ no-allocation variant
@@ -433,4 +580,56 @@ extern "C" snn_status snn_rewire_deepr_dev(snn_ragged* r, const int64_t* rewire_
     cudaStream_t s = (cudaStream_t)stream;
     const long long* ridx = (const long long*)rewire_idx_dev;
     return d.dtype == SNN_F32 ? rewire_impl<float>(r, 0, ridx, stats, s) : rewire_impl<double>(r, 0, ridx, stats, s);
+}
+
+extern "C" snn_status snn_ragged_set_deepr_guide(snn_ragged* r, const snn_deepr_guide* g, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(r, "snn_ragged_set_deepr_guide: NULL handle");
+    if (!g) {
+        r->guide_on = 0;
+        return SNN_OK;
+    }
+    SNN_REQUIRE(g->reserved == 0, "snn_ragged_set_deepr_guide: reserved must be 0");
+    SNN_REQUIRE(g->L > 0 && (long long)g->L * g->L < (1ll << 31), "snn_ragged_set_deepr_guide: bad L = %d", g->L);
+    SNN_REQUIRE(g->sigma > 0.0, "snn_ragged_set_deepr_guide: sigma must be > 0");
+    SNN_REQUIRE(g->pre_site && g->post_site, "snn_ragged_set_deepr_guide: pre_site and post_site are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = 2 * (g->L / 2) * (g->L / 2) + 1;
+    // weights by squared distance, floor(2^24 exp(-d2 / (2 sigma^2))), on the host in double
+    std::vector<uint32_t> q(n);
+    for (int d2 = 0; d2 < n; ++d2)
+        q[d2] = (uint32_t)(std::exp(-(double)d2 / (2.0 * g->sigma * g->sigma)) * 16777216.0);
+    // table plus one word for the site check
+    if (r->guide_qcap < n + 1) {
+        cudaFree(r->guide_q);
+        r->guide_q = nullptr;
+        r->guide_qcap = 0;
+        if (cudaMalloc(&r->guide_q, (size_t)(n + 1) * sizeof(uint32_t)) != cudaSuccess) {
+            set_error("snn_ragged_set_deepr_guide: cudaMalloc failed");
+            return SNN_ENOMEM;
+        }
+        r->guide_qcap = n + 1;
+    }
+    r->guide_on = 0;
+    SNN_CUDA(cudaMemcpyAsync(r->guide_q, q.data(), (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    int32_t* flag = (int32_t*)(r->guide_q + n);
+    SNN_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    const int lim = g->L * g->L;
+    k_check_sites<<<ceil_div(r->d.P, 256), 256, 0, s>>>(g->pre_site, r->d.P, lim, flag);
+    SNN_LAUNCH_CHECK();
+    k_check_sites<<<ceil_div(r->d.Q, 256), 256, 0, s>>>(g->post_site, r->d.Q, lim, flag);
+    SNN_LAUNCH_CHECK();
+    int32_t st = 0;
+    SNN_CUDA(cudaMemcpyAsync(&st, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    if (st != 0) {
+        r->guide_on = 0;
+        set_error("snn_ragged_set_deepr_guide: a site is outside [0, L*L)");
+        return SNN_ESTATE;
+    }
+    r->guide_on = 1;
+    r->guide_L = g->L;
+    r->guide_pre = g->pre_site;
+    r->guide_post = g->post_site;
+    return SNN_OK;
 }

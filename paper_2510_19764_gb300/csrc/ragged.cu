@@ -124,7 +124,7 @@ using namespace snn;
 extern "C" {
 
 const char* snn_last_error(void) { return g_last_error.c_str(); }
-int32_t snn_abi_version(void) { return 5; }
+int32_t snn_abi_version(void) { return 6; }
 
 snn_status snn_create_ragged(const snn_ragged_desc* d, int32_t init_bits, snn_stream stream, snn_ragged** out) {
     clear_error();
@@ -193,6 +193,7 @@ snn_status snn_create_ragged(const snn_ragged_desc* d, int32_t init_bits, snn_st
 
 snn_status snn_destroy_ragged(snn_ragged* r) {
     if (!r) return SNN_OK;
+    cudaFree(r->guide_q);
     cudaFree(r->status);
     cudaFree(r->dormant);
     cudaFree(r->taken);

@@ -10,16 +10,24 @@
 namespace snn {
 
 struct TopoK {
-    int L, L_f, radius2, t_stim, n_ref, N, Nw;
+    int L, L_f, t_stim, n_ref, N, Nw;
     float ds, dplus, dminus, dt_over_tau_m, V_rest, E_exc, V_theta, V_reset, g_leak, g_max, A_plus, A_minus;
-    uint64_t thr_in, thr_base;
+};
+
+// Input thresholds by squared distance to the focus: thr[min(d2, n - 1)] (the host
+// checks that the profile is flat from entry n - 1 on).  Passed by value (8 KB of kernel
+// parameters) and copied to shared memory by each CTA: lanes index it with their own d2,
+// which in the constant bank would serialise.
+constexpr int TOPO_IN_TAB = 1024;
+struct TopoIn {
+    uint64_t thr[TOPO_IN_TAB];
+    int n;
 };
 
 static TopoK topo_consts(const snn_topo_params* p) {
     TopoK k;
     k.L = p->L;
     k.L_f = p->L_f;
-    k.radius2 = p->radius2;
     k.t_stim = p->t_stim;
     k.n_ref = p->n_ref;
     k.N = p->L * p->L;
@@ -36,9 +44,45 @@ static TopoK topo_consts(const snn_topo_params* p) {
     k.g_max = (float)p->g_max;
     k.A_plus = (float)p->A_plus;
     k.A_minus = (float)p->A_minus;
-    k.thr_in = prob_threshold(p->f_in * p->dt * 1e-3);
-    k.thr_base = prob_threshold(p->f_base * p->dt * 1e-3);
     return k;
+}
+
+// Rate threshold of squared focus distance d2: the disc (sigma_stim = 0) or the Gaussian
+// profile of Tab. 1 "Input", floor(rate dt 1e-3 2^64) in double on the host.
+static uint64_t input_threshold(const snn_topo_params* p, int d2) {
+    if (p->sigma_stim > 0.0)
+        return prob_threshold((p->f_base + p->f_in * std::exp(-(double)d2 / (2.0 * p->sigma_stim * p->sigma_stim))) *
+                              p->dt * 1e-3);
+    return prob_threshold((d2 <= p->radius2 ? p->f_in : p->f_base) * p->dt * 1e-3);
+}
+
+// The threshold table of the input profile; rebuilt only when the parameters that
+// define it change (the per-step calls would otherwise evaluate it every step).
+static snn_status topo_input_table(const snn_topo_params* p, TopoIn& in) {
+    struct Key {
+        int L_f, radius2;
+        double dt, f_base, f_in, sigma;
+        bool operator==(const Key& o) const {
+            return L_f == o.L_f && radius2 == o.radius2 && dt == o.dt && f_base == o.f_base && f_in == o.f_in &&
+                   sigma == o.sigma;
+        }
+    };
+    static thread_local Key last{-1, 0, 0, 0, 0, 0};
+    static thread_local TopoIn cached;
+    static thread_local bool ok = false;
+    const Key key{p->L_f, p->radius2, p->dt, p->f_base, p->f_in, p->sigma_stim};
+    if (!(key == last)) {
+        const int max_d2 = 2 * (p->L_f / 2) * (p->L_f / 2);
+        cached.n = max_d2 + 1 < TOPO_IN_TAB ? max_d2 + 1 : TOPO_IN_TAB;
+        for (int d2 = 0; d2 < cached.n; ++d2) cached.thr[d2] = input_threshold(p, d2);
+        ok = true;
+        for (int d2 = cached.n; d2 <= max_d2 && ok; ++d2) ok = input_threshold(p, d2) == cached.thr[cached.n - 1];
+        last = key;
+    }
+    SNN_REQUIRE(ok, "topo: the input profile is not flat beyond squared distance %d (sigma_stim too wide for L_f)",
+                TOPO_IN_TAB - 1);
+    in = cached;
+    return SNN_OK;
 }
 
 // ---- per-step arithmetic shared by the per-call kernels and the fused step loop
@@ -52,8 +96,8 @@ __device__ __forceinline__ void topo_focus(const TopoK& k, uint64_t seed, long l
 
 // Source channels 4g .. 4g+3 of step t (one Philox block): spike bits as a nibble;
 // xs[q] is channel 4g+q's trace, updated in place.
-__device__ __forceinline__ uint32_t topo_input_group(const TopoK& k, uint64_t seed, long long t, int g, int fx,
-                                                     int fy, float (&xs)[4]) {
+__device__ __forceinline__ uint32_t topo_input_group(const TopoK& k, const uint64_t* thr, int n_thr, uint64_t seed,
+                                                     long long t, int g, int fx, int fy, float (&xs)[4]) {
     uint32_t nib = 0;
     const u64x4 u = philox(seed, PH_TOPO_INPUT, (uint64_t)t, (uint64_t)g, 0, 0);
 #pragma unroll
@@ -64,8 +108,7 @@ __device__ __forceinline__ uint32_t topo_input_group(const TopoK& k, uint64_t se
             int dy = abs((c / k.L) % k.L_f - fy);
             dx = min(dx, k.L_f - dx);
             dy = min(dy, k.L_f - dy);
-            const uint64_t thr = (dx * dx + dy * dy <= k.radius2) ? k.thr_in : k.thr_base;
-            const bool s = u[q] < thr;
+            const bool s = u[q] < thr[min(dx * dx + dy * dy, n_thr - 1)];
             if (s) nib |= 1u << q;
             xs[q] = xs[q] * k.dplus + (s ? 1.0f : 0.0f);
         }
@@ -112,10 +155,12 @@ __device__ __forceinline__ float stdp_slot(float g, bool pre, bool post, float y
 }
 
 // Thread = 4 source channels (one Philox block); nibbles of 8 lanes form one word.
-__global__ void k_topo_input(TopoK k, uint64_t seed, long long t, uint32_t* __restrict__ bits,
-                             float* __restrict__ x_src) {
+__global__ void k_topo_input(TopoK k, const __grid_constant__ TopoIn in, uint64_t seed, long long t,
+                             uint32_t* __restrict__ bits, float* __restrict__ x_src) {
     __shared__ int focus[2];
+    __shared__ uint64_t s_thr[TOPO_IN_TAB];
     if (threadIdx.x == 0) topo_focus(k, seed, t, focus[0], focus[1]);
+    for (int d = threadIdx.x; d < in.n; d += blockDim.x) s_thr[d] = in.thr[d];
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int n_groups = (k.N + 3) >> 2;
@@ -124,7 +169,7 @@ __global__ void k_topo_input(TopoK k, uint64_t seed, long long t, uint32_t* __re
         float xs[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) xs[q] = 4 * g + q < k.N ? x_src[4 * g + q] : 0.0f;
-        nib = topo_input_group(k, seed, t, g, focus[0], focus[1], xs);
+        nib = topo_input_group(k, s_thr, in.n, seed, t, g, focus[0], focus[1], xs);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (4 * g + q < k.N) x_src[4 * g + q] = xs[q];
@@ -183,6 +228,7 @@ struct RewireK {
     float g_theta, g_new;
     uint64_t thr_dep, thr_pot;
     uint64_t seed, rewire;
+    unsigned long long *elim_d2, *form_d2;   // optional event histograms by squared distance
 };
 
 __device__ __forceinline__ int torus_d2(int i, int j, int L) {
@@ -278,6 +324,7 @@ __device__ void topo_rewire_cta(const RewireK& k, int32_t* __restrict__ len, int
             const bool keep = valid && !rm;
             const uint32_t mask = __ballot_sync(0xffffffffu, keep);
             removed += rm ? 1 : 0;
+            if (rm && k.elim_d2) atomicAdd(&k.elim_d2[torus_d2(i, j, k.L)], 1ull);
             __syncwarp();
             if (is_c) atomicAnd(&cand[j >> 5], ~(1u << (j & 31)));
             if (keep) {
@@ -309,6 +356,7 @@ __device__ void topo_rewire_cta(const RewireK& k, int32_t* __restrict__ len, int
                     ind[row + slot] = j;
                     w[row + slot] = k.g_new;
                     ++formed;
+                    if (k.form_d2) atomicAdd(&k.form_d2[torus_d2(i, j, k.L)], 1ull);
                 } else {
                     ++overflow;
                 }
@@ -349,6 +397,7 @@ static snn_status check_topo(const snn_topo_params* p) {
     SNN_REQUIRE(p->L > 0 && p->L_f > 0 && p->L % p->L_f == 0, "topo: need L > 0 and L a multiple of L_f");
     SNN_REQUIRE(p->t_stim > 0 && p->n_ref >= 0 && p->dt > 0 && p->tau_m > 0 && p->tau_s > 0 && p->g_leak > 0,
                 "topo: bad time constants");
+    SNN_REQUIRE(p->sigma_stim >= 0.0, "topo: sigma_stim must be >= 0");
     return SNN_OK;
 }
 
@@ -387,6 +436,8 @@ static snn_status rewire_prepare(snn_ragged* r, const snn_topo_rewire* p, Rewire
     k.thr_pot = prob_threshold(p->p_elim_pot);
     k.seed = d.seed;
     k.rewire = 0;
+    k.elim_d2 = (unsigned long long*)p->elim_d2;
+    k.form_d2 = (unsigned long long*)p->form_d2;
     SNN_REQUIRE(rewire_smem(k.P, k.n_att, k.Qw, 1024) <= 227 * 1024, "snn_rewire_topo: P = %d too large for one CTA",
                 k.P);
     return SNN_OK;
@@ -408,6 +459,29 @@ static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t
     return SNN_OK;
 }
 
+// Connectivity profile: one warp per row; every synapse adds to its torus displacement's
+// count and weight sum and to its target's in-degree (global atomics; an analysis pass,
+// called once per time bin, not per step).
+__global__ void k_topo_profile(const int32_t* __restrict__ len, const int32_t* __restrict__ ind,
+                               const float* __restrict__ w, int P, int C, int L,
+                               unsigned long long* __restrict__ count, double* __restrict__ wsum,
+                               int32_t* __restrict__ indeg) {
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= P) return;
+    const int n = len[i], ix = i % L, iy = i / L;
+    const size_t row = (size_t)i * C;
+    for (int s = lane_id(); s < n; s += 32) {
+        const int j = ind[row + s];
+        int dx = j % L - ix, dy = j / L - iy;
+        dx += dx < 0 ? L : 0;
+        dy += dy < 0 ? L : 0;
+        const int bin = dy * L + dx;
+        if (count) atomicAdd(&count[bin], 1ull);
+        if (wsum) atomicAdd(&wsum[bin], (double)w[row + s]);
+        if (indeg) atomicAdd(&indeg[j], 1);
+    }
+}
+
 // ---- fused step loop: the whole network in one thread-block cluster
 //
 // One cluster of CS CTAs x FUSED_THREADS threads runs many steps in one launch.  Global
@@ -424,6 +498,7 @@ static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t
 // identical to the sequence of per-call launches.
 struct TopoRun {
     TopoK k;
+    TopoIn in;
     int32_t* len[2];      // ff, lateral
     int32_t* ind[2];
     float* w[2];
@@ -449,7 +524,7 @@ constexpr int FUSED_THREADS = 512;
 constexpr int TOPO_FUSED_MAX_NPT = 4;   // neurons per thread the fused loop accepts (1, 2 or 4)
 
 template <int NPT>
-__global__ void __launch_bounds__(FUSED_THREADS, 1) k_topo_fused(TopoRun r) {
+__global__ void __launch_bounds__(FUSED_THREADS, 1) k_topo_fused(const __grid_constant__ TopoRun r) {
     extern __shared__ __align__(16) unsigned char smem[];
     const TopoK& k = r.k;
     const int N = k.N, Nw = k.Nw;
@@ -459,6 +534,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_topo_fused(TopoRun r) {
     const int gwarp = gt >> 5, nwarps = TT >> 5;
     uint32_t* sb_src = (uint32_t*)smem;           // [Nw] spike words of the step (STDP)
     uint32_t* sb_tgt = sb_src + Nw;               // [Nw]
+    __shared__ uint64_t s_thr[TOPO_IN_TAB];       // input thresholds by squared focus distance
+    for (int d = threadIdx.x; d < r.in.n; d += blockDim.x) s_thr[d] = r.in.thr[d];
+    __syncthreads();
     float V[NPT], gs[NPT], y[NPT], xt[NPT];
     int ref[NPT];
 #pragma unroll
@@ -488,7 +566,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_topo_fused(TopoRun r) {
                     fper = t / k.t_stim;
                     topo_focus(k, r.in_seed, t, fx, fy);
                 }
-                nib = topo_input_group(k, r.in_seed, t, gt, fx, fy, xs);
+                nib = topo_input_group(k, s_thr, r.in.n, r.in_seed, t, gt, fx, fy, xs);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (4 * gt + q < N) r.x_src[4 * gt + q] = xs[q];
@@ -673,9 +751,11 @@ snn_status snn_topo_input(const snn_topo_params* p, const snn_topo_state* st, ui
     if (e != SNN_OK) return e;
     SNN_REQUIRE(st && st->src_bits && st->x_src && t >= 0, "snn_topo_input: bad argument");
     TopoK k = topo_consts(p);
+    static thread_local TopoIn in;
+    if ((e = topo_input_table(p, in)) != SNN_OK) return e;
     const int groups = (k.N + 3) / 4;
-    k_topo_input<<<ceil_div(groups, 256), 256, 0, (cudaStream_t)stream>>>(k, seed, t, st->src_bits + (t & 1) * k.Nw,
-                                                                          st->x_src);
+    k_topo_input<<<ceil_div(groups, 256), 256, 0, (cudaStream_t)stream>>>(k, in, seed, t,
+                                                                          st->src_bits + (t & 1) * k.Nw, st->x_src);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -714,6 +794,27 @@ snn_status snn_rewire_topo(snn_ragged* r, const snn_topo_rewire* p, int64_t rewi
     return rewire_launch(r, p, rewire_idx, stats, (cudaStream_t)stream);
 }
 
+snn_status snn_topo_connectivity(const snn_ragged* r, int32_t L, int64_t* disp_count, double* disp_wsum,
+                                 int32_t* in_degree, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(r, "snn_topo_connectivity: NULL handle");
+    const snn_ragged_desc& d = r->d;
+    SNN_REQUIRE(d.dtype == SNN_F32, "snn_topo_connectivity: F32 ragged matrices only");
+    SNN_REQUIRE(L > 0 && (long long)L * L == d.Q && d.P == d.Q,
+                "snn_topo_connectivity: the matrix must be L*L x L*L (got P=%d Q=%d L=%d)", d.P, d.Q, L);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)L * L;
+    if (disp_count) SNN_CUDA(cudaMemsetAsync(disp_count, 0, N * sizeof(int64_t), s));
+    if (disp_wsum) SNN_CUDA(cudaMemsetAsync(disp_wsum, 0, N * sizeof(double), s));
+    if (in_degree) SNN_CUDA(cudaMemsetAsync(in_degree, 0, N * sizeof(int32_t), s));
+    if (!disp_count && !disp_wsum && !in_degree) return SNN_OK;
+    const int threads = 256;
+    k_topo_profile<<<ceil_div((long long)d.P * 32, threads), threads, 0, s>>>(
+        d.row_len, d.ind, (const float*)d.w, d.P, d.C, L, (unsigned long long*)disp_count, disp_wsum, in_degree);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
 snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_ragged* ff, snn_ragged* lat,
                         const snn_topo_rewire* rw_ff, const snn_topo_rewire* rw_lat, uint64_t input_seed,
                         int32_t rewire_every, int64_t t0, int32_t n_steps, snn_rewire_stats* stats_ff,
@@ -748,6 +849,7 @@ snn_status snn_topo_run(const snn_topo_params* p, const snn_topo_state* st, snn_
         if (npt > 2 && npt <= 4) cs = fused_cluster_size<4>(smem, s);
         if (cs >= 2 && npt <= TOPO_FUSED_MAX_NPT && N <= (npt > 2 ? 4 : npt) * cs * FUSED_THREADS) {
             run.k = topo_consts(p);
+            if ((e = topo_input_table(p, run.in)) != SNN_OK) return e;
             for (int m = 0; m < 2; ++m) {
                 snn_ragged* r = m == 0 ? ff : lat;
                 run.len[m] = r->d.row_len;

@@ -212,14 +212,20 @@ def spikes_from_bits(bits: np.ndarray, n: int) -> np.ndarray:
 
 
 def adam_params(lr: float, step: int, l1: float = 0.0, beta1: float = 0.9, beta2: float = 0.999,
-                eps: float = 1e-8, b1t: float | None = None, b2t: float | None = None, bias_dev=None) -> abi.Adam:
+                eps: float = 1e-8, b1t: float | None = None, b2t: float | None = None, bias_dev=None,
+                temperature: float = 0.0, noise_idx: int | None = None, noise_idx_dev=None) -> abi.Adam:
     """Adam hyper-parameters; bias_dev (device float64 {beta1^t, beta2^t}) makes the
-    kernels read the bias corrections from device memory."""
+    kernels read the bias corrections from device memory.  temperature > 0 turns on the
+    DEEP R noise term with Philox counter noise_idx (default: step - 1) or, if given,
+    the device int64 noise_idx_dev."""
     a = abi.Adam()
     a.lr, a.beta1, a.beta2, a.eps, a.l1 = lr, beta1, beta2, eps, l1
     a.b1t = beta1 ** step if b1t is None else b1t
     a.b2t = beta2 ** step if b2t is None else b2t
     a.bias_dev = abi.ptr(bias_dev)
+    a.temperature = temperature
+    a.noise_idx = step - 1 if noise_idx is None else noise_idx
+    a.noise_idx_dev = abi.ptr(noise_idx_dev)
     return a
 
 
@@ -240,7 +246,9 @@ def train_batch(cls: DeviceClassifier, batch: DeviceBatch, adam: abi.Adam, rewir
 def topo_params(L: int = 32, L_f: int | None = None, radius: int = 3, t_stim: int = 20, dt: float = 1.0,
                 tau_m=20.0, V_rest=-70.0, E_exc=0.0, V_theta=-54.0, V_reset=-70.0, tau_ref=5.0, tau_s=5.0,
                 g_leak=1.0, f_base=20.0, f_in=100.0, g_max=0.2, tau_plus=20.0, tau_minus=64.0,
-                B_ratio=1.2) -> abi.TopoParams:
+                B_ratio=1.2, sigma_stim: float = 0.0) -> abi.TopoParams:
+    """Topographic-map parameters (Tab. 1-2).  t_stim is in steps; sigma_stim > 0 selects
+    the Gaussian input profile (f_in then is the peak rate), 0 the disc of `radius`."""
     p = abi.TopoParams()
     p.L, p.L_f, p.radius2, p.t_stim = L, L_f or L, radius * radius, t_stim
     p.n_ref, p.reserved = int(round(tau_ref / dt)), 0
@@ -249,6 +257,7 @@ def topo_params(L: int = 32, L_f: int | None = None, radius: int = 3, t_stim: in
     p.tau_plus, p.tau_minus = tau_plus, tau_minus
     p.A_plus = 0.1 * g_max
     p.A_minus = B_ratio * p.A_plus * tau_plus / tau_minus
+    p.sigma_stim = sigma_stim
     return p
 
 
@@ -258,6 +267,28 @@ def topo_rewire(L: int, p_form: float, sigma: float, n_att: int, g_max: float = 
     r.p_form, r.sigma, r.p_elim_dep, r.p_elim_pot = p_form, sigma, p_elim_dep, p_elim_pot
     r.g_theta, r.g_new, r.L, r.n_att = 0.5 * g_max, g_max, L, n_att
     return r
+
+
+def attach_event_histograms(rw: abi.TopoRewire, L: int, device="cuda"):
+    """Zeroed elimination / formation histograms (int64, bins = squared torus distance
+    0 .. 2 (L/2)^2) that the rewiring with parameters `rw` adds to; the caller keeps
+    the returned tensors alive while `rw` is in use."""
+    n = 2 * (L // 2) ** 2 + 1
+    elim = torch.zeros(n, dtype=torch.int64, device=device)
+    form = torch.zeros(n, dtype=torch.int64, device=device)
+    rw.elim_d2, rw.form_d2 = abi.ptr(elim), abi.ptr(form)
+    return elim, form
+
+
+def topo_connectivity(r: "DeviceRagged", L: int, stream=None):
+    """(count [L*L] int64, wsum [L*L] float64, in_degree [L*L] int32) by torus
+    displacement dy*L + dx of a topographic projection, on the device."""
+    dev = r.row_len.device
+    count = torch.empty(L * L, dtype=torch.int64, device=dev)
+    wsum = torch.empty(L * L, dtype=torch.float64, device=dev)
+    indeg = torch.empty(L * L, dtype=torch.int32, device=dev)
+    abi.snn_topo_connectivity(r.handle, L, count, wsum, indeg, stream)
+    return count, wsum, indeg
 
 
 class DeviceTopoState:

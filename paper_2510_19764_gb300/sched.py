@@ -55,7 +55,8 @@ def batched_specs(n: int = 64, seed: int = 0) -> list[InstanceSpec]:
 class Instance:
     """One classifier with its training state and device-resident iteration counters."""
 
-    def __init__(self, spec: InstanceSpec, task, device="cuda", lr: float = 1e-3, l1: float = 1e-5):
+    def __init__(self, spec: InstanceSpec, task, device="cuda", lr: float = 1e-3, l1: float = 1e-5,
+                 temperature: float = 0.0):
         import synth
         self.spec = spec
         N, T, p, sd = spec.N, spec.T, spec.p, spec.seed
@@ -77,7 +78,9 @@ class Instance:
         self.betas = torch.tensor([0.9, 0.999], dtype=torch.float64, device=device)
         self.bias = torch.ones(2, dtype=torch.float64, device=device)         # beta^t after the update
         self.stats = torch.zeros((2, 4), dtype=torch.int64, device=device)
-        self.adam = net.adam_params(lr, 1, l1=l1, bias_dev=self.bias)
+        # DEEP R noise (temperature > 0) draws with the iteration counter as Philox field
+        self.adam = net.adam_params(lr, 1, l1=l1, bias_dev=self.bias, temperature=temperature,
+                                    noise_idx_dev=self.step)
         self.lr, self.l1 = lr, l1
         self.events = 0
 

@@ -38,7 +38,7 @@ def test_binding_covers_every_declared_symbol(lib_path):
     from paper_2510_19764_gb300 import abi
     assert sorted(abi.EXPORTED) == _declared_symbols()
     lib = abi.load()
-    assert lib.snn_abi_version() == 5
+    assert lib.snn_abi_version() == 6
     for name in abi.EXPORTED:
         assert callable(getattr(abi, name)), name
 
@@ -55,13 +55,35 @@ def test_argument_errors_are_synchronous_and_need_no_gpu(lib_path):
         abi.snn_eprop_update(None, None, 0, None)
 
 
-def test_struct_layouts_match_header():
+_STRUCTS = {"RaggedDesc": "snn_ragged_desc", "RewireStats": "snn_rewire_stats", "Adam": "snn_adam",
+            "ClassifierDesc": "snn_classifier_desc", "Batch": "snn_batch", "TopoParams": "snn_topo_params",
+            "TopoRewire": "snn_topo_rewire", "TopoState": "snn_topo_state", "DeeprGuide": "snn_deepr_guide"}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes structure has the size and field offsets that a C compiler gives the
+    header's structure of the same fields (compiled with gcc from include/snnsp.h)."""
+    import shutil
+    import subprocess
     from paper_2510_19764_gb300 import abi
-    assert ctypes.sizeof(abi.RaggedDesc) == 24 + 8 * 8 + 8
-    assert ctypes.sizeof(abi.RewireStats) == 32
-    assert ctypes.sizeof(abi.Adam) == 64
-    assert ctypes.sizeof(abi.ClassifierDesc) == 168
-    assert ctypes.sizeof(abi.Batch) == 8 + 19 * 8
-    assert ctypes.sizeof(abi.TopoParams) == 24 + 15 * 8
-    assert ctypes.sizeof(abi.TopoRewire) == 6 * 8 + 8
-    assert ctypes.sizeof(abi.TopoState) == 10 * 8
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "snnsp.h"', "int main(void) {"]
+    for py, c in _STRUCTS.items():
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for f in getattr(abi, py)._fields_:
+            lines.append(f'printf("{py} {f[0]} %zu\\n", offsetof({c}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        py, field, val = ln.split()
+        got[(py, field)] = int(val)
+    for py in _STRUCTS:
+        cls = getattr(abi, py)
+        assert ctypes.sizeof(cls) == got[(py, "size")], py
+        for f in cls._fields_:
+            assert getattr(cls, f[0]).offset == got[(py, f[0])], (py, f[0])

@@ -163,7 +163,47 @@ def test_adam_l1_apply(dtype):
     np.testing.assert_allclose(s.dev.b_out.double().cpu().numpy(), w, rtol=rtol, atol=atol)
 
 
-def _oracle_train(s, batches, lr, l1, T):
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_adam_noise_apply(dtype):
+    """DEEP R's noise term: after the Adam step every active ragged weight adds
+    sqrt(2 lr T) nu with the oracle's Box-Muller normals (host counter, then the device
+    counter); the dense readout gets no noise; padding slots stay untouched."""
+    from paper_2510_19764_gb300 import abi, net
+    s = _setups.classifier(seed=4, dtype=dtype, lif=False, T=10, max_B=1, n_in=40, N=90, K=3)
+    rng = np.random.default_rng(5)
+    lr, temp = 1e-3, 2e-3
+    idx_dev = torch.tensor([7], dtype=torch.int64, device="cuda")
+    for step, (noise_idx, dev_idx) in enumerate(((5, None), (0, idx_dev)), start=1):
+        host = {}
+        for name, d in (("in", s.dev.w_in), ("rec", s.dev.w_rec)):
+            G = _setups.as_dtype(rng.normal(0, 1, d.w.shape), dtype)
+            d.grad.copy_(torch.as_tensor(G))
+            host[name] = (G, d.host())
+        Go = np.zeros((3, 90))
+        s.dev.G_out.copy_(torch.as_tensor(Go))
+        s.dev.G_b.zero_()
+        W0 = s.dev.W_out.double().cpu().numpy()
+        ad = net.adam_params(lr, step, temperature=temp, noise_idx=noise_idx, noise_idx_dev=dev_idx)
+        abi.snn_eprop_update(s.dev.handle, None, abi.SNN_EPROP_APPLY, ad)
+        torch.cuda.synchronize()
+        rtol, atol = (1e-6, 1e-7) if dtype == F32 else (1e-13, 1e-15)
+        k = 7 if dev_idx is not None else noise_idx
+        for name, d in (("in", s.dev.w_in), ("rec", s.dev.w_rec)):
+            G, h = host[name]
+            nu = od.langevin_normals(d.desc.seed, k, h["row_len"], d.C)
+            w, m, v = oc.adam_ragged(h["w"], h["m"], h["v"], G, h["row_len"], lr, 0.9 ** step, 0.999 ** step,
+                                     temperature=temp, nu=nu)
+            got = d.host()
+            np.testing.assert_allclose(got["w"], w, rtol=rtol, atol=atol)       # padding included
+            np.testing.assert_allclose(got["m"], m, rtol=rtol, atol=atol)
+            assert np.abs(nu).max() > 1.0
+        # readout: plain Adam on a zero gradient leaves W_out unchanged
+        np.testing.assert_array_equal(s.dev.W_out.double().cpu().numpy(), W0)
+    with pytest.raises(abi.SnnError):
+        abi.snn_eprop_update(s.dev.handle, None, abi.SNN_EPROP_APPLY, net.adam_params(lr, 1, temperature=-1.0))
+
+
+def _oracle_train(s, batches, lr, l1, T, temperature=0.0):
     """Oracle training run: per batch forward all trials, sum gradients, L1 + Adam,
     DEEP R on both projections (bitfields from the oracle's own init)."""
     n = s.onet
@@ -197,7 +237,9 @@ def _oracle_train(s, batches, lr, l1, T):
         for name in ("in", "rec"):
             rl, ind, w, m, v = st[name]
             Gl = oc.l1_on_sign(G[name], rl, ind, sign[name], l1)
-            w, m, v = oc.adam_ragged(w, m, v, Gl, rl, lr, b1t, b2t)
+            nu = od.langevin_normals(seed_in if name == "in" else seed_rec, bi, rl, w.shape[1]) \
+                if temperature > 0 else None
+            w, m, v = oc.adam_ragged(w, m, v, Gl, rl, lr, b1t, b2t, temperature=temperature, nu=nu)
             out = od.rewire(rl, ind, w, m, v, sign[name], conn[name], w.shape[1], n.N, name == "rec",
                             seed_in if name == "in" else seed_rec, bi)
             st[name] = [out["row_len"], out["ind"], out["w"], out["m"], out["v"]]
@@ -207,12 +249,13 @@ def _oracle_train(s, batches, lr, l1, T):
     return st, conn, W, b, rasters, preds
 
 
-@pytest.mark.parametrize("dtype", [F64, F32])
-def test_training_run_tiny_config(dtype):
+@pytest.mark.parametrize("dtype,temperature", [(F64, 0.0), (F32, 0.0), (F64, 1e-6)])
+def test_training_run_tiny_config(dtype, temperature):
     """32 Poisson inputs -> 64 LIF (v_thr 1) -> 4 readouts, 200 steps, 10 trials of batch
-    1 with e-prop, L1 1e-5, Adam lr 1e-3 and DEEP R after every trial.  FP64: every
-    raster and the final connectivity equal the oracle's exactly; FP32: >= 99.9 % spike
-    agreement and identical predictions."""
+    1 with e-prop, L1 1e-5, Adam lr 1e-3 and DEEP R after every trial, without and with
+    DEEP R's noise term at temperature 1e-6.  FP64: every raster and the final
+    connectivity equal the oracle's exactly; FP32: >= 99.9 % spike agreement and
+    identical predictions."""
     from paper_2510_19764_gb300 import abi, net
     T, n_trials, lr, l1 = 200, 10, 1e-3, 1e-5
     s = _setups.classifier(seed=0, dtype=dtype, lif=True, v_thr=1.0, T=T, max_B=1, w_scale=1.5)
@@ -221,12 +264,12 @@ def test_training_run_tiny_config(dtype):
     batch = net.DeviceBatch(s.dev, batches[0].labels, batches[0].bin_len, batches[0].trial_ids, T)
     for i, tb in enumerate(batches):
         batch.set_trials(tb.labels, tb.bin_len, tb.trial_ids)
-        net.train_batch(s.dev, batch, net.adam_params(lr, i + 1, l1=l1), i)
+        net.train_batch(s.dev, batch, net.adam_params(lr, i + 1, l1=l1, temperature=temperature), i)
         torch.cuda.synchronize()
         g_rasters.append(net.spikes_from_bits(net.u32_to_numpy(batch.z_rec[0]), s.onet.N).astype(np.float64))
         g_preds.append(int(np.argmax(batch.ysum[0].double().cpu().numpy())))
     assert s.dev.w_in.status() == abi.SNN_OK and s.dev.w_rec.status() == abi.SNN_OK
-    st, conn, W, b, rasters, preds = _oracle_train(s, batches, lr, l1, T)
+    st, conn, W, b, rasters, preds = _oracle_train(s, batches, lr, l1, T, temperature)
     total = sum(r.sum() for r in rasters)
     assert total > 100
     if dtype == F64:

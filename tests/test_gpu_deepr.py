@@ -119,3 +119,83 @@ def test_capacity_overflow_reported():
         _compare(d, out, stats)
         overflowed += out["overflow"]
     assert overflowed > 0
+
+
+def _guide(P, Q, L, sigma, seed):
+    """Sites of both populations on an L x L torus: targets in grid order (Q <= L^2),
+    sources spread over the grid by a seeded permutation."""
+    from paper_2510_19764_gb300 import abi
+    rng = np.random.default_rng(seed)
+    pre = (rng.permutation(L * L)[:P] if P <= L * L else rng.integers(0, L * L, P)).astype(np.int32)
+    post = np.arange(Q, dtype=np.int32) % (L * L)
+    g = abi.DeeprGuide()
+    g.L, g.reserved, g.sigma = L, 0, sigma
+    pre_t = torch.as_tensor(pre, device="cuda")
+    post_t = torch.as_tensor(post, device="cuda")
+    g.pre_site, g.post_site = abi.ptr(pre_t), abi.ptr(post_t)
+    return g, (pre_t, post_t), (pre, post, L, od.guide_weights(sigma, L))
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("P,Q,p,no_aut,L,sigma", [(64, 64, 0.2, True, 8, 1.5), (700, 1024, 0.1, False, 32, 3.0),
+                                                  (1024, 1024, 0.1, True, 32, 2.0), (33, 1000, 0.05, False, 32, 40.0),
+                                                  (200, 256, 0.3, False, 16, 0.3)])
+def test_guided_rewire_bit_exact(dtype, P, Q, p, no_aut, L, sigma):
+    """Distance-guided formation (the Discussion's proposal) against the oracle: rows,
+    moved state, bitfields and counts bit for bit, over three rewirings; sigma = 0.3
+    leaves most rows' free targets weightless (uniform fallback)."""
+    from paper_2510_19764_gb300 import abi, net
+    rag = synth.random_ragged(12, P, Q, p, no_autapse=no_aut)
+    rag.w = as_dtype(rag.w, dtype)
+    rng = np.random.default_rng(6)
+    z = np.zeros_like(rag.w)
+    d = net.DeviceRagged(rag.row_len, rag.ind, rag.w, Q, dtype=dtype, no_autapse=no_aut, adam=True, deepr=True,
+                         seed=77)
+    g, keep, oguide = _guide(P, Q, L, sigma, 3)
+    abi.snn_ragged_set_deepr_guide(d.handle, g)
+    sign = net.u32_to_numpy(d.sign_bits).copy()
+    conn = net.u32_to_numpy(d.conn_bits).copy()
+    state = (rag.row_len.copy(), rag.ind.copy(), rag.w.copy(), z.copy(), z.copy())
+    formed = 0
+    for ridx in range(3):
+        rl, ind, w, m, v = state
+        mask = np.arange(rag.C)[None] < rl[:, None]
+        w = as_dtype(np.where(mask, w + rng.normal(0, 0.15, w.shape), w), dtype)
+        d.w.copy_(torch.as_tensor(w))
+        stats = _stats()
+        abi.snn_rewire_deepr(d.handle, ridx, stats)
+        torch.cuda.synchronize()
+        out = od.rewire(rl, ind, w, m, v, sign, conn, rag.C, Q, no_aut, 77, ridx, guide=oguide)
+        _compare(d, out, stats)
+        formed += out["formed"]
+        state = (out["row_len"], out["ind"], out["w"], out["m"], out["v"])
+        conn = out["conn"]
+    assert formed > 0
+    # detaching restores the uniform rule
+    abi.snn_ragged_set_deepr_guide(d.handle, None)
+    rl, ind, w, m, v = state
+    mask = np.arange(rag.C)[None] < rl[:, None]
+    w = as_dtype(np.where(mask, -w, w), dtype)              # every synapse turns dormant
+    d.w.copy_(torch.as_tensor(w))
+    stats = _stats()
+    abi.snn_rewire_deepr(d.handle, 3, stats)
+    torch.cuda.synchronize()
+    _compare(d, od.rewire(rl, ind, w, m, v, sign, conn, rag.C, Q, no_aut, 77, 3), stats)
+
+
+def test_guide_rejects_bad_sites_and_arguments():
+    from paper_2510_19764_gb300 import abi, net
+    rag = synth.random_ragged(13, 40, 64, 0.2)
+    d = net.DeviceRagged(rag.row_len, rag.ind, rag.w, 64, adam=True, deepr=True, seed=1)
+    g, keep, _ = _guide(40, 64, 8, 2.0, 1)
+    keep[1][5] = 64                                   # outside the 8 x 8 grid
+    with pytest.raises(abi.SnnError) as e:
+        abi.snn_ragged_set_deepr_guide(d.handle, g)
+    assert e.value.status == abi.SNN_ESTATE
+    keep[1][5] = 5
+    g.sigma = 0.0
+    with pytest.raises(abi.SnnError):
+        abi.snn_ragged_set_deepr_guide(d.handle, g)
+    g.sigma = 2.0
+    abi.snn_ragged_set_deepr_guide(d.handle, g)
+    assert d.status() == abi.SNN_OK

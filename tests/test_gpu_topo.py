@@ -58,22 +58,36 @@ def test_rewire_bit_exact(L, C, n_att, name):
     assert changes > 0
 
 
-def test_steps_match_oracle_from_same_state():
+def _device_params(p):
+    """The library's parameter structs for an oracle TopoParams."""
+    from paper_2510_19764_gb300 import net
+    return net.topo_params(L=p.L, L_f=p.L_f, radius=p.radius, t_stim=p.t_stim, dt=p.dt, tau_ref=p.tau_ref,
+                           f_base=p.f_base, f_in=p.f_in, sigma_stim=p.sigma_stim)
+
+
+@pytest.mark.parametrize("setting", ["disc", "paper"])
+def test_steps_match_oracle_from_same_state(setting):
+    """disc: the 1 ms workload (disc input, 40/200 Hz); paper: Tab. 1-2 as printed
+    (h = 0.1 ms, Gaussian input, 20 ms stimulus interval, rewiring every 1 ms)."""
     from paper_2510_19764_gb300 import abi, net
-    L, C, T = 16, 32, 60
+    L, C = 16, 32
     N = L * L
-    p = ot.TopoParams(L=L, n_att=10, f_base=40.0, f_in=200.0)
+    if setting == "disc":
+        T = 60
+        p = ot.TopoParams(L=L, n_att=10, f_base=40.0, f_in=200.0)
+    else:
+        T = 300
+        p = ot.paper_setting(L)
     ff = synth.topo_initial(1, L, p.p_form_ff, p.sigma_ff, C, p.g_max)
     lat = synth.topo_initial(2, L, p.p_form_lat, p.sigma_lat, C, p.g_max)
     for r in (ff, lat):
         r.w = as_dtype(r.w, 0)
     dff = net.DeviceRagged(ff.row_len, ff.ind, ff.w, N, dtype=0, seed=11)
     dlat = net.DeviceRagged(lat.row_len, lat.ind, lat.w, N, dtype=0, seed=12)
-    tp = net.topo_params(L=L, f_base=40.0, f_in=200.0)
+    tp = _device_params(p)
     rw_ff = net.topo_rewire(L, p.p_form_ff, p.sigma_ff, p.n_att)
     rw_lat = net.topo_rewire(L, p.p_form_lat, p.sigma_lat, p.n_att)
     st = net.DeviceTopoState(N, p.V_rest)
-    Nw = net.words(N)
     seed_in = 5
     thr_dep, thr_pot = oph.threshold(p.p_elim_dep), oph.threshold(p.p_elim_pot)
     spikes = 0
@@ -136,20 +150,23 @@ def test_steps_match_oracle_from_same_state():
     assert flips <= 2
 
 
-@pytest.mark.parametrize("L,C,T,n_att", [(16, 32, 40, 10), (32, 64, 200, 40), (112, 64, 30, 490)])
-def test_topo_run_matches_granular_calls(L, C, T, n_att):
+@pytest.mark.parametrize("L,C,T,n_att,paper", [(16, 32, 40, 10, False), (32, 64, 200, 40, False),
+                                               (112, 64, 30, 490, False), (16, 32, 400, 10, True),
+                                               (32, 64, 300, 40, True)])
+def test_topo_run_matches_granular_calls(L, C, T, n_att, paper):
     """snn_topo_run (the fused cluster loop) equals the same sequence of granular calls,
-    bit for bit: connectivity, conductances, neuron state and traces."""
+    bit for bit: connectivity, conductances, neuron state and traces; also in the
+    printed setting (h = 0.1 ms, Gaussian input, replicated foci at 32 x 32)."""
     from paper_2510_19764_gb300 import abi, net
     N = L * L
-    p = ot.TopoParams(L=L, n_att=n_att)
+    p = ot.paper_setting(L) if paper else ot.TopoParams(L=L, n_att=n_att)
     res = []
     for mode in ("run", "granular"):
         ff = synth.topo_initial(1, L, p.p_form_ff, p.sigma_ff, C, p.g_max)
         lat = synth.topo_initial(2, L, p.p_form_lat, p.sigma_lat, C, p.g_max)
         dff = net.DeviceRagged(ff.row_len, ff.ind, ff.w, N, dtype=0, seed=11)
         dlat = net.DeviceRagged(lat.row_len, lat.ind, lat.w, N, dtype=0, seed=12)
-        tp = net.topo_params(L=L)
+        tp = _device_params(p)
         rw_ff = net.topo_rewire(L, p.p_form_ff, p.sigma_ff, p.n_att)
         rw_lat = net.topo_rewire(L, p.p_form_lat, p.sigma_lat, p.n_att)
         st = net.DeviceTopoState(N, p.V_rest)
@@ -178,3 +195,30 @@ def test_topo_run_matches_granular_calls(L, C, T, n_att):
     for k in res[0][2]:
         np.testing.assert_array_equal(res[0][2][k], res[1][2][k], err_msg=k)
     assert res[0][2]["tgt_bits"].any() or res[0][2]["y"].max() > 0
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_gaussian_input_bit_exact(L):
+    """snn_topo_input with Tab. 1's Gaussian profile at h = 0.1 ms (replicated 16 x 16
+    foci at 32 x 32) equals the oracle's spikes over several stimulus intervals; a
+    profile too wide for the threshold table is rejected."""
+    from paper_2510_19764_gb300 import abi, net
+    p = ot.paper_setting(L, t_stim=7)
+    tp = _device_params(p)
+    st = net.DeviceTopoState(p.N, p.V_rest)
+    fired = 0
+    for t in range(40):
+        abi.snn_topo_input(tp, st.desc, 9, t)
+        torch.cuda.synchronize()
+        got = net.spikes_from_bits(net.u32_to_numpy(st.src_bits[t & 1]), p.N).astype(bool)
+        want = ot.input_spikes(9, t, p)
+        np.testing.assert_array_equal(got, want)
+        fired += want.sum()
+    assert fired > 10
+    # one 64 x 64 focus tile: squared distances up to 2048 exceed the 1024-entry table;
+    # sigma_stim = 2 has decayed to f_base's rounding by then, sigma_stim = 40 has not
+    big = net.DeviceTopoState(64 * 64, p.V_rest)
+    abi.snn_topo_input(_device_params(ot.paper_setting(64, L_f=None)), big.desc, 9, 0)
+    with pytest.raises(abi.SnnError):
+        abi.snn_topo_input(_device_params(ot.paper_setting(64, L_f=None, sigma_stim=40.0)), big.desc, 9, 0)
+    torch.cuda.synchronize()

@@ -6,6 +6,7 @@ import pytest
 
 import synth
 from oracle import deepr
+from oracle import deepr as od
 
 
 def _bits_of_rows(row_len, ind, P, Q):
@@ -148,3 +149,129 @@ def test_distribution_respects_room_and_reports_overflow():
     dormant = np.array([0, 0, 0, 5], np.int32)      # only 1 slot free in total
     taken, overflow = deepr.distribute(row_len, dormant, C, Q, False, seed=3, rewire_idx=0)
     assert list(taken) == [0, 0, 1, 0] and overflow == 4
+
+
+# --------------------------------------------------------------------------- noise term
+
+def test_box_muller_closed_forms():
+    """u1 = ((w0 >> 11) + 1) 2^-53, u2 = (w1 >> 11) 2^-53, nu = sqrt(-2 ln u1) cos(2 pi u2)
+    at points where the transform has a closed form."""
+    top = np.uint64(2 ** 64 - 1)                  # w >> 11 = 2^53 - 1 -> u1 = 1
+    half = np.uint64(2 ** 63)                     # w >> 11 = 2^52 -> u2 = 1/2, u1 = 1/2 + 2^-53
+    quarter = np.uint64(2 ** 62)                  # u2 = 1/4: cos = 0
+    # smallest u1 = 2^-53 with u2 = 0: sqrt(106 ln 2)
+    assert od.box_muller(0, 0) == pytest.approx(math.sqrt(106 * math.log(2.0)), rel=1e-15)
+    assert od.box_muller(half, half) == pytest.approx(-math.sqrt(-2 * math.log(0.5 + 2 ** -53)), rel=1e-15)
+    assert abs(od.box_muller(half, quarter)) < 1e-15
+    assert od.box_muller(top, 0) == 0.0           # u1 = 1
+    # u1 = 1 - 2^-53: -2 ln u1 = 2^-52 (1 + O(2^-53)), so nu = 2^-26
+    assert od.box_muller(np.uint64((2 ** 53 - 2) << 11), 0) == pytest.approx(2.0 ** -26, rel=1e-6)
+    # only the top 53 bits of each word count
+    assert od.box_muller(np.uint64(0x7FF), np.uint64(0x7FF)) == od.box_muller(0, 0)
+
+
+def test_langevin_normals_are_standard_normal_and_fresh_per_index():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    P, C = 300, 64
+    row_len = np.random.default_rng(0).integers(0, C + 1, P).astype(np.int32)
+    nu = od.langevin_normals(11, 3, row_len, C)
+    active = np.arange(C)[None] < row_len[:, None]
+    assert np.all(nu[~active] == 0.0)
+    x = nu[active]
+    assert x.size > 8000
+    assert scipy_stats.kstest(x, "norm").pvalue > 1e-4
+    assert abs(x.mean()) < 5 / math.sqrt(x.size)
+    assert abs(x.var() - 1.0) < 5 * math.sqrt(2.0 / x.size)
+    y = od.langevin_normals(11, 4, row_len, C)[active]
+    assert abs(np.corrcoef(x, y)[0, 1]) < 5 / math.sqrt(x.size)
+    # a slot's draw depends on (noise_idx, row, slot) only, not on the row's length
+    full = od.langevin_normals(11, 3, np.full(P, C, np.int32), C)
+    np.testing.assert_array_equal(full[active], x)
+
+
+def test_noise_term_variance_is_two_lr_temperature():
+    """With a zero gradient and zero moments the Adam step is exactly 0, so the weight
+    change is the noise alone: sqrt(2 lr T) nu, variance 2 lr T (Bellec et al. 2018)."""
+    from oracle import classifier as oc
+    P, C, lr, T = 200, 50, 1e-3, 1e-6
+    row_len = np.full(P, C, np.int32)
+    w = np.random.default_rng(1).normal(size=(P, C))
+    z = np.zeros((P, C))
+    nu = od.langevin_normals(5, 0, row_len, C)
+    w2, m2, v2 = oc.adam_ragged(w, z, z, z, row_len, lr, 0.9, 0.999, temperature=T, nu=nu)
+    dw = (w2 - w).ravel()
+    n = dw.size
+    assert abs(dw.var() / (2 * lr * T) - 1.0) < 5 * math.sqrt(2.0 / n)
+    assert np.all(m2 == 0) and np.all(v2 == 0)
+    w3, _, _ = oc.adam_ragged(w, z, z, z, row_len, lr, 0.9, 0.999, temperature=0.0, nu=nu)
+    np.testing.assert_array_equal(w3, w)
+
+
+# ------------------------------------------------------------- distance-guided formation
+
+def _rewire_state(seed, P, Q, p, C, no_autapse):
+    rag = synth.random_ragged(seed, P, Q, p, C=C, no_autapse=no_autapse)
+    sign, conn = od.init_bitfields(rag.row_len, rag.ind, rag.w, Q, seed + 1)
+    rng = np.random.default_rng(seed)
+    w = rag.w * np.where(rng.random(rag.w.shape) < 0.1, -1.0, 1.0)     # some synapses turn dormant
+    z = np.zeros_like(w)
+    return rag, w, z, sign, conn
+
+
+def test_weighted_pick_by_hand():
+    wts = [0, 3, 0, 2, 5]
+    got = [od.weighted_pick(wts, r) for r in range(10)]
+    assert got == [1, 1, 1, 3, 3, 4, 4, 4, 4, 4]
+    with pytest.raises(ValueError):
+        od.weighted_pick(wts, 10)
+
+
+@pytest.mark.parametrize("const,Q", [(7, 64), (0, 64), (2 ** 24, 1000)])
+def test_guided_formation_with_equal_weights_is_uniform_formation(const, Q):
+    """Equal weights c: r = mulhi(u, c n_free) lands in bucket floor(r / c) =
+    mulhi(u, n_free), the uniform rule's m; all-zero weights take the uniform fallback.
+    c = 2^24 over ~1000 free targets puts the weight total above 2^32."""
+    P = 64
+    C = 32 if Q == 64 else 128
+    rag, w, z, sign, conn = _rewire_state(3, P, Q, 0.2 if Q == 64 else 0.05, C, True)
+    sites = np.arange(Q)
+    L = 8 if Q == 64 else 32
+    for ridx in range(3):
+        a = od.rewire(rag.row_len, rag.ind, w, z, z, sign, conn, C, Q, True, 9, ridx)
+        b = od.rewire(rag.row_len, rag.ind, w, z, z, sign, conn, C, Q, True, 9, ridx,
+                      guide=(sites, sites, L, [const] * (2 * (L // 2) ** 2 + 1)))
+        assert a["formed"] > 0
+        for k in ("row_len", "ind", "conn"):
+            np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_guided_targets_follow_the_distance_law():
+    """Rows with one activation on an otherwise empty 16 x 16 torus: the chosen target's
+    squared distance d^2 has probability n(d^2) q[d^2] / sum, n(d^2) the sites at d^2."""
+    L, sigma = 16, 2.0
+    Q = P = L * L
+    q = od.guide_weights(sigma, L)
+    assert q[0] == 2 ** 24 and all(q[k] >= q[k + 1] for k in range(len(q) - 1))
+    sites = np.arange(Q)
+    empty = (np.zeros(P, np.int32), np.full((P, 4), -1, np.int32), np.zeros((P, 4)))
+    conn = np.zeros((P, Q // 32), np.uint32)
+    counts = {}
+    n_draw = 0
+    for ridx in range(12):
+        out = od.form_guided(*empty, np.zeros((P, 4)), np.zeros((P, 4)), conn, np.ones(P, np.int32), Q, False,
+                             5, ridx, sites, sites, L, q)
+        for i in range(P):
+            d2 = od.torus_d2_sites(i, int(out[1][i, 0]), L)
+            counts[d2] = counts.get(d2, 0) + 1
+            n_draw += 1
+    n_at = {}
+    for j in range(Q):
+        d2 = od.torus_d2_sites(0, j, L)
+        n_at[d2] = n_at.get(d2, 0) + 1
+    tot = sum(n_at[d2] * q[d2] for d2 in n_at)
+    for d2 in (0, 1, 2, 4, 5, 8, 9, 10, 13, 16, 18):
+        prob = n_at[d2] * q[d2] / tot
+        assert abs(counts.get(d2, 0) - n_draw * prob) < 5 * math.sqrt(n_draw * prob * (1 - prob)) + 1, d2
+    far = sum(c for d2, c in counts.items() if d2 > 32)
+    p_far = sum(n_at[d2] * q[d2] for d2 in n_at if d2 > 32) / tot
+    assert abs(far - n_draw * p_far) < 5 * math.sqrt(n_draw * p_far * (1 - p_far)) + 1

@@ -225,3 +225,129 @@ def test_parameters_match_paper_tables():
     assert all(tab[n][1] for n in ("t_d", "C_m", "f_base", "f_peak", "sigma_stim", "N_attempts", "h", "t_rewiring"))
     # rewiring every t_rewiring / h steps, as printed (10), at the oracle's 1 ms step
     assert p.rewire_every == round(tab["t_rewiring"][0] / tab["h"][0])
+
+
+# --------------------------------------------------------------------- connectivity analysis
+
+def _row_sets(row_len, ind):
+    return [set(int(j) for j in ind[i, :row_len[i]]) for i in range(len(row_len))]
+
+
+def test_event_histograms_equal_the_row_set_differences_of_each_call():
+    """Within one rewiring call a candidate is either eliminated or formed, never both,
+    so the call's eliminations are exactly the synapses missing afterwards and its
+    formations the ones that are new; their squared-distance histograms must equal the
+    ones the rewiring records."""
+    L, C = 16, 16
+    p = topo.TopoParams(L=L, n_att=400)
+    rag = synth.topo_initial(6, L, p.p_form_ff, p.sigma_ff, C, p.g_max)
+    rng = np.random.default_rng(3)
+    g = np.where(rag.ind >= 0, rng.uniform(0, p.g_max, rag.w.shape), 0.0)
+    state = (rag.row_len, rag.ind, g)
+    tot_rm = tot_fm = 0
+    for r in range(6):
+        out = topo.rewire(*state, C, L * L, L, 17, r, p.n_att, philox.threshold(p.p_elim_dep),
+                          philox.threshold(p.p_elim_pot), p.g_theta,
+                          topo.form_thresholds(p.p_form_ff, p.sigma_ff, L), p.g_max)
+        before, after = _row_sets(state[0], state[1]), _row_sets(out["row_len"], out["ind"])
+        gone = [topo.torus_d2(i, j, L) for i in range(L * L) for j in before[i] - after[i]]
+        new = [topo.torus_d2(i, j, L) for i in range(L * L) for j in after[i] - before[i]]
+        np.testing.assert_array_equal(topo.d2_histogram(out["removed_d2"], L), topo.d2_histogram(gone, L))
+        np.testing.assert_array_equal(topo.d2_histogram(out["formed_d2"], L), topo.d2_histogram(new, L))
+        tot_rm += len(gone)
+        tot_fm += len(new)
+        state = (out["row_len"], out["ind"], out["g"])
+    assert tot_rm > 20 and tot_fm > 20
+
+
+def test_unit_distance_bins_by_hand():
+    # L = 4: squared distances 0..8; d = 0 -> bin 0; 1, sqrt2, sqrt3 -> 1; 2 .. sqrt8 -> 2
+    h = np.arange(1, 10, dtype=np.int64)                     # h[d2] = d2 + 1
+    np.testing.assert_array_equal(topo.unit_distance_bins(h), [1, 2 + 3 + 4, 5 + 6 + 7 + 8 + 9])
+    # L = 8: d2 = 9 (d = 3) opens bin 3, d2 = 16 (d = 4) bin 4, d2 = 32 is the largest
+    h = np.zeros(33, dtype=np.int64)
+    h[[8, 9, 15, 16, 32]] = 1
+    np.testing.assert_array_equal(topo.unit_distance_bins(h), [0, 0, 1, 2, 1, 1])
+
+
+def test_connectivity_profile_by_hand():
+    # 3 x 3 torus; x = index % 3, y = index // 3
+    L = 3
+    row_len = np.zeros(9, np.int32)
+    ind = np.full((9, 3), -1, np.int32)
+    g = np.zeros((9, 3))
+    def put(i, js, ws):
+        row_len[i] = len(js)
+        ind[i, :len(js)] = js
+        g[i, :len(js)] = ws
+    put(0, [1, 3, 8], [0.5, 0.25, 0.125])    # (0,0) -> (1,0), (0,1), (2,2)
+    put(4, [0, 4], [1.0, 2.0])               # (1,1) -> (0,0) = (-1,-1) = (2,2); itself (0,0)
+    put(7, [1], [4.0])                       # (1,2) -> (1,0): dy = -2 = 1
+    count, wsum, indeg = topo.connectivity_profile(row_len, ind, g, L)
+    want_c = np.zeros(9, np.int64)
+    want_w = np.zeros(9)
+    for (dx, dy), w in (((1, 0), 0.5), ((0, 1), 0.25), ((2, 2), 0.125), ((2, 2), 1.0), ((0, 0), 2.0),
+                        ((0, 1), 4.0)):
+        want_c[dy * L + dx] += 1
+        want_w[dy * L + dx] += w
+    np.testing.assert_array_equal(count, want_c)
+    np.testing.assert_array_equal(wsum, want_w)
+    np.testing.assert_array_equal(indeg, [1, 2, 0, 1, 1, 0, 0, 0, 1])
+
+
+def test_connectivity_profile_of_initial_maps_follows_the_formation_law():
+    """Pairwise-Bernoulli initial connectivity: the synapses at displacement (dx, dy)
+    number Binomial(N, p_form exp(-d^2 / 2 sigma^2)); in- and out-degrees sum to the
+    synapse count and have the lattice-sum mean."""
+    L, p_form, sigma = 32, 0.16, 2.5
+    N = L * L
+    rag = synth.topo_initial(9, L, p_form, sigma, 64, 0.2)
+    rng = np.random.default_rng(1)
+    g = np.where(rag.ind >= 0, rng.uniform(0, 0.2, rag.w.shape), 0.0)
+    count, wsum, indeg = topo.connectivity_profile(rag.row_len, rag.ind, g, L)
+    assert count.sum() == indeg.sum() == rag.row_len.sum()
+    d2 = synth.torus_d2(np.zeros(N, np.int64), np.arange(N), L)      # displacement k = (k % L, k // L)
+    pk = p_form * np.exp(-d2 / (2 * sigma ** 2))
+    assert np.all(np.abs(count - N * pk) <= 5 * np.sqrt(N * pk * (1 - pk)) + 1)
+    # weights U[0, 0.2): the mean weight of each well-populated displacement is near 0.1
+    big = count > 100
+    assert np.all(np.abs(wsum[big] / count[big] - 0.1) < 5 * 0.2 / math.sqrt(12) / np.sqrt(count[big]))
+    assert abs(indeg.mean() - pk.sum()) < 5 * math.sqrt((pk * (1 - pk)).sum() / N)
+
+
+# ------------------------------------------------------------- the paper's own setting
+
+def test_paper_setting_matches_the_printed_tables():
+    """oracle.topo.paper_setting reproduces the printed time step, delay, input and
+    rewiring-interval lines that the default workload replaces by readings."""
+    tab = _paper_tables()
+    p = topo.paper_setting(16)
+    assert p.dt == tab["h"][0] == tab["t_d"][0]                      # delay = one step
+    assert p.f_base == tab["f_base"][0] and p.f_in == tab["f_peak"][0]
+    assert p.sigma_stim == tab["sigma_stim"][0]
+    assert p.t_stim * p.dt == pytest.approx(tab["t_stim"][0])
+    assert p.rewire_every * p.dt == pytest.approx(tab["t_rewiring"][0])
+    assert p.n_att == tab["N_attempts"][0]
+    assert topo.paper_setting(32).n_att == 4 * tab["N_attempts"][0]  # scaled with s^2
+    assert p.n_ref * p.dt == pytest.approx(tab["tau_ref"][0])
+
+
+def test_gaussian_input_rates_follow_the_profile():
+    """With the focus held (one stimulus interval), channel firing counts in each
+    squared-distance shell are binomial with p = (5 + 152.8 exp(-d^2/8)) Hz x 0.1 ms."""
+    p = topo.paper_setting(16, t_stim=10 ** 9)
+    seed, T = 3, 3000
+    fx, fy = topo.focus(seed, 0, p.L)
+    d2 = synth.torus_d2(np.full(p.N, fx + p.L * fy), np.arange(p.N), p.L)
+    cnt = np.zeros(p.N)
+    for t in range(T):
+        cnt += topo.input_spikes(seed, t, p)
+    for shell in (0, 1, 2, 4, 5, 8, 9, 10, 13, 25, 50, 128):
+        m = d2 == shell
+        if not m.any():
+            continue
+        prob = (5.0 + 152.8 * math.exp(-shell / 8.0)) * 1e-4
+        n = T * m.sum()
+        assert abs(cnt[m].sum() - n * prob) < 5 * math.sqrt(n * prob * (1 - prob)) + 1, shell
+    # the profile's threshold at the focus in closed form
+    assert philox.threshold((5.0 + 152.8) * 0.1 * 1e-3) == int((5.0 + 152.8) * 0.1 * 1e-3 * 2.0 ** 64)
