@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 LAUNCHES_PER_BATCH = 27
 # DRAM bytes (read + write) of one k_forward launch at 512 trials: 4 x the 507.3 MB that
 # ncu measured for the 128-trial case of the same kernel build (None once it changes)
-FORWARD_TRAFFIC = 4 * 507.27e6
+FORWARD_TRAFFIC = 4 * 506.79e6
 METRIC = "e-prop+DEEP R training samples/s"
 UNIT = "samples/s"
 WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}
