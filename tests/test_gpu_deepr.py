@@ -199,3 +199,56 @@ def test_guide_rejects_bad_sites_and_arguments():
     g.sigma = 2.0
     abi.snn_ragged_set_deepr_guide(d.handle, g)
     assert d.status() == abi.SNN_OK
+
+
+def test_rows_rewritten_between_calls():
+    """A caller that reorders rows, moves synapses to other targets and shortens rows
+    between rewirings (keeping the bitfields consistent) gets the oracle's result bit
+    for bit: the library keeps no per-slot state between calls."""
+    from paper_2510_19764_gb300 import abi, net
+    P, Q = 300, 700
+    rag = synth.random_ragged(21, P, Q, 0.08, no_autapse=False)
+    rng = np.random.default_rng(8)
+    d = net.DeviceRagged(rag.row_len, rag.ind, rag.w, Q, dtype=0, adam=True, deepr=True, seed=55)
+    sign = net.u32_to_numpy(d.sign_bits).copy()
+    rl, ind, w = rag.row_len.copy(), rag.ind.copy(), rag.w.copy()
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    conn = net.u32_to_numpy(d.conn_bits).copy()
+    for ridx in range(4):
+        mask = np.arange(rag.C)[None] < rl[:, None]
+        w = as_dtype(np.where(mask, w + rng.normal(0, 0.1, w.shape), w), 0)
+        if ridx > 0:
+            # caller-side edits: shuffle every row, retarget one synapse of every third
+            # row to a free target, drop the last synapse of every fifth row
+            for i in range(P):
+                n = int(rl[i])
+                if n == 0:
+                    continue
+                perm = rng.permutation(n)
+                for arr in (ind, w, m, v):
+                    arr[i, :n] = arr[i, :n][perm]
+                if i % 3 == 0:
+                    taken = set(int(x) for x in ind[i, :n])
+                    new = int(rng.choice([j for j in range(Q) if j not in taken]))
+                    old = int(ind[i, 0])
+                    conn[i, old >> 5] &= np.uint32(~(1 << (old & 31)) & 0xFFFFFFFF)
+                    conn[i, new >> 5] |= np.uint32(1 << (new & 31))
+                    ind[i, 0] = new
+                if i % 5 == 0:
+                    last = int(ind[i, n - 1])
+                    conn[i, last >> 5] &= np.uint32(~(1 << (last & 31)) & 0xFFFFFFFF)
+                    rl[i] = n - 1
+            d.row_len.copy_(torch.as_tensor(rl))
+            d.ind.copy_(torch.as_tensor(np.where(ind >= 0, ind, 0).astype(np.int32)))
+            d.m.copy_(torch.as_tensor(m, dtype=torch.float32))
+            d.v.copy_(torch.as_tensor(v, dtype=torch.float32))
+            d.conn_bits.copy_(torch.as_tensor(conn.view(np.int32)))
+        d.w.copy_(torch.as_tensor(w, dtype=torch.float32))
+        stats = _stats()
+        abi.snn_rewire_deepr(d.handle, ridx, stats)
+        torch.cuda.synchronize()
+        out = od.rewire(rl, ind, w, m, v, sign, conn, rag.C, Q, False, 55, ridx)
+        assert out["removed"] > 0
+        _compare(d, out, stats)
+        rl, ind, w, m, v, conn = out["row_len"], out["ind"], out["w"], out["m"], out["v"], out["conn"]
