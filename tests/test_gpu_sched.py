@@ -17,22 +17,25 @@ def _lib():
     abi.load()
 
 
-def _instances(specs):
+def _instances(specs, temperature=0.0):
     from paper_2510_19764_gb300 import sched
     task = synth.spoken_digit_task(3, n_in=sched.N_IN, n_classes=sched.N_CLASSES, T=1000, n_bins=sched.N_BINS)
-    return [sched.Instance(s, task) for s in specs]
+    return [sched.Instance(s, task, temperature=temperature) for s in specs]
 
 
-def test_batched_graph_equals_plain_per_step():
+@pytest.mark.parametrize("temperature", [0.0, 1e-4])
+def test_batched_graph_equals_plain_per_step(temperature):
+    """Also with DEEP R's noise term, whose Philox counter the captured graph reads from
+    the instance's device iteration counter."""
     from paper_2510_19764_gb300 import sched
     specs = [sched.InstanceSpec(N, T, p, i) for i, (N, T, p) in
              enumerate([(64, 37, 0.2), (128, 80, 0.1), (256, 55, 0.05), (96, 64, 0.15), (300, 41, 0.1)])]
-    plain = _instances(specs)
+    plain = _instances(specs, temperature)
     pr = sched.PlainRunner(plain)
     for _ in range(3):
         pr.iterate()
     torch.cuda.synchronize()
-    batched = _instances(specs)
+    batched = _instances(specs, temperature)
     br = sched.BatchedRunner(batched, n_streams=3)
     br.capture()
     for _ in range(3):
@@ -53,6 +56,14 @@ def test_batched_graph_equals_plain_per_step():
         rewired += int(b.stats[:, 0].sum().item())
         assert a.d_in.status() == 0 and a.d_rec.status() == 0
     assert rewired > 0
+    if temperature > 0:
+        # the noise is there: a noiseless run of the first instance ends elsewhere
+        quiet = _instances(specs[:1])
+        qr = sched.PlainRunner(quiet)
+        for _ in range(3):
+            qr.iterate()
+        torch.cuda.synchronize()
+        assert not np.array_equal(quiet[0].snapshot()["in"]["w"], plain[0].snapshot()["in"]["w"])
 
 
 def test_autotuner_picks_admissible_schedules():
