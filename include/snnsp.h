@@ -101,8 +101,12 @@ typedef struct {
  * connectivity bits cleared, all sign bits drawn from Philox (purpose SIGN, counter
  * (row, word, 0, 0), low 32 bits of word 0), then for every synapse its connectivity
  * bit set and its sign bit forced to the sign of its weight (w > 0: set, w < 0: clear,
- * w == 0: unchanged).  Allocates the handle's fixed scratch (O(P) words).  Returns
- * SNN_EINVAL for bad sizes/pointers, SNN_ESTATE if the contents are invalid. */
+ * w == 0: unchanged).  Allocates the handle's fixed scratch (O(P) words; with sign_bits
+ * also a P*C word array in which DEEP R caches each live slot's sign bit, tagged with the
+ * slot's target: a slot whose target changed outside the library reads the bitfield
+ * again, so callers may rewrite row_len and ind freely, but the sign bit of a potential
+ * connection must stay fixed, as the method has it, Sec. 2.1.2).  Returns SNN_EINVAL for
+ * bad sizes/pointers, SNN_ESTATE if the contents are invalid. */
 snn_status snn_create_ragged(const snn_ragged_desc* desc, int32_t init_deepr_bitfields,
                              snn_stream stream, snn_ragged** out);
 snn_status snn_destroy_ragged(snn_ragged* r);

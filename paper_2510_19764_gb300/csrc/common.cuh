@@ -195,6 +195,9 @@ struct snn_ragged {
     int32_t thr_cap;
     double thr_p, thr_sigma; // parameters the table was built for
     int32_t thr_L;
+    // DEEP R sign tags [P*C]: (target | sign bit << 31) per slot, 0xFFFFFFFF = none;
+    // only handles with sign bits
+    uint32_t* stag;
     // distance-guided DEEP R formation (snn_ragged_set_deepr_guide)
     int32_t guide_on;
     int32_t guide_L;

@@ -157,12 +157,14 @@ snn_status snn_create_ragged(const snn_ragged_desc* d, int32_t init_bits, snn_st
     e = e != cudaSuccess ? e : cudaMalloc(&r->cnt, P * sizeof(int32_t));
     e = e != cudaSuccess ? e : cudaMalloc(&r->scal, 4 * sizeof(int32_t));
     e = e != cudaSuccess ? e : cudaMalloc(&r->thr_form, (size_t)r->thr_cap * sizeof(uint64_t));
+    if (d->sign_bits) e = e != cudaSuccess ? e : cudaMalloc(&r->stag, P * (size_t)d->C * sizeof(uint32_t));
     if (e != cudaSuccess) {
         snn_destroy_ragged(r);
         set_error("snn_create_ragged: cudaMalloc failed: %s", cudaGetErrorString(e));
         return SNN_ENOMEM;
     }
     SNN_CUDA(cudaMemsetAsync(r->status, 0, sizeof(int32_t), s));
+    if (r->stag) SNN_CUDA(cudaMemsetAsync(r->stag, 0xFF, P * (size_t)d->C * sizeof(uint32_t), s));   // no tags yet
     int threads = 256;
     int blocks = ceil_div((long long)d->P * 32, threads);
     k_validate<<<blocks, threads, 0, s>>>(d->row_len, d->ind, d->P, d->Q, d->C, d->no_autapse, r->status);
@@ -194,6 +196,7 @@ snn_status snn_create_ragged(const snn_ragged_desc* d, int32_t init_bits, snn_st
 snn_status snn_destroy_ragged(snn_ragged* r) {
     if (!r) return SNN_OK;
     cudaFree(r->guide_q);
+    cudaFree(r->stag);
     cudaFree(r->status);
     cudaFree(r->dormant);
     cudaFree(r->taken);

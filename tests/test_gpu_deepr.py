@@ -202,9 +202,9 @@ def test_guide_rejects_bad_sites_and_arguments():
 
 
 def test_rows_rewritten_between_calls():
-    """A caller that reorders rows, moves synapses to other targets and shortens rows
-    between rewirings (keeping the bitfields consistent) gets the oracle's result bit
-    for bit: the library keeps no per-slot state between calls."""
+    """The handle caches each slot's sign bit tagged with its target.  A caller that
+    reorders rows, moves synapses to other targets and shortens rows between rewirings
+    (keeping the bitfields consistent) gets the oracle's result bit for bit."""
     from paper_2510_19764_gb300 import abi, net
     P, Q = 300, 700
     rag = synth.random_ragged(21, P, Q, 0.08, no_autapse=False)
@@ -252,3 +252,31 @@ def test_rows_rewritten_between_calls():
         assert out["removed"] > 0
         _compare(d, out, stats)
         rl, ind, w, m, v, conn = out["row_len"], out["ind"], out["w"], out["m"], out["v"], out["conn"]
+
+
+@pytest.mark.parametrize("no_aut", [False, True])
+def test_rewire_bit_exact_wide_rows(no_aut):
+    """Rows of 65536 potential targets (64 chunks of 1024: two per lane in the
+    register-resident formation), three sign flips per row, against the oracle."""
+    from paper_2510_19764_gb300 import abi, net
+    P, Q = 48, 65536
+    rag = synth.random_ragged(31, P, Q, 0.003, C=384, no_autapse=no_aut)
+    d = net.DeviceRagged(rag.row_len, rag.ind, rag.w, Q, dtype=0, no_autapse=no_aut, adam=True, deepr=True, seed=9)
+    sign = net.u32_to_numpy(d.sign_bits).copy()
+    conn = net.u32_to_numpy(d.conn_bits).copy()
+    rl, ind = rag.row_len.copy(), rag.ind.copy()
+    w = as_dtype(rag.w, 0)
+    z = np.zeros_like(w)
+    rng = np.random.default_rng(2)
+    for ridx in range(2):
+        for i in range(P):
+            for s in rng.choice(int(rl[i]), size=min(3, int(rl[i])), replace=False):
+                w[i, s] = -w[i, s]
+        d.w.copy_(torch.as_tensor(w, dtype=torch.float32))
+        stats = _stats()
+        abi.snn_rewire_deepr(d.handle, ridx, stats)
+        torch.cuda.synchronize()
+        out = od.rewire(rl, ind, w, z, z, sign, conn, rag.C, Q, no_aut, 9, ridx)
+        assert out["formed"] > 0
+        _compare(d, out, stats)
+        rl, ind, w, conn = out["row_len"], out["ind"], out["w"], out["conn"]
