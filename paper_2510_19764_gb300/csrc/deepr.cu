@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(DEEPR_THREADS)
     const int nt = taken[i];
     if (nt == 0) return;
     const int lane = lane_id();
-    int32_t* F = form_smem + (size_t)(threadIdx.x >> 5) * NC;
+    int32_t* F = form_smem + (size_t)(threadIdx.x >> 5) * (NC + 1);
     const int forb = (no_autapse && i < Q) ? 1 : 0;
     const uint32_t tail_mask = (Q & 31) ? ~((1u << (Q & 31)) - 1u) : 0u;   // bits beyond Q in the last word
     uint32_t* crow = conn + (size_t)i * Qw;
@@ -269,6 +269,71 @@ __global__ void __launch_bounds__(DEEPR_THREADS)
     }
     __syncwarp();
     const int n0 = len[i];
+    const int n_free0 = Q - forb - n0;
+    if (nt <= 32 && nt <= n_free0 && n0 + nt <= C) {
+        // All activations of the row at once, the same choices as the sequential loop
+        // below.  Activation k takes the m_k-th free target left by the earlier ones,
+        // m_k = mulhi(u_k, n_free0 - k); among the free targets before this call that is
+        // index x_k, the fixed point of x = m_k + |{x_j : j < k, x_j <= x}| (found in
+        // activation order by warp votes); lane k then resolves x_k to its target by a
+        // search of the chunk prefix sums and a scan of one chunk's words, so the
+        // activations of a row resolve side by side instead of one after another.
+        int carry = 0;
+        for (int cb = 0; cb < NC; cb += 32) {        // exclusive prefix of the counts in place
+            const int c = cb + lane;
+            const int f = c < NC ? F[c] : 0;
+            const int incl = warp_incl_scan(f);
+            if (c < NC) F[c] = carry + incl - f;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        __syncwarp();
+        int mk = 0, xk = 0;
+        if (lane < nt) {
+            const uint64_t u = philox(seed, PH_DEEPR_FORM, rewire, (uint64_t)i, (uint64_t)lane, 0).x;
+            mk = (int)mulhi_index(u, (uint64_t)(n_free0 - lane));
+        }
+        for (int k = 0; k < nt; ++k) {
+            const int mkk = __shfl_sync(0xffffffffu, mk, k);
+            int x = mkk;
+            for (int it = 0; it <= k; ++it) {            // x grows by at most k
+                const int xn = mkk + __popc(__ballot_sync(0xffffffffu, lane < k && xk <= x));
+                if (xn == x) break;
+                x = xn;
+            }
+            if (lane == k) xk = x;
+        }
+        int target = -1;
+        if (lane < nt && xk < carry) {
+            int lo = 0, hi = NC - 1;                     // last chunk whose prefix is <= x_k
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (F[mid] <= xk) lo = mid;
+                else hi = mid - 1;
+            }
+            int rem = xk - F[lo];
+            for (int h = 0; h < 32 && target < 0; ++h) {
+                const int wi = lo * 32 + h;
+                const uint32_t fr = ~conn_word(crow, wi, Qw, i, forb, tail_mask);
+                const int pc = __popc(fr);
+                if (rem < pc) target = wi * 32 + nth_set_bit(fr, rem);
+                else rem -= pc;
+            }
+        }
+        const bool bad = __any_sync(0xffffffffu, lane < nt && target < 0);
+        if (!bad && lane < nt) {
+            ind[row + n0 + lane] = target;
+            w[row + n0 + lane] = real(0);
+            m[row + n0 + lane] = real(0);
+            v[row + n0 + lane] = real(0);
+            atomicOr(&crow[target >> 5], 1u << (target & 31));
+        }
+        if (lane == 0) {
+            len[i] = bad ? n0 : n0 + nt;
+            if (bad) atomicOr(status, ST_STATE);
+            else if (stats) atomicAdd((unsigned long long*)&stats->formed, (unsigned long long)nt);
+        }
+        return;
+    }
     int n = n0;
     int formed = 0;
     uint64_t u_l = 0;                                // lane k % 32's draw for activation k
@@ -493,7 +558,7 @@ static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* d
         SNN_LAUNCH_CHECK();
         return SNN_OK;
     }
-    const size_t smem = (size_t)(DEEPR_THREADS / 32) * ((Qw + 31) / 32) * sizeof(int32_t);
+    const size_t smem = (size_t)(DEEPR_THREADS / 32) * ((Qw + 31) / 32 + 1) * sizeof(int32_t);
     SNN_REQUIRE(smem <= 48 * 1024, "snn_rewire_deepr: Q = %d too large for the formation chunk table", d.Q);
     k_deepr_form<real><<<blocks, DEEPR_THREADS, smem, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
                                                             d.conn_bits, taken, d.P, d.C, d.Q, Qw, d.no_autapse,
