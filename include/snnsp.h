@@ -436,6 +436,12 @@ snn_status snn_topo_connectivity(const snn_ragged* r, int32_t L, int64_t* disp_c
 /* ==================================================================================
  * Test hook
  * ================================================================================== */
+/* Failure-detection probe: one warp waits, with the library's bounded mbarrier wait (the
+ * one the adjoint scan's bulk-copy stages use), for a barrier that completes only if
+ * arrive != 0.  After `limit` polls (1 .. 2^24) the wait gives up and sets the timeout
+ * flag in r's status word, so snn_ragged_status then returns SNN_ETIMEOUT; no copy is in
+ * flight and nothing traps, so the context stays usable.  Asynchronous on `stream`. */
+snn_status snn_test_wait_timeout(snn_ragged* r, int32_t arrive, int32_t limit, snn_stream stream);
 /* out[k*4 + q] = word q of Philox4x64-10(key = (seed, purpose), counter = ctr[4k..4k+3])
  * for k < n; ctr and out are device arrays. */
 snn_status snn_philox(uint64_t seed, uint64_t purpose, const uint64_t* ctr, int64_t n,

@@ -1010,6 +1010,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
             : "memory");
     return done != 0;
 }
+// Failure-detection probe: one warp waits, bounded, on an mbarrier that completes only
+// if `arrive` is set; a wait that gives up sets ST_TIMEOUT, as the adjoint scan does.
+// No copy is in flight, so giving up leaves nothing behind.
+__global__ void k_wait_probe(int arrive, int limit, int32_t* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncwarp();
+    if (threadIdx.x == 0 && arrive)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    __syncwarp();
+    const bool got = mbar_wait(&bar, 0u, limit);
+    if (threadIdx.x == 0 && !got) atomicOr(status, ST_TIMEOUT);
+}
+
 // Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) that
 // completes its byte count on the barrier.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -1358,6 +1372,14 @@ snn_status snn_draw_inputs(snn_classifier* c, const snn_batch* b, int32_t t0, in
                 t0, t0 + n_steps, b->T);
     if (n_steps == 0) return SNN_OK;
     return draw_impl(c, b, t0, n_steps, (cudaStream_t)stream);
+}
+
+snn_status snn_test_wait_timeout(snn_ragged* r, int32_t arrive, int32_t limit, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(r && limit > 0 && limit <= (1 << 24), "snn_test_wait_timeout: bad argument");
+    k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(arrive ? 1 : 0, limit, r->status);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
 }
 
 snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase, const snn_adam* adam,

@@ -314,3 +314,29 @@ def test_predrawn_inputs_give_identical_records():
     assert int(net.spikes_from_bits(net.u32_to_numpy(got.z_rec), 128).sum()) > 0
     with pytest.raises(abi.SnnError):
         abi.snn_step_neurons_ex(s.dev.handle, got.desc, 0, T, 2)
+
+
+def test_gradient_of_a_split_batch_is_the_sum_of_its_halves():
+    """The classifier's data-parallel split (trials across ranks, then one sum of the
+    gradients): the gradient of a batch equals the sum of the gradients of its two
+    halves computed separately from the same weights (FP64; only the summation order
+    differs)."""
+    from paper_2510_19764_gb300 import abi, net
+    T, B = 100, 6
+    s = _setups.classifier(seed=11, dtype=F64, lif=False, v_thr=0.6, T=T, max_B=B, n_in=50, N=80, K=4,
+                           n_classes=3, n_bins=2, spoken=True, p_in=0.2, p_rec=0.15, w_scale=1.5)
+    tb = synth.trial_batch(s.task, 0, 0, B)
+
+    def grads(idx):
+        batch = net.DeviceBatch(s.dev, tb.labels[idx], tb.bin_len[idx], tb.trial_ids[idx], T)
+        abi.snn_step_neurons(s.dev.handle, batch.desc, 0, T)
+        abi.snn_eprop_update(s.dev.handle, batch.desc, abi.SNN_EPROP_GRAD, None)
+        torch.cuda.synchronize()
+        return [t.double().cpu().numpy().copy() for t in (s.dev.w_in.grad, s.dev.w_rec.grad, s.dev.G_out, s.dev.G_b)]
+
+    full = grads(np.arange(B))
+    halves = [grads(np.arange(0, B // 2)), grads(np.arange(B // 2, B))]
+    for k, (f, a, b) in enumerate(zip(full, *halves)):
+        scale = max(np.abs(f).max(), 1e-300)
+        assert scale > 0 or k == 3
+        np.testing.assert_allclose(a + b, f, rtol=0, atol=1e-12 * scale)

@@ -208,3 +208,26 @@ def test_rewire_with_nothing_dormant_is_a_no_op():
     for k in before:
         np.testing.assert_array_equal(before[k], after[k], err_msg=k)
     assert r.status() == abi.SNN_OK
+
+
+def test_bounded_wait_gives_up_with_a_status_and_the_context_survives():
+    """Failure detection without a fault: a bounded mbarrier wait on a barrier nothing
+    completes gives up, the handle reports SNN_ETIMEOUT, and the GPU keeps working
+    (a Philox draw afterwards equals the oracle's); the same wait on a completed barrier
+    reports nothing."""
+    import torch
+    from oracle import philox as oph
+    from paper_2510_19764_gb300 import abi, net
+    rag = synth.random_ragged(3, 16, 32, 0.2)
+    d = net.DeviceRagged(rag.row_len, rag.ind, rag.w, 32)
+    abi.snn_test_wait_timeout(d.handle, True, 1 << 20)
+    assert d.status() == abi.SNN_OK
+    abi.snn_test_wait_timeout(d.handle, False, 1 << 16)
+    assert d.status() == abi.SNN_ETIMEOUT
+    assert d.status() == abi.SNN_OK                    # reading the status clears it
+    ctr = torch.tensor([[7, 1, 2, 3]], dtype=torch.int64, device="cuda")
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    abi.snn_philox(5, 1, ctr, 1, out)
+    got = net.u64_to_numpy(out)
+    want = [int(oph.draw(5, 1, np.uint64(7), np.uint64(1), np.uint64(2), np.uint64(3), word=q)) for q in range(4)]
+    assert [int(x) for x in got] == want
