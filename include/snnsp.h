@@ -170,6 +170,26 @@ typedef struct {
  * activation (the uniform rule needs one chunk scan). */
 snn_status snn_ragged_set_deepr_guide(snn_ragged* r, const snn_deepr_guide* g, snn_stream stream);
 
+/* Row updates, the two custom connectivity updates the paper lists (Sec. 2.1: add the
+ * diagonal synapse to every row; remove from every row the synapse to a target the host
+ * drew).  One optional edit per row, rows in parallel (a warp each).  targets: device
+ * int32 [P], -1 = no edit.
+ *  snn_ragged_add_row: appends synapse i -> targets[i] at slot row_len[i] with weight
+ *    w_new[i] (device array of the matrix dtype, or NULL for 0), zero m, v and grad where
+ *    the handle has them, and its connectivity bit where it has bitfields.  A target
+ *    already in the row or a full row is skipped (stats->overflow).
+ *  snn_ragged_remove_row: removes synapse i -> targets[i] if the row has it; the later
+ *    slots move down one and keep their order (the paper moves the last synapse into the
+ *    hole, which leaves the same set), and its connectivity bit is cleared
+ *    (stats->removed).
+ * A target outside [0, Q), or a self target of a no_autapse matrix, is skipped and sets
+ * the invalid-state flag (SNN_ESTATE at the next snn_ragged_status).  Sign bits are not
+ * touched.  stats: device or NULL (formed counts the adds).  Asynchronous. */
+snn_status snn_ragged_add_row(snn_ragged* r, const int32_t* targets, const void* w_new, snn_rewire_stats* stats,
+                              snn_stream stream);
+snn_status snn_ragged_remove_row(snn_ragged* r, const int32_t* targets, snn_rewire_stats* stats,
+                                 snn_stream stream);
+
 /* DEEP R rewiring that allocates nothing (the paper has no counterpart; this entry
  * exists for callers that cannot allocate device memory).  Some callers cannot call
  * cudaMalloc: a serving process that reserved its whole device-memory budget at start-up

@@ -26,7 +26,7 @@ EXPORTED = [
     "snn_eprop_update", "snn_topo_input", "snn_topo_neurons", "snn_stdp_update", "snn_rewire_topo", "snn_topo_run",
     "snn_philox", "snn_rewire_deepr_noalloc", "snn_classifier_set_schedule", "snn_rewire_deepr_dev",
     "snn_draw_inputs", "snn_step_neurons_ex", "snn_topo_connectivity", "snn_ragged_set_deepr_guide",
-    "snn_test_wait_timeout",
+    "snn_test_wait_timeout", "snn_ragged_add_row", "snn_ragged_remove_row",
 ]
 
 
@@ -134,6 +134,8 @@ def load() -> C.CDLL:
         "snn_topo_connectivity": (i32, [vp, i32, vp, vp, vp, vp]),
         "snn_ragged_set_deepr_guide": (i32, [vp, vp, vp]),
         "snn_test_wait_timeout": (i32, [vp, i32, i32, vp]),
+        "snn_ragged_add_row": (i32, [vp, vp, vp, vp, vp]),
+        "snn_ragged_remove_row": (i32, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -258,6 +260,14 @@ def snn_topo_run(p: TopoParams, st: TopoState, ff: int, lat: int, rw_ff: TopoRew
 
 def snn_ragged_set_deepr_guide(h: int, g: "DeeprGuide | None", stream=None) -> None:
     check(load().snn_ragged_set_deepr_guide(h, C.byref(g) if g is not None else None, stream_ptr(stream)))
+
+
+def snn_ragged_add_row(h: int, targets, w_new=None, stats=None, stream=None) -> None:
+    check(load().snn_ragged_add_row(h, ptr(targets), ptr(w_new), ptr(stats), stream_ptr(stream)))
+
+
+def snn_ragged_remove_row(h: int, targets, stats=None, stream=None) -> None:
+    check(load().snn_ragged_remove_row(h, ptr(targets), ptr(stats), stream_ptr(stream)))
 
 
 def snn_test_wait_timeout(h: int, arrive: bool, limit: int, stream=None) -> None:

@@ -70,6 +70,90 @@ __global__ void k_sign_from_weights(const int32_t* __restrict__ row_len, const i
     }
 }
 
+// ------------------------------------------------------------------ row updates
+// One warp per row with an edit (targets[i] >= 0).  Add: skip a target already in the
+// row (connectivity bit when the handle has bitfields, else a ballot over the row) or a
+// full row, else append at slot row_len with the given weight and zero optimiser state.
+// Remove: find the target's slot, move the later slots down one (every lane of a chunk
+// reads before any writes), clear the bit.  Counts go to stats (formed / removed /
+// overflow for skipped adds).
+template <typename real>
+__global__ void k_row_edit(int remove, int32_t* __restrict__ len, int32_t* __restrict__ ind, real* __restrict__ w,
+                           real* __restrict__ m, real* __restrict__ v, real* __restrict__ grad,
+                           uint32_t* __restrict__ conn, const int32_t* __restrict__ targets,
+                           const real* __restrict__ w_new, int P, int Q, int C, int Qw, int no_autapse,
+                           int32_t* status, snn_rewire_stats* stats) {
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= P) return;
+    const int t = targets[i];
+    if (t < 0) return;
+    const int lane = lane_id();
+    if (t >= Q || (no_autapse && t == i)) {
+        if (lane == 0) {
+            atomicOr(status, ST_STATE);
+            if (stats && !remove) atomicAdd((unsigned long long*)&stats->overflow, 1ull);
+        }
+        return;
+    }
+    const int n = len[i];
+    const size_t row = (size_t)i * C;
+    int found = -1;                                  // slot of t in the row, or -1
+    if (remove || !conn) {
+        for (int b0 = 0; b0 < n && found < 0; b0 += 32) {
+            const int s = b0 + lane;
+            const uint32_t hm = __ballot_sync(0xffffffffu, s < n && ind[row + s] == t);
+            if (hm) found = b0 + __ffs(hm) - 1;
+        }
+    } else {
+        found = ((conn[(size_t)i * Qw + (t >> 5)] >> (t & 31)) & 1u) ? 0 : -1;
+    }
+    if (!remove) {
+        if (lane == 0) {
+            if (found >= 0 || n >= C) {
+                if (stats) atomicAdd((unsigned long long*)&stats->overflow, 1ull);
+            } else {
+                ind[row + n] = t;
+                w[row + n] = w_new ? w_new[i] : real(0);
+                if (m) m[row + n] = real(0);
+                if (v) v[row + n] = real(0);
+                if (grad) grad[row + n] = real(0);
+                if (conn) conn[(size_t)i * Qw + (t >> 5)] |= 1u << (t & 31);
+                len[i] = n + 1;
+                if (stats) atomicAdd((unsigned long long*)&stats->formed, 1ull);
+            }
+        }
+        return;
+    }
+    if (found < 0) return;
+    for (int b0 = found + 1; b0 < n; b0 += 32) {
+        const int s = b0 + lane;
+        const bool ok = s < n;
+        int j = 0;
+        real ww = 0, mm = 0, vv = 0, gg = 0;
+        if (ok) {
+            j = ind[row + s];
+            ww = w[row + s];
+            if (m) mm = m[row + s];
+            if (v) vv = v[row + s];
+            if (grad) gg = grad[row + s];
+        }
+        __syncwarp();
+        if (ok) {
+            ind[row + s - 1] = j;
+            w[row + s - 1] = ww;
+            if (m) m[row + s - 1] = mm;
+            if (v) v[row + s - 1] = vv;
+            if (grad) grad[row + s - 1] = gg;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (conn) conn[(size_t)i * Qw + (t >> 5)] &= ~(1u << (t & 31));
+        len[i] = n - 1;
+        if (stats) atomicAdd((unsigned long long*)&stats->removed, 1ull);
+    }
+}
+
 // ------------------------------------------------------------------ propagation
 // Grid (word blocks, B).  A warp owns one 32-row word of the presynaptic spike bits of
 // instance b and walks its set bits; lanes stride the row's slots and add the weight
@@ -229,6 +313,36 @@ snn_status snn_ragged_status(snn_ragged* r, snn_stream stream) {
         return SNN_ECAPACITY;
     }
     return SNN_OK;
+}
+
+static snn_status row_edit(snn_ragged* r, int remove, const int32_t* targets, const void* w_new,
+                           snn_rewire_stats* stats, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(r && targets, "snn_ragged_%s_row: NULL argument", remove ? "remove" : "add");
+    const snn_ragged_desc& d = r->d;
+    const int threads = 256;
+    const int blocks = ceil_div((long long)d.P * 32, threads);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d.dtype == SNN_F32)
+        k_row_edit<float><<<blocks, threads, 0, s>>>(remove, d.row_len, d.ind, (float*)d.w, (float*)d.m, (float*)d.v,
+                                                     (float*)d.grad, d.conn_bits, targets, (const float*)w_new, d.P,
+                                                     d.Q, d.C, r->Qw, d.no_autapse, r->status, stats);
+    else
+        k_row_edit<double><<<blocks, threads, 0, s>>>(remove, d.row_len, d.ind, (double*)d.w, (double*)d.m,
+                                                      (double*)d.v, (double*)d.grad, d.conn_bits, targets,
+                                                      (const double*)w_new, d.P, d.Q, d.C, r->Qw, d.no_autapse,
+                                                      r->status, stats);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+snn_status snn_ragged_add_row(snn_ragged* r, const int32_t* targets, const void* w_new, snn_rewire_stats* stats,
+                              snn_stream stream) {
+    return row_edit(r, 0, targets, w_new, stats, stream);
+}
+
+snn_status snn_ragged_remove_row(snn_ragged* r, const int32_t* targets, snn_rewire_stats* stats, snn_stream stream) {
+    return row_edit(r, 1, targets, nullptr, stats, stream);
 }
 
 snn_status snn_propagate(const snn_ragged* r, const uint32_t* pre_bits, int32_t B, int64_t* post_acc,
