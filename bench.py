@@ -577,12 +577,34 @@ def run_topo(args):
     b.synchronize()
     ms = a.elapsed_time(b)
     stats_ff, stats_lat = s_ff.cpu().tolist(), s_lat.cpu().tolist()
+    cpu = topo_cpu_baseline(args, L)
     return {"workload": "topo", "metric": f"simulated steps/s ({dt:g} ms steps)", "setting": args.topo_setting,
+            "cpu_baseline": cpu,
             "L": L, "neurons_per_sheet": N, "steps": n, "steps_per_s": round(n / (ms / 1e3), 1),
             "realtime_factor": round(n * dt / ms, 2), "ms_per_1000_steps": round(ms / n * 1000, 3),
             "path": "one thread-block-cluster launch per 1000 steps (up to 4 neurons per thread)",
             "rewire_ff": dict(zip(["removed", "formed", "overflow", "attempts"], stats_ff)),
             "rewire_lat": dict(zip(["removed", "formed", "overflow", "attempts"], stats_lat))}
+
+
+def topo_cpu_baseline(args, L, budget_s=3.0, max_steps=1000):
+    """The FP64 oracle on one core for the same map, setting and seeds: steps from t = 0
+    until about budget_s seconds have passed (at most max_steps), rewiring included."""
+    import synth
+    from oracle import topo as ot
+    p = ot.paper_setting(L) if args.topo_setting == "paper" else \
+        ot.TopoParams(L=L, n_att=10 * args.scale * args.scale, L_f=16 if args.scale > 2 else None)
+    ff = synth.topo_initial(args.seed + 1, L, 0.16, 2.5, 64, 0.2)
+    lat = synth.topo_initial(args.seed + 2, L, 1.0, 1.0, 64, 0.2)
+    st = ot.initial_state([ff.row_len, ff.ind, ff.w], [lat.row_len, lat.ind, lat.w], p)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and (n < 20 or time.perf_counter() - t0 < budget_s):
+        ot.step(st, n, p, {"input": 5, "ff": 11, "lat": 12}, 64)
+        n += 1
+    dt_s = time.perf_counter() - t0
+    return {"value": round(n / dt_s, 2), "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} steps from t = 0 of the same map ({dt_s:.1f} s)"}
 
 
 def run_topo_evolution(args):
