@@ -696,7 +696,7 @@ def run_kernels(args):
     """DEEP R rewiring and standalone ragged propagation on a 65536 x 65536 projection
     (~287 synapses per row, 18.8 M synapses; arrays and bitfields ~1.4 GB, far larger
     than L2): mean CUDA-event time per call after warm-up, and the algorithmic bytes of
-    each call (the survey's per-unit byte model) per second against the measured HBM
+    each call (bytes the method must move per unit of work) per second against the measured HBM
     copy bandwidth."""
     import torch
     import synth
