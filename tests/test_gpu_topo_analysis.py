@@ -56,7 +56,7 @@ def test_rewire_event_histograms_match_oracle(L, C, n_att, name):
     assert d.status() == abi.SNN_OK
 
 
-@pytest.mark.parametrize("L,C,T,n_att", [(16, 32, 100, 40), (32, 64, 400, 40)])
+@pytest.mark.parametrize("L,C,T,n_att", [(16, 32, 100, 40), (32, 64, 400, 40), (112, 64, 40, 490)])
 def test_fused_run_records_the_same_events_as_granular_calls(L, C, T, n_att):
     """snn_topo_run (one cluster launch) fills the histograms exactly as the per-step
     calls do, and the connectivity profile of the final state matches the oracle's."""
