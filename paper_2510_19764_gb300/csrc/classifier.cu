@@ -391,51 +391,43 @@ __global__ void k_reduce_gb(const real* __restrict__ gb_part, real* __restrict__
 
 // Filtered readout error D_k^t = d_k^{t+1} + alpha D_k^{t+1} (D^{T-1} = 0), i.e.
 // D_k^t = sum_{u > t} alpha^{u-t-1} d_k^u, and the bias gradient partial sum_t d_k^t.
-// One warp per (trial, readout): lane L scans steps [L S, (L+1) S) backwards with a zero
-// carry, then the carries D^{(L+1) S} are chained across lanes from the last lane down
-// (D^t = local^t + alpha^{(L+1) S - t} carry_L).
+// One warp per trial, lane k per readout (padding lanes k >= K write zeros): the warp
+// walks the steps backwards reading and writing one contiguous row per step, with the
+// rows of the next RS_AHEAD steps loaded ahead of the recurrence.
+constexpr int RS_AHEAD = 8;
+
 template <typename real>
 __global__ void k_readout_scan(const real* __restrict__ d, real* __restrict__ Dout, real* __restrict__ gb_part,
                                int B, int T, int K, int Kp, real alpha) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = lane_id();
-    if (w >= B * Kp) return;
-    const int b = w / Kp, k = w % Kp;
-    const int S = (T + 31) / 32;
-    const int s0 = lane * S, s1 = min(T, s0 + S);
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int k = lane_id();
+    if (b >= B || k >= Kp) return;
     const real* db = d + (size_t)b * T * K;
     real* Db = Dout + (size_t)b * T * Kp;
-    if (k >= K) {
-        for (int t = s0; t < s1; ++t) Db[(size_t)t * Kp + k] = real(0);
-        return;
+    const bool live = k < K;
+    real E = 0, gsum = 0;
+    real dn = 0;                                     // d^{t+1}
+    // steps in blocks of RS_AHEAD, from the end: the block's d rows are loaded first
+    for (int t1 = T; t1 > 0; t1 -= RS_AHEAD) {
+        const int t0 = t1 - RS_AHEAD > 0 ? t1 - RS_AHEAD : 0;
+        real dv[RS_AHEAD];
+#pragma unroll
+        for (int r = 0; r < RS_AHEAD; ++r) {
+            const int t = t1 - 1 - r;
+            dv[r] = (live && t >= t0) ? db[(size_t)t * K + k] : real(0);
+        }
+#pragma unroll
+        for (int r = 0; r < RS_AHEAD; ++r) {
+            const int t = t1 - 1 - r;
+            if (t >= t0) {
+                E = (t == T - 1) ? real(0) : dn + alpha * E;
+                Db[(size_t)t * Kp + k] = E;
+                gsum += dv[r];
+                dn = dv[r];
+            }
+        }
     }
-    // local backward scan with zero carry: E^t = d^{t+1} + alpha E^{t+1} inside the chunk
-    real E = 0, gsum = 0, apow = 1;   // apow = alpha^{s1 - s0} at the end
-    for (int t = s1 - 1; t >= s0; --t) {
-        const real dn = (t + 1 < T) ? db[(size_t)(t + 1) * K + k] : real(0);
-        E = (t == T - 1) ? real(0) : dn + alpha * E;
-        gsum += db[(size_t)t * K + k];
-        apow *= alpha;
-    }
-    const real E0 = E;                       // E at the chunk's first step s0
-    // carry_L = D^{s1}: chain from the last lane: D^{s0 of lane L} = E0_L + alpha^{len_L} carry_L
-    real carry = 0;
-    for (int L = 30; L >= 0; --L) {
-        const real e0_next = __shfl_sync(0xffffffffu, E0, L + 1);
-        const real ap_next = __shfl_sync(0xffffffffu, apow, L + 1);
-        const real c_next = __shfl_sync(0xffffffffu, carry, L + 1);
-        if (lane == L) carry = e0_next + ap_next * c_next;
-    }
-    // final values: D^t = E^t + alpha^{s1 - t} carry
-    real Dt = 0, ap = alpha;
-    for (int t = s1 - 1; t >= s0; --t) {
-        const real dn = (t + 1 < T) ? db[(size_t)(t + 1) * K + k] : real(0);
-        Dt = (t == T - 1) ? real(0) : dn + alpha * Dt;
-        Db[(size_t)t * Kp + k] = (t == T - 1) ? real(0) : Dt + ap * carry;
-        ap *= alpha;
-    }
-    gsum = warp_sum(gsum);
-    if (lane == 0) gb_part[(size_t)b * K + k] = gsum;
+    if (live) gb_part[(size_t)b * K + k] = gsum;
 }
 
 // The adjoint scan.  CTA = (trial, BWD_THREADS hidden neurons); steps are walked backwards
@@ -1175,7 +1167,7 @@ static snn_status grad_impl(snn_classifier* c, const snn_batch* bt, cudaStream_t
     const int B = bt->B, T = bt->T, N = d.N, K = d.K, Kp = (K + 3) & ~3;
     const int Win = (d.n_in + 31) / 32, Wh = (N + 31) / 32;
     real* gb_part = (real*)c->part_out + (size_t)c->KS * N * K;
-    k_readout_scan<real><<<ceil_div((long long)B * Kp * 32, 256), 256, 0, s>>>(
+    k_readout_scan<real><<<ceil_div((long long)B * 32, 128), 128, 0, s>>>(
         (const real*)bt->d_rec, (real*)bt->Dout, gb_part, B, T, K, Kp, (real)c->alpha);
     SNN_LAUNCH_CHECK();
     switch (Kp / 4) {
