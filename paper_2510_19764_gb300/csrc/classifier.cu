@@ -324,21 +324,39 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
 }
 
 // d^t = softmax(y^t) - onehot(label) for every recorded (trial, step), in place over the
-// y values the forward left in the d record.  Thread = one (trial, step).
+// y values the forward left in the d record.  A warp takes 32 consecutive steps of one
+// trial: their rows are one contiguous span of 32 K values, read and written whole by
+// the warp (coalesced); lane r computes row r from shared memory.
+constexpr int SMX_WARPS = 4;
+
 template <typename real>
-__global__ void k_softmax_d(real* __restrict__ d, const int32_t* __restrict__ labels, int n_classes,
-                            const int32_t* __restrict__ trial_T, int B, int T, int K, int t0, int n_steps) {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= (long long)B * n_steps) return;
-    const int b = (int)(g / n_steps), t = t0 + (int)(g % n_steps);
-    if (trial_T && t >= trial_T[b]) return;
-    const int label = min(max(labels[b], 0), n_classes - 1);
-    real* y = d + ((size_t)b * T + t) * K;
-    real mx = y[0];
-    for (int k = 1; k < K; ++k) mx = y[k] > mx ? y[k] : mx;
-    real ssum = 0;
-    for (int k = 0; k < K; ++k) ssum += exp_real(y[k] - mx);
-    for (int k = 0; k < K; ++k) y[k] = exp_real(y[k] - mx) / ssum - (k == label ? real(1) : real(0));
+__global__ void __launch_bounds__(SMX_WARPS * 32)
+    k_softmax_d(real* __restrict__ d, const int32_t* __restrict__ labels, int n_classes,
+                const int32_t* __restrict__ trial_T, int B, int T, int K, int t0, int n_steps) {
+    extern __shared__ __align__(16) unsigned char smx_raw[];
+    real* sh = (real*)smx_raw + (size_t)(threadIdx.x >> 5) * 32 * K;
+    const int lane = lane_id();
+    const int blocks_per_trial = (n_steps + 31) / 32;
+    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wg >= (long long)B * blocks_per_trial) return;
+    const int b = (int)(wg / blocks_per_trial);
+    const int ts = t0 + (int)(wg % blocks_per_trial) * 32;          // first step of the span
+    const int nr = min(32, t0 + n_steps - ts);                      // rows in the span
+    real* span = d + ((size_t)b * T + ts) * K;
+    for (int e = lane; e < nr * K; e += 32) sh[e] = span[e];
+    __syncwarp();
+    const int t = ts + lane;
+    if (lane < nr && !(trial_T && t >= trial_T[b])) {
+        const int label = min(max(labels[b], 0), n_classes - 1);
+        real* y = sh + lane * K;
+        real mx = y[0];
+        for (int k = 1; k < K; ++k) mx = y[k] > mx ? y[k] : mx;
+        real ssum = 0;
+        for (int k = 0; k < K; ++k) ssum += exp_real(y[k] - mx);
+        for (int k = 0; k < K; ++k) y[k] = exp_real(y[k] - mx) / ssum - (k == label ? real(1) : real(0));
+    }
+    __syncwarp();
+    for (int e = lane; e < nr * K; e += 32) span[e] = sh[e];
 }
 
 // Packed forward rows: row r < n_in is input row r, row n_in + j is hidden row j; Cf
@@ -865,9 +883,10 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
         default: st = launch_forward_th<real, 256>(p, bt->B, smem, s); break;
     }
     if (st != SNN_OK || !bt->d_rec) return st;
-    const long long n = (long long)bt->B * n_steps;
-    k_softmax_d<real><<<ceil_div(n, 256), 256, 0, s>>>((real*)bt->d_rec, bt->labels, d.n_classes, bt->trial_T, bt->B,
-                                                       bt->T, d.K, t0, n_steps);
+    const long long warps = (long long)bt->B * ((n_steps + 31) / 32);
+    const size_t smx = (size_t)SMX_WARPS * 32 * d.K * sizeof(real);   // <= 32 KB (K <= 32)
+    k_softmax_d<real><<<ceil_div(warps, SMX_WARPS), SMX_WARPS * 32, smx, s>>>(
+        (real*)bt->d_rec, bt->labels, d.n_classes, bt->trial_T, bt->B, bt->T, d.K, t0, n_steps);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
