@@ -53,6 +53,16 @@ def test_argument_errors_are_synchronous_and_need_no_gpu(lib_path):
     assert "P, Q, C" in abi.load().snn_last_error().decode()
     with pytest.raises(abi.SnnError):
         abi.snn_eprop_update(None, None, 0, None)
+    # the entry points added for the analysis, the DEEP R variants and the row updates
+    # check their handles before touching the device
+    for call in (lambda: abi.snn_topo_connectivity(None, 8),
+                 lambda: abi.snn_ragged_set_deepr_guide(None, abi.DeeprGuide()),
+                 lambda: abi.snn_ragged_add_row(None, None),
+                 lambda: abi.snn_ragged_remove_row(None, None),
+                 lambda: abi.snn_test_wait_timeout(None, False, 16)):
+        with pytest.raises(abi.SnnError) as e:
+            call()
+        assert e.value.status == abi.SNN_EINVAL
 
 
 _STRUCTS = {"RaggedDesc": "snn_ragged_desc", "RewireStats": "snn_rewire_stats", "Adam": "snn_adam",
