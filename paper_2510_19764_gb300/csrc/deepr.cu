@@ -1,19 +1,24 @@
 // DEEP R rewiring on the ragged matrix with sign and connectivity bitfields
 // (Sec. 2.1.2, Fig. 2B-C of the paper).
 //
-//  k_deepr_eliminate  : one warp per row; a synapse is dormant when its weight's sign is
-//                       strictly opposite to its fixed sign bit; survivors are compacted
+//  k_deepr_eliminate  : one warp per row, two 32-slot chunks per memory round trip; a
+//                       synapse is dormant when its weight's sign is strictly opposite to
+//                       its fixed sign bit (read from the slot's sign tag when the tag's
+//                       target matches, else from the bitfield); survivors are compacted
 //                       stably with a warp ballot + prefix count (w, m, v move along),
 //                       connectivity bits of removed synapses are cleared; the dormant
 //                       total D is summed on the device.
 //  k_deepr_round0     : the whole grid draws round 0 of the redistribution (D rows)
 //                       into a per-row histogram with integer atomics.
-//  k_deepr_distribute : one CTA; accepts round 0 up to each row's room and runs the
-//                       remaining rounds on the leftovers (order-independent counts).
-//  k_deepr_form       : one warp per row with activations; each activation appends the
-//                       m-th free target: a scan over per-chunk free counts (chunks of
-//                       1024 targets, kept in shared memory) finds the chunk, one
-//                       32-word scan finds the bit.
+//  k_deepr_accept0    : the whole grid accepts round 0 up to each row's room.
+//  k_deepr_distribute : one CTA; runs the remaining rounds on the leftovers
+//                       (order-independent counts).
+//  k_deepr_form       : one warp per row with activations; per-chunk free counts (chunks
+//                       of 1024 targets, kept in shared memory); a row's first 32
+//                       activations are resolved side by side (one lane each), longer
+//                       lists one after another: a scan over the chunk counts finds the
+//                       chunk, a 32-word scan finds the bit.
+//  k_deepr_form_guided: distance-guided variant (a guide attached to the handle).
 #include "common.cuh"
 
 #include <cmath>
