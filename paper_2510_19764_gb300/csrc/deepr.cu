@@ -14,10 +14,10 @@
 //  k_deepr_distribute : one CTA; runs the remaining rounds on the leftovers
 //                       (order-independent counts).
 //  k_deepr_form       : one warp per row with activations; per-chunk free counts (chunks
-//                       of 1024 targets, kept in shared memory); a row's first 32
-//                       activations are resolved side by side (one lane each), longer
-//                       lists one after another: a scan over the chunk counts finds the
-//                       chunk, a 32-word scan finds the bit.
+//                       of 1024 targets, kept in shared memory); a row with up to 32
+//                       activations resolves them side by side (one lane each), a row
+//                       with more one after another; either way a scan over the chunk
+//                       counts finds the chunk and a 32-word scan finds the bit.
 //  k_deepr_form_guided: distance-guided variant (a guide attached to the handle).
 #include "common.cuh"
 
