@@ -398,13 +398,24 @@ __global__ void k_pack(const real* __restrict__ w_in, const int32_t* __restrict_
 }
 
 // ------------------------------------------------------------------ backward
+// G_b[k] = sum over trials of the per-trial partials: one CTA per readout, a strided
+// sum per thread, then a fixed-order tree (deterministic).
+constexpr int RGB_THREADS = 256;
+
 template <typename real>
-__global__ void k_reduce_gb(const real* __restrict__ gb_part, real* __restrict__ G_b, int B, int K) {
-    int k = threadIdx.x;
-    if (k >= K) return;
+__global__ void __launch_bounds__(RGB_THREADS)
+    k_reduce_gb(const real* __restrict__ gb_part, real* __restrict__ G_b, int B, int K) {
+    __shared__ real red[RGB_THREADS];
+    const int k = blockIdx.x;
     real s = 0;
-    for (int b = 0; b < B; ++b) s += gb_part[(size_t)b * K + k];
-    G_b[k] = s;
+    for (int b = threadIdx.x; b < B; b += RGB_THREADS) s += gb_part[(size_t)b * K + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = RGB_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) G_b[k] = red[0];
 }
 
 // Filtered readout error D_k^t = d_k^{t+1} + alpha D_k^{t+1} (D^{T-1} = 0), i.e.
@@ -1200,7 +1211,7 @@ static snn_status grad_impl(snn_classifier* c, const snn_batch* bt, cudaStream_t
         default: launch_backward<real, 8>(c, bt, s); break;
     }
     SNN_LAUNCH_CHECK();
-    k_reduce_gb<real><<<1, 32, 0, s>>>(gb_part, (real*)d.G_b, B, K);
+    k_reduce_gb<real><<<K, RGB_THREADS, 0, s>>>(gb_part, (real*)d.G_b, B, K);
     SNN_LAUNCH_CHECK();
     const long long BT = (long long)B * T;
     const int KS = c->KS;
