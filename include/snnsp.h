@@ -206,6 +206,10 @@ snn_status snn_ragged_remove_row(snn_ragged* r, const int32_t* targets, snn_rewi
  *    (1 = leftover activations, 2 = invalid state); NULL discards them.
  *  - The first call on a device looks up the scratch's device address (once per
  *    device, with that device current); make that first call before any stream capture.
+ *    The address is kept for the life of the process: after cudaDeviceReset (or any
+ *    teardown of the device's primary context) this entry point must not be called
+ *    again on that device in the same process.
+ *  - desc->reserved must be 0, as for snn_create_ragged.
  *  - Every call shares the one scratch array and leaves its contents behind; the
  *    kernels re-initialise what they read.  Calls that overlap on the GPU (different
  *    streams, or different host threads, without ordering between them) race on it and

@@ -177,6 +177,9 @@ __device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
 
 __host__ __device__ __forceinline__ int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
 
+// Multiprocessor count of the current device (cached per device ordinal; 152 on GB300).
+int sm_count();
+
 }  // namespace snn
 
 // ------------------------------------------------------------------ handles

@@ -543,12 +543,16 @@ static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* d
                                     uint64_t rewire, const long long* ridx_dev, snn_rewire_stats* stats,
                                     cudaStream_t s, const GuideK* guide = nullptr, uint32_t* tag = nullptr) {
     const int blocks = ceil_div((long long)d.P * 32, DEEPR_THREADS);
+    // every size check before the first launch: a refused call leaves the matrix untouched
+    const size_t smem = (size_t)(DEEPR_THREADS / 32) * ((Qw + 31) / 32 + 1) * sizeof(int32_t);
+    SNN_REQUIRE(guide || smem <= 48 * 1024, "snn_rewire_deepr: Q = %d too large for the formation chunk table",
+                d.Q);
     SNN_CUDA(cudaMemsetAsync(dsum, 0, 2 * sizeof(unsigned long long), s));
     k_deepr_eliminate<real><<<blocks, DEEPR_THREADS, 0, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
                                                               d.sign_bits, d.conn_bits, tag, dormant, cnt, dsum, d.P,
                                                               d.C, Qw);
     SNN_LAUNCH_CHECK();
-    k_deepr_round0<<<2 * 152, 256, 0, s>>>(dsum, cnt, d.P, d.seed, rewire, ridx_dev);
+    k_deepr_round0<<<2 * sm_count(), 256, 0, s>>>(dsum, cnt, d.P, d.seed, rewire, ridx_dev);
     SNN_LAUNCH_CHECK();
     k_deepr_accept0<<<ceil_div(d.P, 256), 256, 0, s>>>(d.row_len, cnt, room, taken, dsum + 1, d.P, d.C, d.Q,
                                                        d.no_autapse);
@@ -563,8 +567,6 @@ static snn_status rewire_launch_all(const snn_ragged_desc& d, int Qw, int32_t* d
         SNN_LAUNCH_CHECK();
         return SNN_OK;
     }
-    const size_t smem = (size_t)(DEEPR_THREADS / 32) * ((Qw + 31) / 32 + 1) * sizeof(int32_t);
-    SNN_REQUIRE(smem <= 48 * 1024, "snn_rewire_deepr: Q = %d too large for the formation chunk table", d.Q);
     k_deepr_form<real><<<blocks, DEEPR_THREADS, smem, s>>>(d.row_len, d.ind, (real*)d.w, (real*)d.m, (real*)d.v,
                                                             d.conn_bits, taken, d.P, d.C, d.Q, Qw, d.no_autapse,
                                                             d.seed, rewire, ridx_dev, status, stats);
@@ -648,6 +650,7 @@ extern "C" snn_status snn_rewire_deepr_noalloc(const snn_ragged_desc* d, int64_t
                 d->P, NOALLOC_MAX_ROWS);
     SNN_REQUIRE((long long)d->P * d->C < (1ll << 31), "snn_rewire_deepr_noalloc: P*C must be < 2^31");
     SNN_REQUIRE(d->dtype == SNN_F32 || d->dtype == SNN_F64, "snn_rewire_deepr_noalloc: bad dtype");
+    SNN_REQUIRE(d->reserved == 0, "snn_rewire_deepr_noalloc: reserved must be 0");
     SNN_REQUIRE(d->row_len && d->ind && d->w && d->m && d->v && d->sign_bits && d->conn_bits,
                 "snn_rewire_deepr_noalloc: needs row_len, ind, w, m, v, sign_bits and conn_bits");
     int32_t* scratch = nullptr;

@@ -19,6 +19,18 @@ void set_error(const char* fmt, ...) {
 }
 void clear_error() { g_last_error.clear(); }
 
+int sm_count() {
+    static int cached[256] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 152;
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
 // ------------------------------------------------------------------ validation
 // One warp per row: row length range, target range, self targets, duplicate targets.
 __global__ void k_validate(const int32_t* __restrict__ row_len, const int32_t* __restrict__ ind, int P, int Q,

@@ -280,3 +280,24 @@ def test_rewire_bit_exact_wide_rows(no_aut):
         assert out["formed"] > 0
         _compare(d, out, stats)
         rl, ind, w, conn = out["row_len"], out["ind"], out["w"], out["conn"]
+
+
+def test_refused_rewire_leaves_matrix_untouched():
+    """A rewiring whose formation table would not fit (Q > ~1.57 M targets) is refused
+    with SNN_EINVAL before any kernel runs: row lengths, targets and bitfields stay as
+    they were, so the synapse count is not left pruned without regrowth."""
+    from paper_2510_19764_gb300 import abi, net
+    P, Q, C = 2, 1_700_000, 4
+    ind = np.array([[5, 1_600_000, -1, -1], [7, 9, 11, -1]], dtype=np.int32)
+    row_len = np.array([2, 3], dtype=np.int32)
+    w = np.array([[0.5, -0.25, 0, 0], [0.1, 0.2, -0.3, 0]])
+    d = net.DeviceRagged(row_len, ind, w, Q, adam=True, deepr=True, seed=3)
+    d.w.neg_()                                     # every synapse now opposes its sign bit
+    before = {k: getattr(d, k).clone() for k in ("row_len", "ind", "w", "conn_bits")}
+    with pytest.raises(abi.SnnError) as e:
+        abi.snn_rewire_deepr(d.handle, 0, _stats())
+    assert e.value.status == abi.SNN_EINVAL
+    torch.cuda.synchronize()
+    for k, t in before.items():
+        assert torch.equal(getattr(d, k), t), k
+    assert d.status() == abi.SNN_OK

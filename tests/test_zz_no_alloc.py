@@ -65,3 +65,9 @@ def test_noalloc_rejects_too_many_rows():
         abi.snn_rewire_deepr_noalloc(desc, 0)
     assert e.value.status == abi.SNN_EINVAL
     assert "16384" in abi.snn_last_error()
+    # a descriptor the handle API refuses (reserved != 0) is refused here too
+    desc.P, desc.reserved = 8, 1
+    with pytest.raises(abi.SnnError) as e:
+        abi.snn_rewire_deepr_noalloc(desc, 0)
+    assert e.value.status == abi.SNN_EINVAL
+    assert "reserved" in abi.snn_last_error()
