@@ -39,7 +39,13 @@ Pins (tests/test_oracle_topo.py): exponential Euler = analytic solution for cons
 g; refractory hold; STDP pair rule for a single pre/post pair at lag Delta; Fig. 3's
 worked example with scripted draws (compared as row sets); formation rate on empty
 rows = (1/Q) p_form sum_j exp(-d^2/2 sigma^2) (binomial bound); all-depressed rows
-lose every selected synapse; Poisson counts binomial; focus uniform.
+lose every selected synapse; Poisson counts binomial; focus uniform.  The composition
+of step() on scripted two- to four-neuron networks: a source spike reaches g one step
+later (Tab. 2 delay t_d = h) after that step's decay; V then follows the numerically
+integrated membrane equation for that g; a same-step pre/post pair is potentiated by
+A+ (no depression), a later pre spike depressed by A- y with y decayed in between;
+propagation uses the weights STDP left; rewiring follows STDP after steps with
+(t + 1) % rewire_every == 0 only.
 """
 from __future__ import annotations
 
@@ -364,11 +370,12 @@ def initial_state(ff, lat, p: TopoParams) -> TopoState:
                      np.zeros(N, dtype=bool), np.zeros(N, dtype=bool))
 
 
-def step(st: TopoState, t: int, p: TopoParams, seeds: dict, C: int) -> dict:
+def step(st: TopoState, t: int, p: TopoParams, seeds: dict, C: int, inputs=None) -> dict:
     """Advance the topographic network by one step (in place).  seeds: {"input",
-    "ff", "lat"}.  Returns the step's spikes and rewiring stats."""
+    "ff", "lat"}.  inputs (tests): the source spikes of step t, instead of the Poisson
+    draw.  Returns the step's spikes and rewiring stats."""
     N = p.N
-    s = input_spikes(seeds["input"], t, p)
+    s = input_spikes(seeds["input"], t, p) if inputs is None else np.asarray(inputs, dtype=bool)
     I = propagate_rows(st.ff, st.s_prev, N)
     I += propagate_rows(st.lat, st.z_prev, N)
     st.V, st.gs, st.ref, z = neuron_step(st.V, st.gs, st.ref, I, p)

@@ -227,6 +227,24 @@ def test_adam_equals_torch():
     np.testing.assert_allclose(ow, w.detach().numpy(), rtol=1e-12, atol=1e-15)
 
 
+def test_adam_ragged_leaves_padding_untouched():
+    """Only the synapses s < row_len take the Adam step (the padding slots are room for
+    growth, Fig. 1): padding w, m, v come back bit for bit, live slots equal the dense
+    Adam step (torch.optim.Adam is pinned separately)."""
+    rng = np.random.default_rng(4)
+    P, C = 6, 5
+    row_len = np.array([0, 1, 5, 3, 2, 4], np.int32)
+    w, m, v = rng.normal(size=(P, C)), rng.normal(size=(P, C)), rng.random((P, C))
+    g = rng.normal(size=(P, C))
+    w2, m2, v2 = oc.adam_ragged(w, m, v, g, row_len, 1e-3, 0.9 ** 3, 0.999 ** 3)
+    wd, md, vd = oc.adam(w, m, v, g, 1e-3, 0.9 ** 3, 0.999 ** 3)
+    live = np.arange(C)[None] < row_len[:, None]
+    for got, dense, before in ((w2, wd, w), (m2, md, m), (v2, vd, v)):
+        np.testing.assert_array_equal(got[~live], before[~live])
+        np.testing.assert_array_equal(got[live], dense[live])
+        assert not np.array_equal(dense[~live], before[~live])   # the dense step would have moved them
+
+
 def test_l1_on_sign_by_hand():
     G = np.array([[1.0, 2.0, 9.0], [0.5, 7.0, 7.0]])
     row_len = np.array([2, 1])

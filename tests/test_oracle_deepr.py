@@ -34,6 +34,39 @@ def test_init_bitfields():
     assert 0.45 < frac < 0.55
 
 
+def test_init_bitfields_zero_weight_keeps_the_drawn_sign():
+    """Fig. 2A: a synapse of weight exactly 0 has no sign to impose, so its potential
+    connection keeps the randomly drawn sign bit (the same bit a matrix without that
+    synapse draws: Philox SIGN, counter (row, word), low 32 bits of word 0; the
+    generator itself is pinned against numpy's Philox4x64); w > 0 sets the bit, w < 0
+    clears it, and all three get their connectivity bit."""
+    P, Q, C, seed = 3, 64, 3, 9
+    row_len = np.array([3, 3, 0], np.int32)
+    ind = np.array([[1, 33, 40], [2, 5, 63], [-1, -1, -1]], np.int32)
+    w = np.array([[0.0, 0.5, -0.5], [-0.0, 0.0, 0.0], [0, 0, 0]])
+    sign, conn = deepr.init_bitfields(row_len, ind, w, Q, seed)
+    empty, conn0 = deepr.init_bitfields(np.zeros(P, np.int32), ind, w, Q, seed)
+    assert not conn0.any()
+    for i in range(P):
+        for wd in range(2):
+            assert int(empty[i, wd]) == int(deepr.philox.draw(seed, deepr.philox.SIGN, np.uint64(i), np.uint64(wd),
+                                                              0, 0, word=0)) & 0xFFFFFFFF
+    for i, s in ((0, 0), (1, 0), (1, 1), (1, 2)):         # w == 0 (and -0.0): drawn bit kept
+        assert _bit(sign, i, ind[i, s]) == _bit(empty, i, ind[i, s])
+    assert _bit(sign, 0, 33) == 1 and _bit(sign, 0, 40) == 0
+    np.testing.assert_array_equal(conn, _bits_of_rows(row_len, ind, P, Q))
+    # bits of targets without a synapse are the drawn ones
+    untouched = np.ones((P, 2), np.uint32) * np.uint32(0xFFFFFFFF)
+    for i in range(P):
+        for s in range(row_len[i]):
+            untouched[i, ind[i, s] >> 5] &= np.uint32(~(1 << (int(ind[i, s]) & 31)) & 0xFFFFFFFF)
+    np.testing.assert_array_equal(sign & untouched, empty & untouched)
+    # both sign values occur among the w == 0 synapses' drawn bits for some seed: the
+    # test above is not passing on an all-ones or all-zeros draw
+    bits = {_bit(deepr.init_bitfields(row_len, ind, w, Q, sd)[0], 1, 2) for sd in range(16)}
+    assert bits == {0, 1}
+
+
 def test_fig2_shaped_scripted_example():
     """5 pre x 4 post, max out-degree 3 (Fig. 2).  Rows and sign bits are scripted;
     weights whose sign disagrees with the sign bit are removed, survivors keep order."""

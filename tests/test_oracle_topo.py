@@ -351,3 +351,138 @@ def test_gaussian_input_rates_follow_the_profile():
         assert abs(cnt[m].sum() - n * prob) < 5 * math.sqrt(n * prob * (1 - prob)) + 1, shell
     # the profile's threshold at the focus in closed form
     assert philox.threshold((5.0 + 152.8) * 0.1 * 1e-3) == int((5.0 + 152.8) * 0.1 * 1e-3 * 2.0 ** 64)
+
+
+# --------------------------------------------------------- composition of one step
+#
+# Tab. 2 fixes the synaptic delay t_d at one time step h, the exponential synapse
+# (g decays with tau_s, each spike adds its weight) and the rewiring period; Tab. 1
+# fixes the pair-based STDP rule.  These scripted networks pin how topo.step() puts
+# the parts together: a source spike of step t reaches the conductance at step t + 1,
+# after that step's decay; the membrane then integrates the new conductance; STDP runs
+# after the neuron update with the depression seeing y before the step's post spikes
+# and the potentiation seeing x after the step's pre spikes; propagation at t + 1 uses
+# the weights STDP left at t; rewiring follows STDP after steps with
+# (t + 1) % rewire_every == 0.  A zero-delay, jump-before-decay, swapped-STDP or
+# off-by-one-cadence version of step() fails one of them.
+
+def _scripted(L, C, syn, **kw):
+    """Topographic state with feed-forward synapses `syn` = [(i, j, w), ...], no lateral
+    ones, silent Poisson input (inputs are scripted per step)."""
+    p = topo.TopoParams(L=L, n_att=kw.pop("n_att", 0), f_base=0.0, f_in=0.0, **kw)
+    N = p.N
+    ff = [np.zeros(N, np.int32), np.full((N, C), -1, np.int32), np.zeros((N, C))]
+    for i, j, w in syn:
+        s = int(ff[0][i])
+        ff[1][i, s], ff[2][i, s] = j, w
+        ff[0][i] = s + 1
+    lat = [np.zeros(N, np.int32), np.full((N, C), -1, np.int32), np.zeros((N, C))]
+    return p, topo.initial_state(ff, lat, p)
+
+
+def _run(st, p, C, script, t_end):
+    """Steps 0 .. t_end - 1; script[t] = source neurons spiking at step t.  Returns the
+    state arrays recorded after every step."""
+    rec = []
+    for t in range(t_end):
+        s = np.zeros(p.N, bool)
+        s[list(script.get(t, ()))] = True
+        out = topo.step(st, t, p, {"input": 1, "ff": 2, "lat": 3}, C, inputs=s)
+        rec.append({"gs": st.gs.copy(), "V": st.V.copy(), "z": out["z"].copy(), "w": st.ff[2].copy(),
+                    "x": st.x_src.copy(), "y": st.y.copy(), "rewired": "ff" in out, "out": out})
+    return rec
+
+
+def _cond_lif_exact(V0, g, p, dt):
+    """Membrane equation tau_m dV/dt = (V_rest - V) + g/g_leak (E_exc - V) with g held
+    over the step, integrated numerically (an independent check of the closed form)."""
+    from scipy.integrate import solve_ivp
+    f = lambda _t, V: [((p.V_rest - V[0]) + g / p.g_leak * (p.E_exc - V[0])) / p.tau_m]  # noqa: E731
+    return solve_ivp(f, (0.0, dt), [V0], rtol=1e-12, atol=1e-12, method="DOP853").y[0, -1]
+
+
+def test_source_spike_reaches_the_conductance_one_step_later_after_the_decay():
+    w = 0.05
+    p, st = _scripted(2, 4, [(0, 1, w)])
+    rec = _run(st, p, 4, {3: [0]}, 7)
+    for t in range(4):
+        assert rec[t]["gs"][1] == 0.0, t                   # nothing before the delay has passed
+        assert rec[t]["V"][1] == p.V_rest, t
+    assert rec[4]["gs"][1] == w                            # 0 * decay + w: decay first, then the jump
+    assert rec[5]["gs"][1] == pytest.approx(w * math.exp(-p.dt / p.tau_s), rel=1e-15)
+    assert rec[6]["gs"][1] == pytest.approx(w * math.exp(-2 * p.dt / p.tau_s), rel=1e-15)
+    assert np.all(rec[6]["gs"][[0, 2, 3]] == 0.0)          # only the target receives it
+
+
+def test_membrane_integrates_the_conductance_of_its_own_step():
+    w = 0.05
+    p, st = _scripted(2, 4, [(0, 1, w)])
+    rec = _run(st, p, 4, {3: [0]}, 6)
+    V4 = _cond_lif_exact(p.V_rest, w, p, p.dt)
+    assert rec[4]["V"][1] == pytest.approx(V4, abs=1e-9)
+    assert rec[4]["V"][1] > p.V_rest + 1e-3                # the jump of step 4 is already felt
+    V5 = _cond_lif_exact(rec[4]["V"][1], w * math.exp(-p.dt / p.tau_s), p, p.dt)
+    assert rec[5]["V"][1] == pytest.approx(V5, abs=1e-9)
+    assert rec[5]["V"][0] == p.V_rest
+
+
+def test_stdp_within_a_step_and_propagation_of_the_updated_weight():
+    """Source 0 drives target 1 over threshold (its spike of step 3 arrives at step 4);
+    source 2 fires at step 4 too, so synapse 2 -> 1 sees a pre and a post spike in the
+    same step: no depression (y before the post spike is 0), potentiation by A+ x with
+    x = 1 (this step's pre spike counted).  Source 2 fires again at step 7: depression
+    by A- y with y decayed over three steps.  Its spike of step 4 arrives at step 5 with
+    the weight STDP left at step 4."""
+    w_drive, w0 = 50.0, 0.05
+    p, st = _scripted(2, 4, [(0, 1, w_drive), (2, 1, w0)])
+    rec = _run(st, p, 4, {3: [0], 4: [2], 7: [2]}, 8)
+    assert not rec[3]["z"].any() and rec[4]["z"][1] and rec[4]["z"].sum() == 1
+    assert rec[4]["x"][2] == 1.0 and rec[4]["y"][1] == 1.0
+    w_after4 = w0 + p.A_plus * 1.0
+    assert rec[4]["w"][2, 0] == pytest.approx(w_after4, rel=1e-15)
+    assert rec[4]["w"][0, 0] == p.g_max                    # 50 + A+ e^{-1/20} clamped
+    assert rec[5]["gs"][1] == pytest.approx(w_drive * math.exp(-p.dt / p.tau_s) + w_after4, rel=1e-15)
+    for t in (5, 6):
+        assert rec[t]["w"][2, 0] == pytest.approx(w_after4, rel=1e-15)
+    assert not rec[5]["z"].any() and not rec[6]["z"].any() and not rec[7]["z"].any()   # refractory
+    y7 = math.exp(-3 * p.dt / p.tau_minus)
+    assert rec[7]["w"][2, 0] == pytest.approx(w_after4 - p.A_minus * y7, rel=1e-14)
+
+
+def test_rewiring_runs_after_steps_with_t_plus_1_multiple_of_the_period_after_stdp():
+    """4 x 4 sheets, every target a candidate of every row (2000 attempts).  The
+    network is silent except for a scripted pair that potentiates synapse 5 -> 6 from
+    below g_theta to above it in step 9 itself: rewiring after STDP sees it potentiated
+    and (with this seed's draw) keeps it, where a depressed synapse is always removed
+    (p_elim_dep clamps to 1).  Rewiring happens after steps 9 and 19 only, with rewire
+    indices 0 and 1."""
+    L, C = 4, 16
+    g_theta = 0.5 * 0.2
+    w56 = g_theta - 0.01
+    p, st = _scripted(L, C, [(0, 6, 50.0), (5, 6, w56), (3, 9, 0.15)], n_att=2000)
+    assert p.rewire_every == 10
+    seed_ff = 2
+    R = philox.draw(seed_ff, philox.TOPO_DRAW, np.uint64(0), np.uint64(5), np.uint64(6), 0, word=0)
+    assert int(R) >= philox.threshold(p.p_elim_pot)        # kept if potentiated
+    rec = _run(st, p, C, {7: [5], 8: [0]}, 20)
+    assert [t for t in range(20) if rec[t]["rewired"]] == [9, 19]
+    assert rec[9]["z"][6]                                   # post spike of step 9
+    assert rec[8]["w"][5, 0] == w56
+    # the rewiring of step 9 starts from the state after step 9's STDP
+    pre = rec[9]["out"]["ff"]
+    assert 6 in set(pre["ind"][5, :pre["row_len"][5]].tolist())
+    # the same call on the pre-STDP weights (a rewiring placed before STDP) removes it
+    w_pre = rec[8]["w"].copy()
+    ff_len = np.array([1 if i in (0, 5, 3) else 0 for i in range(p.N)], np.int32)
+    ind0 = np.full((p.N, C), -1, np.int32)
+    ind0[0, 0], ind0[5, 0], ind0[3, 0] = 6, 6, 9
+    early = topo.rewire(ff_len, ind0, w_pre, C, p.N, L, seed_ff, 0, p.n_att, philox.threshold(p.p_elim_dep),
+                        philox.threshold(p.p_elim_pot), p.g_theta, topo.form_thresholds(p.p_form_ff, p.sigma_ff, L),
+                        p.g_max)
+    assert 6 not in set(early["ind"][5, :early["row_len"][5]].tolist())
+    # index 1 at step 19: the draws of rewire index 1 (attempt histogram) were used
+    att1 = np.bincount(philox.mulhi(philox.draw(seed_ff, philox.TOPO_ATT, np.uint64(1),
+                                                np.arange(p.n_att, dtype=np.uint64) // np.uint64(4), 0, 0,
+                                                word=(np.arange(p.n_att) % 4).astype(np.int64)), p.N).astype(np.int64),
+                       minlength=p.N)
+    np.testing.assert_array_equal(rec[19]["out"]["ff"]["attempts"], np.minimum(att1, p.N))
