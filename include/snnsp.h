@@ -60,7 +60,7 @@ typedef void* snn_stream;        /* cudaStream_t */
 /* Message for the most recent failing call on this host thread ("" if none). */
 const char* snn_last_error(void);
 /* ABI version of this header (bumped on any incompatible change). */
-int32_t snn_abi_version(void);   /* 6 */
+int32_t snn_abi_version(void);   /* 7 */
 
 /* ==================================================================================
  * Ragged sparse matrix (Sec. 2.1, Fig. 1; DEEP R bitfields Sec. 2.1.2, Fig. 2)
@@ -270,13 +270,18 @@ typedef struct {
                                   forward only: trials stop at their own length */
 } snn_batch;
 
+/* Adam (Kingma & Ba; the optimiser of Sec. 3.1) with bias corrections 1 - beta1^t,
+ * 1 - beta2^t.  The library forms beta^t itself, as a running product (beta^t = beta^(t-1)
+ * x beta, starting from beta^0 = 1, in double precision: snn_adam_bias gives the values
+ * it uses); the caller passes the step count t only. */
 typedef struct {
     double lr, beta1, beta2, eps;
-    double b1t, b2t;          /* beta1^t, beta2^t of this step (running products) */
+    int64_t step;             /* t >= 1: this is the t-th Adam step */
+    const int64_t* step_dev;  /* optional device int64 holding t, read when the kernels run
+                                 (lets a captured CUDA graph advance the step count on the
+                                 device; the running products then live in the classifier
+                                 handle's device scratch); NULL: use step */
     double l1;                /* DEEP R L1 strength (0: off); needs sign_bits */
-    const double* bias_dev;   /* optional device {beta1^t, beta2^t}: read by the kernels
-                                 instead of b1t, b2t (lets a captured CUDA graph advance
-                                 the step count on the device); NULL: use b1t, b2t */
     /* DEEP R noise term (Bellec et al. 2018; Sec. 2.1.2 notes that the paper leaves it
      * out, as Bellec et al. 2020 did): temperature > 0 adds sqrt(2 lr temperature) nu to
      * every active ragged weight after its Adam step (not to the dense readout), with
@@ -293,6 +298,11 @@ typedef struct {
 
 #define SNN_EPROP_GRAD  0
 #define SNN_EPROP_APPLY 1
+
+/* beta1^t and beta2^t exactly as the Adam step of snn_eprop_update forms them (running
+ * products in double precision); out: host double[2].  Host only: needs no GPU.
+ * SNN_EINVAL if step < 0 or a beta is outside [0, 1). */
+snn_status snn_adam_bias(double beta1, double beta2, int64_t step, double* out);
 
 /* Create a classifier handle; validates sizes (0 < K <= 32, N <= 2048, n_in <= 1024,
  * row capacities <= 2048) and allocates fixed scratch: the e-prop gradient partial sums
@@ -360,12 +370,16 @@ typedef struct {
     int32_t L_f;          /* stimulus tile side (L for a single focus) */
     int32_t radius2;      /* squared focus radius (sites^2) */
     int32_t t_stim;       /* steps between focus re-draws */
-    int32_t n_ref;        /* refractory steps */
-    int32_t reserved;
     double dt, tau_m, V_rest, E_exc, V_theta, V_reset, tau_s, g_leak;
+    double tau_ref;       /* absolute refractory period (ms, Tab. 2D): V is held at V_reset
+                             for round(tau_ref / dt) steps after a spike */
     double f_base, f_in;             /* Hz outside / inside the focus (disc profile); with
                                         sigma_stim > 0: base and peak rate */
-    double g_max, tau_plus, tau_minus, A_plus, A_minus;
+    double g_max, tau_plus, tau_minus;
+    /* STDP rates as Tab. 2F defines them: A_+ = A_plus_rel g_max (A_plus_rel = 0.1 in the
+     * paper) and A_- = B A_+ tau_+ / tau_- (B = 1.2, the ratio of potentiation to
+     * depression); the library derives A_+ and A_- (snn_topo_derive shows the values). */
+    double A_plus_rel, B;
     /* Input profile.  sigma_stim = 0: disc, channel rate f_in within squared torus
      * distance radius2 of its tile's focus, f_base outside.  sigma_stim > 0: the Gaussian
      * of Tab. 1 "Input", rate f_base + f_in exp(-d^2 / (2 sigma_stim^2)) (f_in is f_peak).
@@ -378,10 +392,23 @@ typedef struct {
     double sigma_stim;
 } snn_topo_params;
 
+/* The quantities the library derives from snn_topo_params (Tab. 2D, 2F). */
+typedef struct {
+    int32_t n_ref;        /* refractory steps: round(tau_ref / dt) */
+    int32_t reserved;
+    double A_plus;        /* A_plus_rel g_max */
+    double A_minus;       /* B A_plus tau_plus / tau_minus */
+} snn_topo_derived;
+/* Fills *out with the values every topographic call uses for p (host only: needs no
+ * GPU).  SNN_EINVAL for parameters the calls refuse. */
+snn_status snn_topo_derive(const snn_topo_params* p, snn_topo_derived* out);
+
 typedef struct {
     double p_form, sigma;            /* Gaussian formation probability */
     double p_elim_dep, p_elim_pot;   /* elimination probabilities (clamped to [0,1]) */
-    double g_theta, g_new;           /* depression threshold, weight of new synapses */
+    double g_max;                    /* maximum conductance (Tab. 2F, 2G): a new synapse
+                                        starts at g_max, and a synapse is depressed (uses
+                                        p_elim_dep) iff g < g_theta = g_max / 2 */
     int32_t L;                       /* torus side used for distances */
     int32_t n_att;                   /* attempts per call */
     /* Optional event histograms for the connectivity-evolution analysis of Sec. 3.2

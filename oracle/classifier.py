@@ -251,6 +251,15 @@ def l1_on_sign(G: np.ndarray, row_len: np.ndarray, ind: np.ndarray, sign_bits: n
     return out
 
 
+def adam_bias(beta: float, t: int) -> float:
+    """beta^t as a running product (beta^0 = 1, then one multiplication per step): the
+    form the bias correction 1 - beta^t of Adam takes when it is tracked step by step."""
+    b = 1.0
+    for _ in range(t):
+        b *= beta
+    return b
+
+
 def adam(w, m, v, g, lr: float, b1t: float, b2t: float, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam step (Kingma & Ba, Algorithm 1); b1t, b2t are beta1^t, beta2^t."""
     m = beta1 * m + (1.0 - beta1) * g

@@ -26,7 +26,7 @@ EXPORTED = [
     "snn_eprop_update", "snn_topo_input", "snn_topo_neurons", "snn_stdp_update", "snn_rewire_topo", "snn_topo_run",
     "snn_philox", "snn_rewire_deepr_noalloc", "snn_classifier_set_schedule", "snn_rewire_deepr_dev",
     "snn_draw_inputs", "snn_step_neurons_ex", "snn_topo_connectivity", "snn_ragged_set_deepr_guide",
-    "snn_test_wait_timeout", "snn_ragged_add_row", "snn_ragged_remove_row",
+    "snn_test_wait_timeout", "snn_ragged_add_row", "snn_ragged_remove_row", "snn_adam_bias", "snn_topo_derive",
 ]
 
 
@@ -69,8 +69,8 @@ class Batch(C.Structure):
 
 
 class Adam(C.Structure):
-    _fields_ = [("lr", f64), ("beta1", f64), ("beta2", f64), ("eps", f64), ("b1t", f64), ("b2t", f64), ("l1", f64),
-                ("bias_dev", vp), ("temperature", f64), ("noise_idx", i64), ("noise_idx_dev", vp)]
+    _fields_ = [("lr", f64), ("beta1", f64), ("beta2", f64), ("eps", f64), ("step", i64), ("step_dev", vp),
+                ("l1", f64), ("temperature", f64), ("noise_idx", i64), ("noise_idx_dev", vp)]
 
 
 class DeeprGuide(C.Structure):
@@ -78,15 +78,19 @@ class DeeprGuide(C.Structure):
 
 
 class TopoParams(C.Structure):
-    _fields_ = [("L", i32), ("L_f", i32), ("radius2", i32), ("t_stim", i32), ("n_ref", i32), ("reserved", i32),
+    _fields_ = [("L", i32), ("L_f", i32), ("radius2", i32), ("t_stim", i32),
                 ("dt", f64), ("tau_m", f64), ("V_rest", f64), ("E_exc", f64), ("V_theta", f64), ("V_reset", f64),
-                ("tau_s", f64), ("g_leak", f64), ("f_base", f64), ("f_in", f64), ("g_max", f64), ("tau_plus", f64),
-                ("tau_minus", f64), ("A_plus", f64), ("A_minus", f64), ("sigma_stim", f64)]
+                ("tau_s", f64), ("g_leak", f64), ("tau_ref", f64), ("f_base", f64), ("f_in", f64), ("g_max", f64),
+                ("tau_plus", f64), ("tau_minus", f64), ("A_plus_rel", f64), ("B", f64), ("sigma_stim", f64)]
+
+
+class TopoDerived(C.Structure):
+    _fields_ = [("n_ref", i32), ("reserved", i32), ("A_plus", f64), ("A_minus", f64)]
 
 
 class TopoRewire(C.Structure):
-    _fields_ = [("p_form", f64), ("sigma", f64), ("p_elim_dep", f64), ("p_elim_pot", f64), ("g_theta", f64),
-                ("g_new", f64), ("L", i32), ("n_att", i32), ("elim_d2", vp), ("form_d2", vp)]
+    _fields_ = [("p_form", f64), ("sigma", f64), ("p_elim_dep", f64), ("p_elim_pot", f64), ("g_max", f64),
+                ("L", i32), ("n_att", i32), ("elim_d2", vp), ("form_d2", vp)]
 
 
 class TopoState(C.Structure):
@@ -136,6 +140,8 @@ def load() -> C.CDLL:
         "snn_test_wait_timeout": (i32, [vp, i32, i32, vp]),
         "snn_ragged_add_row": (i32, [vp, vp, vp, vp, vp]),
         "snn_ragged_remove_row": (i32, [vp, vp, vp, vp]),
+        "snn_adam_bias": (i32, [f64, f64, i64, P(f64)]),
+        "snn_topo_derive": (i32, [P(TopoParams), P(TopoDerived)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -280,3 +286,15 @@ def snn_topo_connectivity(h: int, L: int, disp_count=None, disp_wsum=None, in_de
 
 def snn_philox(seed: int, purpose: int, ctr, n: int, out, stream=None) -> None:
     check(load().snn_philox(seed, purpose, ptr(ctr), n, ptr(out), stream_ptr(stream)))
+
+
+def snn_adam_bias(beta1: float, beta2: float, step: int) -> tuple[float, float]:
+    out = (f64 * 2)()
+    check(load().snn_adam_bias(beta1, beta2, step, out))
+    return out[0], out[1]
+
+
+def snn_topo_derive(p: TopoParams) -> TopoDerived:
+    out = TopoDerived()
+    check(load().snn_topo_derive(C.byref(p), C.byref(out)))
+    return out

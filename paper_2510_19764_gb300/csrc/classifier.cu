@@ -719,6 +719,39 @@ __device__ __forceinline__ double deepr_noise(uint64_t seed, uint64_t noise_idx,
     return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
+// beta1^t, beta2^t for a step count read from device memory, kept in the handle's device
+// state: one multiplication per call when t advances by one (graph replay), a fresh
+// running product otherwise.  At most 2^24 multiplications per call: a larger jump sets
+// the invalid-state flag and keeps the partial product (a later call continues it).
+__global__ void k_adam_bias(const long long* __restrict__ step_dev, double beta1, double beta2, AdamBias* st,
+                            int32_t* status) {
+    long long t = *step_dev;
+    if (t < 1) {
+        atomicOr(status, ST_STATE);
+        t = 1;
+    }
+    if (st->t == t && st->beta1 == beta1 && st->beta2 == beta2) return;
+    double b1 = 1.0, b2 = 1.0;
+    long long t0 = 0;
+    if (st->beta1 == beta1 && st->beta2 == beta2 && st->t >= 0 && st->t < t) {
+        b1 = st->b1t;
+        b2 = st->b2t;
+        t0 = st->t;
+    }
+    const long long lim = 1ll << 24;
+    adam_bias_advance(beta1, beta2, t0, b1, b2, t, lim);
+    long long reached = t;
+    if (t - t0 > lim && (b1 != 0.0 || b2 != 0.0)) {
+        atomicOr(status, ST_STATE);
+        reached = t0 + lim;
+    }
+    st->b1t = b1;
+    st->b2t = b2;
+    st->beta1 = beta1;
+    st->beta2 = beta2;
+    st->t = reached;
+}
+
 struct NoiseK {
     double amp;                    // sqrt(2 lr temperature); 0 = off
     uint64_t seed, idx;
@@ -1246,11 +1279,35 @@ static snn_status grad_impl(snn_classifier* c, const snn_batch* bt, cudaStream_t
     return SNN_OK;
 }
 
+// beta1^t, beta2^t on the host, continued from the handle's cache when it matches.
+static void host_adam_bias(snn_classifier* c, double beta1, double beta2, long long t, double& b1t, double& b2t) {
+    if (!(c->h_beta1 == beta1 && c->h_beta2 == beta2 && c->h_t >= 0 && c->h_t <= t)) {
+        c->h_b1t = c->h_b2t = 1.0;
+        c->h_t = 0;
+        c->h_beta1 = beta1;
+        c->h_beta2 = beta2;
+    }
+    adam_bias_advance(beta1, beta2, c->h_t, c->h_b1t, c->h_b2t, t, 1ll << 62);
+    c->h_t = t;
+    b1t = c->h_b1t;
+    b2t = c->h_b2t;
+}
+
 template <typename real>
 static snn_status apply_impl(snn_classifier* c, const snn_adam* ad, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
     const real lr = (real)ad->lr, b1 = (real)ad->beta1, b2 = (real)ad->beta2, eps = (real)ad->eps;
-    const real bc1 = (real)(1.0 - ad->b1t), bc2 = (real)(1.0 - ad->b2t);
+    double b1t = 1.0, b2t = 1.0;
+    const double* bias_dev = nullptr;
+    if (ad->step_dev) {
+        k_adam_bias<<<1, 1, 0, s>>>((const long long*)ad->step_dev, ad->beta1, ad->beta2, (AdamBias*)c->adam_dev,
+                                    d.w_in->status);
+        SNN_LAUNCH_CHECK();
+        bias_dev = (const double*)c->adam_dev;          // {beta1^t, beta2^t} at its start
+    } else {
+        host_adam_bias(c, ad->beta1, ad->beta2, ad->step, b1t, b2t);
+    }
+    const real bc1 = (real)(1.0 - b1t), bc2 = (real)(1.0 - b2t);
     const real omb1 = (real)(1.0 - ad->beta1), omb2 = (real)(1.0 - ad->beta2);
     for (snn_ragged* r : {d.w_in, d.w_rec}) {
         const snn_ragged_desc& rd = r->d;
@@ -1262,15 +1319,15 @@ static snn_status apply_impl(snn_classifier* c, const snn_adam* ad, cudaStream_t
         nz.idx_dev = ad->noise_idx_dev;
         k_adam_ragged<real><<<ceil_div((long long)rd.P * rd.C, 256), 256, 0, s>>>(
             rd.row_len, rd.ind, rd.P, rd.C, r->Qw, (real*)rd.w, (real*)rd.m, (real*)rd.v, (const real*)rd.grad, sign,
-            (real)ad->l1, lr, b1, b2, omb1, omb2, eps, bc1, bc2, ad->bias_dev, nz);
+            (real)ad->l1, lr, b1, b2, omb1, omb2, eps, bc1, bc2, bias_dev, nz);
         SNN_LAUNCH_CHECK();
     }
     k_adam_dense<real><<<ceil_div(d.K * d.N, 256), 256, 0, s>>>((real*)d.W_out, (real*)d.W_out_m, (real*)d.W_out_v,
                                                                 (const real*)d.G_out, d.K * d.N, lr, b1, b2, omb1,
-                                                                omb2, eps, bc1, bc2, ad->bias_dev);
+                                                                omb2, eps, bc1, bc2, bias_dev);
     SNN_LAUNCH_CHECK();
     k_adam_dense<real><<<1, 32, 0, s>>>((real*)d.b_out, (real*)d.b_m, (real*)d.b_v, (const real*)d.G_b, d.K, lr, b1,
-                                        b2, omb1, omb2, eps, bc1, bc2, ad->bias_dev);
+                                        b2, omb1, omb2, eps, bc1, bc2, bias_dev);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -1324,6 +1381,14 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     if (e == cudaSuccess) e = cudaMalloc(&c->pk, (size_t)(d->n_in + d->N) * c->Cf * 8);
     if (e == cudaSuccess)
         e = cudaMalloc(&c->gkeys, ((size_t)d->w_in->d.P * d->w_in->d.C + (size_t)d->w_rec->d.P * d->w_rec->d.C) * 4);
+    c->h_b1t = c->h_b2t = 1.0;
+    c->h_beta1 = c->h_beta2 = -1.0;
+    c->h_t = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&c->adam_dev, sizeof(AdamBias));
+    if (e == cudaSuccess) {
+        const AdamBias init = {1.0, 1.0, -1.0, -1.0, 0, 0};
+        e = cudaMemcpy(c->adam_dev, &init, sizeof(AdamBias), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         snn_destroy_classifier(c);
         set_error("snn_create_classifier: cudaMalloc failed: %s", cudaGetErrorString(e));
@@ -1350,6 +1415,7 @@ snn_status snn_destroy_classifier(snn_classifier* c) {
     cudaFree(c->part_out);
     cudaFree(c->pk);
     cudaFree(c->gkeys);
+    cudaFree(c->adam_dev);
     free(c);
     return SNN_OK;
 }
@@ -1396,6 +1462,18 @@ snn_status snn_draw_inputs(snn_classifier* c, const snn_batch* b, int32_t t0, in
     return draw_impl(c, b, t0, n_steps, (cudaStream_t)stream);
 }
 
+snn_status snn_adam_bias(double beta1, double beta2, int64_t step, double* out) {
+    clear_error();
+    SNN_REQUIRE(out, "snn_adam_bias: NULL output");
+    SNN_REQUIRE(beta1 >= 0.0 && beta1 < 1.0 && beta2 >= 0.0 && beta2 < 1.0, "snn_adam_bias: betas must be in [0, 1)");
+    SNN_REQUIRE(step >= 0, "snn_adam_bias: step must be >= 0");
+    double b1 = 1.0, b2 = 1.0;
+    adam_bias_advance(beta1, beta2, 0, b1, b2, step, 1ll << 62);
+    out[0] = b1;
+    out[1] = b2;
+    return SNN_OK;
+}
+
 snn_status snn_test_wait_timeout(snn_ragged* r, int32_t arrive, int32_t limit, snn_stream stream) {
     clear_error();
     SNN_REQUIRE(r && limit > 0 && limit <= (1 << 24), "snn_test_wait_timeout: bad argument");
@@ -1423,8 +1501,9 @@ snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase
         for (snn_ragged* r : {c->d.w_in, c->d.w_rec})
             SNN_REQUIRE(r->d.m && r->d.v && r->d.grad, "snn_eprop_update: ragged m, v, grad required for APPLY");
         SNN_REQUIRE(c->d.W_out_m && c->d.W_out_v && c->d.b_m && c->d.b_v, "snn_eprop_update: readout moments missing");
-        SNN_REQUIRE(adam->bias_dev || (adam->b1t < 1.0 && adam->b2t < 1.0),
-                    "snn_eprop_update: b1t, b2t must be beta^t with t >= 1");
+        SNN_REQUIRE(adam->beta1 >= 0.0 && adam->beta1 < 1.0 && adam->beta2 >= 0.0 && adam->beta2 < 1.0,
+                    "snn_eprop_update: beta1, beta2 must be in [0, 1)");
+        SNN_REQUIRE(adam->step_dev || adam->step >= 1, "snn_eprop_update: the Adam step count must be >= 1");
         SNN_REQUIRE(adam->temperature >= 0.0 && (adam->temperature == 0.0 || adam->noise_idx >= 0),
                     "snn_eprop_update: temperature must be >= 0 (and noise_idx >= 0 when it is > 0)");
         return c->d.dtype == SNN_F32 ? apply_impl<float>(c, adam, s) : apply_impl<double>(c, adam, s);

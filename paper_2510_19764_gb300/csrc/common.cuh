@@ -180,6 +180,22 @@ __host__ __device__ __forceinline__ int ceil_div(long long a, int b) { return (i
 // Multiprocessor count of the current device (cached per device ordinal; 152 on GB300).
 int sm_count();
 
+// Adam's beta1^t, beta2^t as running products (beta^t = beta^(t-1) beta from beta^0 = 1),
+// advanced from (t0, b1, b2) to t; stops early once both products have underflowed to 0
+// (they stay 0).  Host and device run the same multiplications, so the values agree.
+struct AdamBias {
+    double b1t, b2t, beta1, beta2;
+    long long t;
+    long long pad;
+};
+__host__ __device__ __forceinline__ void adam_bias_advance(double beta1, double beta2, long long t0, double& b1,
+                                                           double& b2, long long t, long long max_iter) {
+    for (long long k = t0, it = 0; k < t && (b1 != 0.0 || b2 != 0.0) && it < max_iter; ++k, ++it) {
+        b1 *= beta1;
+        b2 *= beta2;
+    }
+}
+
 }  // namespace snn
 
 // ------------------------------------------------------------------ handles
@@ -221,4 +237,10 @@ struct snn_classifier {
     void* pk;                // [(n_in + N) * Cf] packed forward rows (refreshed per forward call)
     int32_t* gkeys;          // [P_in*C_in + N*C_rec] gather order: (target << 11) | slot, ascending per row
     int32_t Cf;              // slots per packed row: max(C_in, C_rec + K) rounded up to 32
+    // Adam bias corrections: running products beta^t.  Host copy for calls that pass the
+    // step count by value, device copy (snn::AdamBias) for calls that pass it in device
+    // memory; each remembers the t and betas it was formed for.
+    double h_b1t, h_b2t, h_beta1, h_beta2;
+    long long h_t;
+    void* adam_dev;
 };

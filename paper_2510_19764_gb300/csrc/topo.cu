@@ -24,12 +24,24 @@ struct TopoIn {
     int n;
 };
 
+// Tab. 2D / 2F: refractory steps round(tau_ref / dt); A_+ = A_plus_rel g_max and
+// A_- = B A_+ tau_+ / tau_-, in double precision on the host.
+static snn_topo_derived topo_derived(const snn_topo_params* p) {
+    snn_topo_derived d;
+    d.n_ref = (int32_t)std::llround(p->tau_ref / p->dt);
+    d.reserved = 0;
+    d.A_plus = p->A_plus_rel * p->g_max;
+    d.A_minus = p->B * d.A_plus * p->tau_plus / p->tau_minus;
+    return d;
+}
+
 static TopoK topo_consts(const snn_topo_params* p) {
+    const snn_topo_derived dv = topo_derived(p);
     TopoK k;
     k.L = p->L;
     k.L_f = p->L_f;
     k.t_stim = p->t_stim;
-    k.n_ref = p->n_ref;
+    k.n_ref = dv.n_ref;
     k.N = p->L * p->L;
     k.Nw = (k.N + 31) / 32;
     k.ds = (float)std::exp(-p->dt / p->tau_s);
@@ -42,8 +54,8 @@ static TopoK topo_consts(const snn_topo_params* p) {
     k.V_reset = (float)p->V_reset;
     k.g_leak = (float)p->g_leak;
     k.g_max = (float)p->g_max;
-    k.A_plus = (float)p->A_plus;
-    k.A_minus = (float)p->A_minus;
+    k.A_plus = (float)dv.A_plus;
+    k.A_minus = (float)dv.A_minus;
     return k;
 }
 
@@ -395,8 +407,11 @@ static size_t rewire_smem(int P, int n_att, int Qw, int threads) {
 static snn_status check_topo(const snn_topo_params* p) {
     SNN_REQUIRE(p, "topo: NULL parameters");
     SNN_REQUIRE(p->L > 0 && p->L_f > 0 && p->L % p->L_f == 0, "topo: need L > 0 and L a multiple of L_f");
-    SNN_REQUIRE(p->t_stim > 0 && p->n_ref >= 0 && p->dt > 0 && p->tau_m > 0 && p->tau_s > 0 && p->g_leak > 0,
+    SNN_REQUIRE(p->t_stim > 0 && p->tau_ref >= 0 && p->dt > 0 && p->tau_m > 0 && p->tau_s > 0 && p->g_leak > 0 &&
+                    p->tau_plus > 0 && p->tau_minus > 0,
                 "topo: bad time constants");
+    SNN_REQUIRE(p->tau_ref / p->dt < 1e9, "topo: tau_ref / dt too large");
+    SNN_REQUIRE(p->g_max >= 0 && p->A_plus_rel >= 0 && p->B >= 0, "topo: g_max, A_plus_rel and B must be >= 0");
     SNN_REQUIRE(p->sigma_stim >= 0.0, "topo: sigma_stim must be >= 0");
     return SNN_OK;
 }
@@ -430,8 +445,9 @@ static snn_status rewire_prepare(snn_ragged* r, const snn_topo_rewire* p, Rewire
     k.Qw = r->Qw;
     k.L = p->L;
     k.n_att = p->n_att;
-    k.g_theta = (float)p->g_theta;
-    k.g_new = (float)p->g_new;
+    SNN_REQUIRE(p->g_max >= 0, "snn_rewire_topo: g_max must be >= 0");
+    k.g_theta = (float)(0.5 * p->g_max);      // Tab. 2G: g_theta = g_max / 2
+    k.g_new = (float)p->g_max;                // a new synapse starts at g_max
     k.thr_dep = prob_threshold(p->p_elim_dep);
     k.thr_pot = prob_threshold(p->p_elim_pot);
     k.seed = d.seed;
@@ -774,15 +790,27 @@ snn_status snn_topo_neurons(const snn_topo_params* p, const snn_topo_state* st, 
     return SNN_OK;
 }
 
+snn_status snn_topo_derive(const snn_topo_params* p, snn_topo_derived* out) {
+    clear_error();
+    SNN_REQUIRE(out, "snn_topo_derive: NULL output");
+    snn_status st = check_topo(p);
+    if (st != SNN_OK) return st;
+    *out = topo_derived(p);
+    return SNN_OK;
+}
+
 snn_status snn_stdp_update(snn_ragged* r, const snn_topo_params* p, const uint32_t* pre_bits, const uint32_t* post_bits,
                            const float* x_pre, const float* ydec, snn_stream stream) {
     clear_error();
     SNN_REQUIRE(r && p && pre_bits && post_bits && x_pre && ydec, "snn_stdp_update: NULL argument");
     SNN_REQUIRE(r->d.dtype == SNN_F32, "snn_stdp_update: F32 only");
+    snn_status st = check_topo(p);
+    if (st != SNN_OK) return st;
+    const snn_topo_derived dv = topo_derived(p);
     const snn_ragged_desc& d = r->d;
     k_stdp<<<ceil_div((long long)d.P * 32, 256), 256, 0, (cudaStream_t)stream>>>(
-        d.row_len, d.ind, (float*)d.w, d.P, d.C, pre_bits, post_bits, x_pre, ydec, (float)p->A_plus,
-        (float)p->A_minus, (float)p->g_max);
+        d.row_len, d.ind, (float*)d.w, d.P, d.C, pre_bits, post_bits, x_pre, ydec, (float)dv.A_plus,
+        (float)dv.A_minus, (float)p->g_max);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }

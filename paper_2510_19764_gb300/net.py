@@ -4,7 +4,6 @@ method happens here; every step runs in libsnnsp.so.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -212,17 +211,16 @@ def spikes_from_bits(bits: np.ndarray, n: int) -> np.ndarray:
 
 
 def adam_params(lr: float, step: int, l1: float = 0.0, beta1: float = 0.9, beta2: float = 0.999,
-                eps: float = 1e-8, b1t: float | None = None, b2t: float | None = None, bias_dev=None,
-                temperature: float = 0.0, noise_idx: int | None = None, noise_idx_dev=None) -> abi.Adam:
-    """Adam hyper-parameters; bias_dev (device float64 {beta1^t, beta2^t}) makes the
-    kernels read the bias corrections from device memory.  temperature > 0 turns on the
-    DEEP R noise term with Philox counter noise_idx (default: step - 1) or, if given,
-    the device int64 noise_idx_dev."""
+                eps: float = 1e-8, step_dev=None, temperature: float = 0.0, noise_idx: int | None = None,
+                noise_idx_dev=None) -> abi.Adam:
+    """Adam hyper-parameters for the step-th update (the library forms the bias
+    corrections); step_dev (device int64 holding the step count) makes the kernels read
+    it from device memory.  temperature > 0 turns on the DEEP R noise term with Philox
+    counter noise_idx (default: step - 1) or, if given, the device int64 noise_idx_dev."""
     a = abi.Adam()
     a.lr, a.beta1, a.beta2, a.eps, a.l1 = lr, beta1, beta2, eps, l1
-    a.b1t = beta1 ** step if b1t is None else b1t
-    a.b2t = beta2 ** step if b2t is None else b2t
-    a.bias_dev = abi.ptr(bias_dev)
+    a.step = step
+    a.step_dev = abi.ptr(step_dev)
     a.temperature = temperature
     a.noise_idx = step - 1 if noise_idx is None else noise_idx
     a.noise_idx_dev = abi.ptr(noise_idx_dev)
@@ -246,17 +244,14 @@ def train_batch(cls: DeviceClassifier, batch: DeviceBatch, adam: abi.Adam, rewir
 def topo_params(L: int = 32, L_f: int | None = None, radius: int = 3, t_stim: int = 20, dt: float = 1.0,
                 tau_m=20.0, V_rest=-70.0, E_exc=0.0, V_theta=-54.0, V_reset=-70.0, tau_ref=5.0, tau_s=5.0,
                 g_leak=1.0, f_base=20.0, f_in=100.0, g_max=0.2, tau_plus=20.0, tau_minus=64.0,
-                B_ratio=1.2, sigma_stim: float = 0.0) -> abi.TopoParams:
+                B_ratio=1.2, A_plus_rel=0.1, sigma_stim: float = 0.0) -> abi.TopoParams:
     """Topographic-map parameters (Tab. 1-2).  t_stim is in steps; sigma_stim > 0 selects
     the Gaussian input profile (f_in then is the peak rate), 0 the disc of `radius`."""
     p = abi.TopoParams()
     p.L, p.L_f, p.radius2, p.t_stim = L, L_f or L, radius * radius, t_stim
-    p.n_ref, p.reserved = int(round(tau_ref / dt)), 0
     p.dt, p.tau_m, p.V_rest, p.E_exc, p.V_theta, p.V_reset = dt, tau_m, V_rest, E_exc, V_theta, V_reset
-    p.tau_s, p.g_leak, p.f_base, p.f_in, p.g_max = tau_s, g_leak, f_base, f_in, g_max
-    p.tau_plus, p.tau_minus = tau_plus, tau_minus
-    p.A_plus = 0.1 * g_max
-    p.A_minus = B_ratio * p.A_plus * tau_plus / tau_minus
+    p.tau_s, p.g_leak, p.tau_ref, p.f_base, p.f_in, p.g_max = tau_s, g_leak, tau_ref, f_base, f_in, g_max
+    p.tau_plus, p.tau_minus, p.A_plus_rel, p.B = tau_plus, tau_minus, A_plus_rel, B_ratio
     p.sigma_stim = sigma_stim
     return p
 
@@ -265,7 +260,7 @@ def topo_rewire(L: int, p_form: float, sigma: float, n_att: int, g_max: float = 
                 p_elim_dep: float = 2.45e-2 * 50, p_elim_pot: float = 1.36e-4 * 50) -> abi.TopoRewire:
     r = abi.TopoRewire()
     r.p_form, r.sigma, r.p_elim_dep, r.p_elim_pot = p_form, sigma, p_elim_dep, p_elim_pot
-    r.g_theta, r.g_new, r.L, r.n_att = 0.5 * g_max, g_max, L, n_att
+    r.g_max, r.L, r.n_att = g_max, L, n_att
     return r
 
 

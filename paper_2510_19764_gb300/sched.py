@@ -75,23 +75,22 @@ class Instance:
             np.maximum(1, np.rint(rng.uniform(0.8, 1.2, 64) * T / N_BINS)).astype(np.int32), device=device)
         self.batch = net.DeviceBatch(self.cls, [0], [int(self.bin_table[0])], [0], T, device=device)
         self.step = torch.zeros(1, dtype=torch.int64, device=device)          # iterations done
-        self.betas = torch.tensor([0.9, 0.999], dtype=torch.float64, device=device)
-        self.bias = torch.ones(2, dtype=torch.float64, device=device)         # beta^t after the update
+        self.adam_t = torch.zeros(1, dtype=torch.int64, device=device)        # Adam step count of this iteration
         self.stats = torch.zeros((2, 4), dtype=torch.int64, device=device)
         # DEEP R noise (temperature > 0) draws with the iteration counter as Philox field
-        self.adam = net.adam_params(lr, 1, l1=l1, bias_dev=self.bias, temperature=temperature,
+        self.adam = net.adam_params(lr, 1, l1=l1, step_dev=self.adam_t, temperature=temperature,
                                     noise_idx_dev=self.step)
         self.lr, self.l1 = lr, l1
         self.events = 0
 
     def _prologue(self):
         """Device-side bookkeeping of one iteration: trial id = iteration index, label and
-        time warp from it, Adam's beta powers advanced, state reset."""
+        time warp from it, Adam step count advanced, state reset."""
         bt = self.batch
         bt.trial_ids.copy_(self.step)
         bt.labels.copy_((self.step % N_CLASSES).to(torch.int32))
         bt.bin_len.copy_(self.bin_table.index_select(0, self.step % self.bin_table.numel()))
-        self.bias.mul_(self.betas)
+        self.adam_t.add_(1)
         for t in (bt.v, bt.a, bt.y, bt.ysum, bt.x_bits, bt.z_bits):
             t.zero_()
 

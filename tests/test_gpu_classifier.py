@@ -144,7 +144,7 @@ def test_adam_l1_apply(dtype):
     s.dev.G_b.copy_(torch.as_tensor(Gb))
     W0 = s.dev.W_out.double().cpu().numpy()
     b0 = s.dev.b_out.double().cpu().numpy()
-    ad = net.adam_params(1e-3, 3, l1=1e-2, b1t=0.9 ** 3, b2t=0.999 ** 3)
+    ad = net.adam_params(1e-3, 3, l1=1e-2)
     abi.snn_eprop_update(s.dev.handle, None, abi.SNN_EPROP_APPLY, ad)
     torch.cuda.synchronize()
     # FP32: each stored value is within a few float32 ulps of the FP64 update; moments
@@ -153,14 +153,45 @@ def test_adam_l1_apply(dtype):
     for name, d in (("in", s.dev.w_in), ("rec", s.dev.w_rec)):
         G, m0, v0, sign, rag = host[name]
         Gl = oc.l1_on_sign(G, rag.row_len, rag.ind, sign, 1e-2)
-        w, m, v = oc.adam_ragged(rag.w, m0, v0, Gl, rag.row_len, 1e-3, 0.9 ** 3, 0.999 ** 3)
+        w, m, v = oc.adam_ragged(rag.w, m0, v0, Gl, rag.row_len, 1e-3, oc.adam_bias(0.9, 3),
+                                 oc.adam_bias(0.999, 3))
         mask = np.arange(rag.C)[None] < rag.row_len[:, None]
         for got, ref in ((d.w, w), (d.m, m), (d.v, v)):
             np.testing.assert_allclose(got.double().cpu().numpy()[mask], ref[mask], rtol=rtol, atol=atol)
-    w, m, v = oc.adam(W0, 0 * W0, 0 * W0, Go, 1e-3, 0.9 ** 3, 0.999 ** 3)
+    w, m, v = oc.adam(W0, 0 * W0, 0 * W0, Go, 1e-3, oc.adam_bias(0.9, 3), oc.adam_bias(0.999, 3))
     np.testing.assert_allclose(s.dev.W_out.double().cpu().numpy(), w, rtol=rtol, atol=atol)
-    w, m, v = oc.adam(b0, 0 * b0, 0 * b0, Gb, 1e-3, 0.9 ** 3, 0.999 ** 3)
+    w, m, v = oc.adam(b0, 0 * b0, 0 * b0, Gb, 1e-3, oc.adam_bias(0.9, 3), oc.adam_bias(0.999, 3))
     np.testing.assert_allclose(s.dev.b_out.double().cpu().numpy(), w, rtol=rtol, atol=atol)
+
+
+def test_adam_step_from_device_memory_equals_host_step():
+    """The Adam step count read from device memory (graph replay) gives the same update,
+    bit for bit, as the count passed by value: steps 1, 2, then a jump to 7 and back to 3
+    (the library re-forms the running products), in FP32 and FP64."""
+    from paper_2510_19764_gb300 import abi, net
+    for dtype in (F32, F64):
+        a = _setups.classifier(seed=8, dtype=dtype, lif=False, T=10, max_B=1, n_in=40, N=64, K=3)
+        b = _setups.classifier(seed=8, dtype=dtype, lif=False, T=10, max_B=1, n_in=40, N=64, K=3)
+        rng = np.random.default_rng(1)
+        t_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+        for step in (1, 2, 7, 3):
+            for x, y in ((a.dev.w_in, b.dev.w_in), (a.dev.w_rec, b.dev.w_rec)):
+                G = torch.as_tensor(rng.normal(size=x.w.shape), dtype=x.w.dtype, device="cuda")
+                x.grad.copy_(G)
+                y.grad.copy_(G)
+            Go = torch.as_tensor(rng.normal(size=a.dev.G_out.shape), dtype=a.dev.G_out.dtype, device="cuda")
+            for c in (a.dev, b.dev):
+                c.G_out.copy_(Go)
+                c.G_b.fill_(0.25)
+            t_dev.fill_(step)
+            abi.snn_eprop_update(a.dev.handle, None, abi.SNN_EPROP_APPLY, net.adam_params(1e-2, step, l1=1e-3))
+            abi.snn_eprop_update(b.dev.handle, None, abi.SNN_EPROP_APPLY,
+                                 net.adam_params(1e-2, 1, l1=1e-3, step_dev=t_dev))
+            torch.cuda.synchronize()
+            for x, y in ((a.dev.w_in, b.dev.w_in), (a.dev.w_rec, b.dev.w_rec)):
+                assert torch.equal(x.w, y.w) and torch.equal(x.m, y.m) and torch.equal(x.v, y.v)
+            assert torch.equal(a.dev.W_out, b.dev.W_out) and torch.equal(a.dev.b_out, b.dev.b_out)
+        assert a.dev.w_in.status() == abi.SNN_OK and b.dev.w_in.status() == abi.SNN_OK
 
 
 @pytest.mark.parametrize("dtype", [F32, F64])
@@ -191,8 +222,8 @@ def test_adam_noise_apply(dtype):
         for name, d in (("in", s.dev.w_in), ("rec", s.dev.w_rec)):
             G, h = host[name]
             nu = od.langevin_normals(d.desc.seed, k, h["row_len"], d.C)
-            w, m, v = oc.adam_ragged(h["w"], h["m"], h["v"], G, h["row_len"], lr, 0.9 ** step, 0.999 ** step,
-                                     temperature=temp, nu=nu)
+            w, m, v = oc.adam_ragged(h["w"], h["m"], h["v"], G, h["row_len"], lr, oc.adam_bias(0.9, step),
+                                     oc.adam_bias(0.999, step), temperature=temp, nu=nu)
             got = d.host()
             np.testing.assert_allclose(got["w"], w, rtol=rtol, atol=atol)       # padding included
             np.testing.assert_allclose(got["m"], m, rtol=rtol, atol=atol)
