@@ -329,7 +329,11 @@ snn_status snn_destroy_classifier(snn_classifier* c);
  *   y^t    : alpha y + W_out z^{t-1} + b ;  d^t = softmax(y^t) - onehot(label)
  * and records x, z, psi, d (and v, a, y when those pointers are set).  A label outside
  * [0, n_classes) or a bin_len < 1 sets SNN_ESTATE in w_in's status word and the trial
- * runs with the value clamped into range. */
+ * runs with the value clamped into range.  The synaptic sums are exact in fixed point
+ * (40 fractional bits) while they stay below 2^11 in magnitude: a neuron or readout
+ * whose incoming |weight| sum (input, recurrent and readout weights, the bound on any
+ * step's sum) reaches 2^11 also sets SNN_ESTATE, since its sums could wrap.  Weights
+ * below 2^-17 in magnitude are rounded to the fixed-point grid (2^-40). */
 snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
                             snn_stream stream);
 

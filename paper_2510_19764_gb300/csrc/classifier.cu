@@ -52,7 +52,13 @@ struct FwdParams {
     real* y_rec;
     int record_state;
     const int32_t* trial_T;   // per-trial lengths or NULL
+    const unsigned long long* colsum;   // [N + 64] |weight| sums per accumulator (k_pack)
+    int32_t* status;
 };
+
+// An accumulator's sums are exact while their magnitude stays below 2^11 (2^51 in fixed
+// point); the sum of |weight| over every slot aimed at it bounds any step's sum.
+constexpr unsigned long long FIX_SUM_LIMIT = 1ull << 51;
 
 struct InputParams {
     int n_in, Win, T, t0, n_steps, n_bins, n_classes, B;
@@ -199,6 +205,12 @@ __global__ void __launch_bounds__(TH, 1024 / TH) k_forward(FwdParams<real> p) {
         yk = p.y[(size_t)b * K + lane];
         ysk = p.ysum[(size_t)b * K + lane];
         bk = p.b_out[lane];
+    }
+    if (b == 0) {
+        // a neuron or readout whose |weight| sum reaches 2^11 could wrap its fixed-point sum
+        bool over = false;
+        for (int j = tid; j < N + 64; j += TH) over |= p.colsum[j] >= FIX_SUM_LIMIT;
+        if (__syncthreads_or(over) && tid == 0) atomicOr(p.status, ST_STATE);
     }
     const uint32_t* xrec_b = p.x_rec + (size_t)b * p.T * Win;
     uint32_t* zrec_b = p.z_rec + (size_t)b * p.T * Wh;
@@ -371,7 +383,7 @@ __global__ void k_pack(const real* __restrict__ w_in, const int32_t* __restrict_
                        const int32_t* __restrict__ len_in, int C_in, int n_in, const real* __restrict__ w_rec,
                        const int32_t* __restrict__ ind_rec, const int32_t* __restrict__ len_rec, int C_rec,
                        const real* __restrict__ W_out, int K, int N, int Cf, unsigned long long* __restrict__ pk,
-                       long long n) {
+                       long long n, unsigned long long* __restrict__ colsum) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int r = (int)(i / Cf), s = (int)(i % Cf);
@@ -395,6 +407,7 @@ __global__ void k_pack(const real* __restrict__ w_in, const int32_t* __restrict_
         }
     }
     pk[i] = ((unsigned long long)tgt << 52) | ((unsigned long long)f & ((1ull << 52) - 1));
+    if (f) atomicAdd(&colsum[tgt], (unsigned long long)(f < 0 ? -f : f));
 }
 
 // ------------------------------------------------------------------ backward
@@ -837,10 +850,11 @@ template <typename real>
 static snn_status refresh_fixed(snn_classifier* c, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
     const long long n = (long long)(d.n_in + d.N) * c->Cf;
+    SNN_CUDA(cudaMemsetAsync(c->colsum, 0, (size_t)(d.N + 64) * sizeof(unsigned long long), s));
     k_pack<real><<<ceil_div(n, 256), 256, 0, s>>>(
         (const real*)d.w_in->d.w, d.w_in->d.ind, d.w_in->d.row_len, d.w_in->d.C, d.n_in, (const real*)d.w_rec->d.w,
         d.w_rec->d.ind, d.w_rec->d.row_len, d.w_rec->d.C, (const real*)d.W_out, d.K, d.N, c->Cf,
-        (unsigned long long*)c->pk, n);
+        (unsigned long long*)c->pk, n, c->colsum);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -916,6 +930,8 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.y_rec = (real*)bt->y_rec;
     p.record_state = (bt->v_rec && bt->a_rec) ? 1 : 0;
     p.trial_T = bt->trial_T;
+    p.colsum = c->colsum;
+    p.status = d.w_in->status;
     const size_t smem = fwd_smem(d.n_in, d.N, Win, Wh);
     snn_status st = refresh_fixed<real>(c, s);
     if (st != SNN_OK) return st;
@@ -1385,6 +1401,7 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     c->h_beta1 = c->h_beta2 = -1.0;
     c->h_t = 0;
     if (e == cudaSuccess) e = cudaMalloc(&c->adam_dev, sizeof(AdamBias));
+    if (e == cudaSuccess) e = cudaMalloc(&c->colsum, (size_t)(d->N + 64) * sizeof(unsigned long long));
     if (e == cudaSuccess) {
         const AdamBias init = {1.0, 1.0, -1.0, -1.0, 0, 0};
         e = cudaMemcpy(c->adam_dev, &init, sizeof(AdamBias), cudaMemcpyHostToDevice);
@@ -1416,6 +1433,7 @@ snn_status snn_destroy_classifier(snn_classifier* c) {
     cudaFree(c->pk);
     cudaFree(c->gkeys);
     cudaFree(c->adam_dev);
+    cudaFree(c->colsum);
     free(c);
     return SNN_OK;
 }

@@ -237,6 +237,7 @@ struct snn_classifier {
     void* pk;                // [(n_in + N) * Cf] packed forward rows (refreshed per forward call)
     int32_t* gkeys;          // [P_in*C_in + N*C_rec] gather order: (target << 11) | slot, ascending per row
     int32_t Cf;              // slots per packed row: max(C_in, C_rec + K) rounded up to 32
+    unsigned long long* colsum;  // [N + 64] sum of |weight| (fixed point) aimed at each accumulator
     // Adam bias corrections: running products beta^t.  Host copy for calls that pass the
     // step count by value, device copy (snn::AdamBias) for calls that pass it in device
     // memory; each remembers the t and betas it was formed for.

@@ -231,3 +231,32 @@ def test_bounded_wait_gives_up_with_a_status_and_the_context_survives():
     got = net.u64_to_numpy(out)
     want = [int(oph.draw(5, 1, np.uint64(7), np.uint64(1), np.uint64(2), np.uint64(3), word=q)) for q in range(4)]
     assert [int(x) for x in got] == want
+
+
+@pytest.mark.parametrize("where", ["one_weight", "input_column", "readout_column", "below_limit"])
+def test_fixed_point_range_is_flagged(where):
+    """The forward's sums are exact in fixed point while |sum| < 2^11.  A neuron or
+    readout whose incoming |weight| sum reaches 2^11 (one oversized weight, many input
+    weights onto one neuron, a readout's column of W_out) is reported as SNN_ESTATE;
+    a sum just below the limit is not."""
+    from paper_2510_19764_gb300 import abi, net
+    s = _setups.classifier(seed=3, dtype=abi.SNN_F32, T=20, max_B=2, n_in=32, N=64, K=4, p_in=1.0)
+    d = s.dev
+    if where == "one_weight":
+        d.w_in.w[0, 0] = 3000.0
+    elif where == "input_column":
+        # target of slot 0 of every input row: all 32 rows reach every target (p_in = 1)
+        tgt = int(d.w_in.ind[0, 0])
+        mask = d.w_in.ind == tgt
+        d.w_in.w[mask] = 64.5                      # 32 x 64.5 = 2064 >= 2048
+        assert int(mask.sum()) == 32
+    elif where == "readout_column":
+        d.W_out[1, :] = 32.5                       # 64 x 32.5 = 2080
+    else:
+        d.W_out[1, :] = 31.5                       # 64 x 31.5 = 2016 < 2048
+    tb = synth.trial_batch(s.task, 0, 0, 2)
+    batch = net.DeviceBatch(d, tb.labels, tb.bin_len, tb.trial_ids, 20)
+    abi.snn_step_neurons(d.handle, batch.desc, 0, 20)
+    torch.cuda.synchronize()
+    want = abi.SNN_OK if where == "below_limit" else abi.SNN_ESTATE
+    assert d.w_in.status() == want
