@@ -35,9 +35,10 @@ sys.path.insert(0, ROOT)
 # x2), DEEP R 10 (eliminate, round0, accept0, distribute, form per projection; plus one
 # 16-byte memset each)
 LAUNCHES_PER_BATCH = 27
-# DRAM bytes (read + write) of one k_forward launch at 512 trials: 4 x the 507.3 MB that
-# ncu measured for the 128-trial case of the same kernel build (None once it changes)
-FORWARD_TRAFFIC = 4 * 506.79e6
+# DRAM bytes (read + write) of one k_forward launch at 512 trials from one ncu capture of
+# the current kernel build (None until it has been captured; see profiles/)
+FORWARD_TRAFFIC = None
+FORWARD_TRAFFIC_SOURCE = None
 METRIC = "e-prop+DEEP R training samples/s"
 UNIT = "samples/s"
 WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}
@@ -50,7 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--sample-steps", type=int, default=600, help="oracle sample: steps of one trial")
+    ap.add_argument("--sample-steps", type=int, default=100,
+                    help="--impl reference: steps of the one trial each timed step simulates")
     ap.add_argument("--batch", type=int, default=512, help="trials per batch (512 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--workload", default="classifier",
@@ -382,6 +384,7 @@ def run_ours(args, world, rank, local):
         3: 8.0 * active,
     }
     alg = algs[dom]
+    traffic = FORWARD_TRAFFIC * B / 512 if dom == 0 and FORWARD_TRAFFIC else None
     achieved = alg / (last_call[dom] / 1e3) / 1e9
     by_call = {calls[c]: {"achieved_gbs": round(algs[c] / (last_call[c] / 1e3) / 1e9, 1),
                           "frac": round(algs[c] / (last_call[c] / 1e3) / 1e9 / pk["hbm_gbs"], 4)}
@@ -394,9 +397,16 @@ def run_ours(args, world, rank, local):
         "config": classifier_config(in_rag.C, rec_rag.C, world),
         # synaptic events of the last timed batch over its own step time
         "synaptic_events_per_s": round(events * world / (sum(last_call) / 1e3), 1),
-        # e-prop: the per-synapse trace form updates every active synapse of every trial at
-        # every step; the adjoint gather computes the same gradients from synaptic events
-        "synapse_updates_per_s": round(active * B * T * world / (ms_max / 1e3 / args.steps), 1),
+        # e-prop as computed here (adjoint form): per batch the reverse-time scan visits
+        # every (trial, step, hidden neuron) once and the gather reads one adjoint value per
+        # synaptic event; both over the gradient call's own time
+        "eprop_adjoint": {"neuron_steps_scanned_per_s": round(B * T * N * world / (last_call[1] / 1e3), 1),
+                          "gathered_events_per_s": round(events * world / (last_call[1] / 1e3), 1)},
+        # NOT work done: the update count of the per-synapse trace form (every active
+        # synapse of every trial at every step) that the adjoint form replaces, per second
+        # of the whole training step; a nominal equivalent for comparison with trace-form
+        # implementations only
+        "trace_form_equivalent_synapse_updates_per_s": round(active * B * T * world / (ms_max / 1e3 / args.steps), 1),
         # DEEP R: (removed + formed) over the rewiring calls' own time
         "rewired_synapses_per_s": round(rewired / (per_call[3] * args.steps / 1e3), 1) if per_call[3] > 0 else None,
         "deepr_rewired_fraction": {"per_batch": rewired_fraction,
@@ -404,9 +414,15 @@ def run_ours(args, world, rank, local):
         "per_call_ms": {c: round(x, 4) for c, x in zip(calls, per_call)},
         "roofline": {"kernel": calls[dom], "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-                     "traffic": FORWARD_TRAFFIC * B / 512 if dom == 0 and FORWARD_TRAFFIC else None,
-                     "traffic_source": "k_forward DRAM read+write per launch from one ncu capture of the "
-                                       "128-trial case, scaled by trials (the psi record grows with them)",
+                     "achieved_is": "algorithmic bytes (events x 8 B + spike entries x 4 B + neuron-steps x 32 B) "
+                                    "per launch / CUDA-event time; most of them are served from L2 and shared "
+                                     "memory, see achieved_dram_gbs",
+                     "traffic": traffic,
+                     "achieved_dram_gbs": round(traffic / (last_call[dom] / 1e3) / 1e9, 1) if traffic else None,
+                     "dram_frac": round(traffic / (last_call[dom] / 1e3) / 1e9 / pk["hbm_gbs"], 4) if traffic
+                     else None,
+                     "traffic_source": FORWARD_TRAFFIC_SOURCE if traffic else
+                     "null: no ncu capture of the current k_forward build",
                      "peak_source": pk["source"]},
         "roofline_by_call": by_call,
         "e2e": {"value": round(B * args.steps * world / (e2e_ms / 1e3), 2), "unit": UNIT,
@@ -418,28 +434,74 @@ def run_ours(args, world, rank, local):
     return line
 
 
-def run_reference(args, sample_steps: int, world: int, rank: int):
-    """FP64 CPU oracle on a bounded sample: one trial of `sample_steps` steps of the same
-    network (forward + e-prop traces), scaled to a full 1000-step trial."""
+def cpu_info() -> dict:
+    """Host CPU model and the threads the oracle uses (one)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
+def oracle_batch_sample(seed: int, sample_steps: int, n_trials: int):
+    """The FP64 oracle on one core for one training batch step of the bench workload,
+    on a bounded sample: n_trials trials of sample_steps steps each (forward, e-prop
+    traces and gradients), then the whole per-batch update on the full matrices (L1 +
+    Adam on both projections and the readout, DEEP R on both projections).  The batch
+    time is B x (per-trial time scaled to 1000 steps) + the update time.  Returns
+    (samples/s, description)."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import numpy as np
     import synth
     from oracle import classifier as oc
+    from oracle import deepr as od
     W = WORKLOAD
-    seed = args.seed
     task = synth.spoken_digit_task(seed, n_in=W["n_in"], n_classes=W["n_classes"], T=W["T"], n_bins=W["n_bins"])
     in_rag = synth.random_ragged(seed + 1, W["n_in"], W["N"], W["p"])
     rec_rag = synth.random_ragged(seed + 2, W["N"], W["N"], W["p"], no_autapse=True)
     W_out, b = synth.dense_readout(seed + 3, W["K"], W["N"])
     onet = oc.ClassifierNet(W["n_in"], W["N"], W["K"], in_rag.row_len, in_rag.ind, in_rag.w, rec_rag.row_len,
                             rec_rag.ind, rec_rag.w, W_out, b, oc.NeuronParams())
-    tb = synth.trial_batch(task, seed, 0, 1)
+    tb = synth.trial_batch(task, seed, 0, n_trials)
     t0 = time.perf_counter()
-    r = oc.forward_trial(onet, task.thr, tb.labels[0], tb.bin_len[0], tb.trial_ids[0], seed + 7, sample_steps)
-    oc.eprop_gradients(onet, r["x"], r["z"], r["psi"], r["d"])
-    dt = time.perf_counter() - t0
-    per_trial = dt * W["T"] / sample_steps
-    return 1.0 / per_trial, per_trial, dt, (in_rag.C, rec_rag.C)
+    G = None
+    for k in range(n_trials):
+        r = oc.forward_trial(onet, task.thr, tb.labels[k], tb.bin_len[k], tb.trial_ids[k], seed + 7, sample_steps)
+        g = oc.eprop_gradients(onet, r["x"], r["z"], r["psi"], r["d"])
+        G = list(g) if G is None else [a + c for a, c in zip(G, g)]
+    t_trials = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    b1t, b2t = oc.adam_bias(0.9, 1), oc.adam_bias(0.999, 1)
+    counts = 0
+    for (rag, Gm, sd, no_aut) in ((in_rag, G[0], seed + 100, False), (rec_rag, G[1], seed + 101, True)):
+        sign, conn = od.init_bitfields(rag.row_len, rag.ind, rag.w, W["N"], sd)
+        Gl = oc.l1_on_sign(Gm, rag.row_len, rag.ind, sign, 1e-5)
+        w, m, v = oc.adam_ragged(rag.w, 0 * rag.w, 0 * rag.w, Gl, rag.row_len, 1e-3, b1t, b2t)
+        out = od.rewire(rag.row_len, rag.ind, w, m, v, sign, conn, rag.C, W["N"], no_aut, sd, 0)
+        counts += out["removed"] + out["formed"]
+    oc.adam(W_out, 0 * W_out, 0 * W_out, G[2], 1e-3, b1t, b2t)
+    oc.adam(b, 0 * b, 0 * b, G[3], 1e-3, b1t, b2t)
+    t_update = time.perf_counter() - t1
+    per_trial = t_trials / n_trials * W["T"] / sample_steps
+    batch_s = W["B"] * per_trial + t_update
+    desc = (f"{n_trials} trial(s) x {sample_steps} of {W['T']} steps (forward + e-prop traces, {t_trials:.1f} s) "
+            f"scaled to {W['B']} full trials, + one L1/Adam/DEEP R update of both full projections "
+            f"({t_update:.2f} s, {counts} synapses rewired); FP64 numpy, 1 thread")
+    return W["B"] / batch_s, desc, (in_rag.C, rec_rag.C), batch_s
 
 
 # ------------------------------------------------------------------ other workloads
@@ -836,15 +898,21 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        v, per_trial, dt, caps = run_reference(args, args.sample_steps, world, rank)
+        # each timed step is one bounded sample: one trial of --sample-steps steps plus
+        # the per-batch update (the oracle needs no warm-up)
+        vals, last = [], None
+        for _ in range(max(1, args.steps)):
+            last = oracle_batch_sample(args.seed, args.sample_steps, 1)
+            vals.append(last[0])
+        v = sum(vals) / len(vals)
+        cpu = cpu_info()
         line = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_trial * WORKLOAD["B"] * 1e3, 1),
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(WORKLOAD["B"] / v * 1e3, 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": classifier_config(caps[0], caps[1], world),
+                "config": classifier_config(last[2][0], last[2][1], world),
                 "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"1 trial x {args.sample_steps} of 1000 steps (forward + e-prop traces), "
-                                           f"{dt:.1f} s, scaled to a full trial"},
+                                 "sample": last[1], **cpu},
                 "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -852,10 +920,9 @@ def main():
     if rank == 0 and args.no_cpu_baseline:
         print(json.dumps(line), flush=True)
     elif rank == 0:
-        cv, per_trial, dt, _ = run_reference(args, args.sample_steps, world, rank)
-        line["cpu_baseline"] = {"value": round(cv, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"1 trial x {args.sample_steps} of 1000 steps (forward + e-prop traces), "
-                                          f"{dt:.1f} s, scaled to a full trial"}
+        cv, desc, _, _ = oracle_batch_sample(args.seed, 1000, 1)
+        line["cpu_baseline"] = {"value": round(cv, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                **cpu_info()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
