@@ -55,6 +55,8 @@ def parse():
                     help="--impl reference: steps of the one trial each timed step simulates")
     ap.add_argument("--batch", type=int, default=512, help="trials per batch (512 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="skip the batched and served rows of the default line (profiling runs)")
     ap.add_argument("--workload", default="classifier",
                     choices=["classifier", "batched", "serve", "topo", "topo-evolution", "kernels"],
                     help="classifier (default, the benchmark line); batched: 64 uneven instances, plain vs "
@@ -506,57 +508,88 @@ def oracle_batch_sample(seed: int, sample_steps: int, n_trials: int):
 
 # ------------------------------------------------------------------ other workloads
 
-def run_batched(args):
-    """64 independent classifier instances of uneven size and trial length: plain
-    one-at-a-time execution with per-step launches vs one CUDA-graph replay per
-    iteration over 16 streams with autotuned row schedules."""
+def run_batched(args, timed: int | None = None):
+    """64 independent classifier instances of uneven size and trial length (hidden
+    256..2048, 200..1000 steps, 5..20 %), one training trial + DEEP R each per
+    iteration, in four forms of the same computation: the persistent multi-instance
+    kernel (one launch per iteration, row schedules autotuned), a CUDA graph of the
+    per-call launches over 16 streams, and the plain one-instance-at-a-time forms with
+    one forward launch per trial and with one per step.  samples/s = instances /
+    iteration time (CUDA events for the device-timed forms, the host clock around a
+    synchronised iteration for the plain ones)."""
     import torch
     import synth
     from paper_2510_19764_gb300 import abi, build, sched
     build.build()
     abi.load()
+    timed = timed or max(3, args.steps)
     specs = sched.batched_specs(64, args.seed)
     task = synth.spoken_digit_task(args.seed, n_in=sched.N_IN, n_classes=sched.N_CLASSES, T=1000,
                                    n_bins=sched.N_BINS)
     insts = [sched.Instance(s, task) for s in specs]
-    tuner = sched.Autotuner()
+    tuner = sched.Autotuner(warps=(8,))
     table = tuner.tune(insts)
+
+    def dev_time(fn, n):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3 / n
+
+    def host_time(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    mr = sched.MultiRunner(insts)
+    for _ in range(3):
+        mr.iterate()
+    t_multi = dev_time(mr.iterate, timed)
+    ok_multi = mr.status() == abi.SNN_OK
+    mr.capture(4)
+    mr.replay()
+    t_multi_graph = dev_time(mr.replay, max(1, timed // 4)) / 4
     br = sched.BatchedRunner(insts, n_streams=16)
     for inst in insts:          # first calls outside capture
         inst.enqueue(torch.cuda.current_stream())
-    torch.cuda.synchronize()
     br.capture()
-    for _ in range(max(1, args.warmup)):
-        br.iterate()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        br.iterate()
-    b.record()
-    b.synchronize()
-    t_batched = a.elapsed_time(b) / 1e3 / args.steps
-    pr = sched.PlainRunner(insts)
-    pr.iterate()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    pr.iterate()
-    torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t0
+    br.iterate()
+    t_graph = dev_time(br.iterate, timed)
+    whole = sched.PlainRunner(insts, per_step=False)
+    whole.iterate()
+    t_whole = host_time(whole.iterate)
+    per_step = sched.PlainRunner(insts, per_step=True)
+    t_step = host_time(per_step.iterate)
+    ok = ok_multi and all(i.d_in.status() == abi.SNN_OK and i.d_rec.status() == abi.SNN_OK for i in insts)
     n = len(insts)
+    mr.close()
     return {"workload": "batched", "metric": "training samples/s (64 uneven instances, one trial each)",
             "instances": n, "steps_total": int(sum(s.T for s in specs)),
-            "batched_samples_per_s": round(n / t_batched, 2), "plain_samples_per_s": round(n / t_plain, 2),
-            "speedup": round(t_plain / t_batched, 2), "batched_ms_per_iteration": round(t_batched * 1e3, 3),
-            "plain_ms_per_iteration": round(t_plain * 1e3, 1),
-            "autotune_table": {str(k): v for k, v in table.items()},
-            "autotune_ms": {str(k): {w: round(t, 4) for w, t in v.items()} for k, v in tuner.timings.items()}}
+            "persistent_samples_per_s": round(n / t_multi, 2),
+            "persistent_graph_samples_per_s": round(n / t_multi_graph, 2),
+            "graph_of_calls_samples_per_s": round(n / t_graph, 2),
+            "plain_whole_trial_samples_per_s": round(n / t_whole, 2),
+            "plain_per_step_samples_per_s": round(n / t_step, 2),
+            "speedup_vs_plain_whole_trial": round(t_whole / t_multi, 2),
+            "speedup_vs_plain_per_step": round(t_step / t_multi, 2),
+            "ms_per_iteration": {"persistent": round(t_multi * 1e3, 3), "persistent_graph": round(t_multi_graph * 1e3, 3),
+                                 "graph_of_calls": round(t_graph * 1e3, 3), "plain_whole_trial": round(t_whole * 1e3, 2),
+                                 "plain_per_step": round(t_step * 1e3, 1)},
+            "status_ok": bool(ok),
+            "row_schedule_table": {str(k): list(v) for k, v in table.items()}}
 
 
-def run_serve(args):
+def run_serve(args, quick: bool = False):
     """Request loop over 4 resident classifiers (hidden 256..2048, 10 %), requests of
     100-1000 steps, 10 % fine-tuning jobs, Poisson arrivals at 200 / 1000 / 5000 req/s:
-    continuous batching vs one request at a time."""
+    continuous batching vs one request at a time (latency = arrival to result on the
+    host)."""
     import numpy as np
     import torch
     import synth
@@ -570,9 +603,9 @@ def run_serve(args):
     warm = serve.poisson_requests(64, 1e6, len(models), seed=99)
     eng.run(warm, realtime=False)
     eng.run_plain(warm[:8], realtime=False)
-    out = {"workload": "serve", "metric": "served requests/s with p50/p99 latency", "rates": {}}
+    out = {"workload": "serve", "metric": "served requests/s with p50/p99 latency (ms)", "rates": {}}
     for rate in (200.0, 1000.0, 5000.0):
-        n = int(min(4000, rate * 2.0))
+        n = int(min(1500 if quick else 4000, rate * (1.0 if quick else 2.0)))
         reqs = serve.poisson_requests(n, rate, len(models), seed=int(rate))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -584,8 +617,24 @@ def run_serve(args):
         wall_p = time.perf_counter() - t0
         s_p = serve.latency_summary(res_p, wall_p)
         same = all(np.array_equal(x.ysum, y.ysum) for x, y in zip(res, res_p))
-        out["rates"][str(int(rate))] = {"batched": s_b, "plain": s_p, "results_identical": bool(same)}
+        out["rates"][str(int(rate))] = {"requests": n, "continuous": s_b, "plain": s_p,
+                                        "results_identical": bool(same)}
     out["engine_stats"] = eng.stats
+    return out
+
+
+def systems_rows(args) -> dict:
+    """The systems rows of the metric on the default line: the batched form against
+    both plain forms, and served p50/p99 against plain serving (shorter runs than the
+    --workload batched / serve lines)."""
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.empty_cache()
+    out = {"batched": run_batched(args, timed=5)}
+    gc.collect()
+    torch.cuda.empty_cache()
+    out["served"] = run_serve(args, quick=True)
     return out
 
 
@@ -917,6 +966,8 @@ def main():
         print(json.dumps(line), flush=True)
         return 0
     line = run_ours(args, world, rank, local)
+    if rank == 0 and world == 1 and not args.no_systems:
+        line["systems"] = systems_rows(args)
     if rank == 0 and args.no_cpu_baseline:
         print(json.dumps(line), flush=True)
     elif rank == 0:

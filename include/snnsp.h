@@ -314,6 +314,15 @@ snn_status snn_create_classifier(const snn_classifier_desc* desc, snn_classifier
  * spiking rows and neurons (default 8).  Results do not depend on it (integer
  * accumulation); an autotuner picks it per (N, row length, spike rate). */
 snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_trial);
+/* How the warps of a trial share the spiking rows of a step (results do not depend on
+ * it): SNN_ROWS_PAIRS (default) a warp per row, two rows in flight per warp;
+ * SNN_ROWS_PER_WARP a warp per row, one row at a time (many short rows);
+ * SNN_ROWS_PER_BLOCK all warps on each row, a 32-slot chunk each (few long rows).  Used
+ * by snn_step_neurons and by the persistent multi-instance kernel (snn_multi_run). */
+#define SNN_ROWS_PAIRS     0
+#define SNN_ROWS_PER_WARP  1
+#define SNN_ROWS_PER_BLOCK 2
+snn_status snn_classifier_set_row_schedule(snn_classifier* c, int32_t mode);
 snn_status snn_destroy_classifier(snn_classifier* c);
 
 /* Advance every trial of the batch by n_steps steps, t0 .. t0+n_steps-1 (t0 + n_steps
@@ -364,6 +373,66 @@ snn_status snn_step_neurons_ex(snn_classifier* c, const snn_batch* b, int32_t t0
  *   W_out, b_out (needs the moment arrays). */
 snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase,
                             const snn_adam* adam, snn_stream stream);
+
+/* ==================================================================================
+ * Batched form: many classifier instances trained in one persistent launch
+ * ================================================================================== */
+/* One instance of the batched form: its own classifier (FP32; ragged handles with Adam
+ * moments, gradient and DEEP R bitfields, no distance guide), one trial per iteration.
+ * Iteration it of the instance runs exactly what these per-call steps run, in order:
+ *   trial_ids[0] = it, labels[0] = label_table[it % n_label],
+ *   bin_len[0] = bin_table[it % n_bin], state (v, a, y, ysum, x_bits, z_bits) zeroed;
+ *   snn_step_neurons(cls, &batch, 0, T);  snn_eprop_update(GRAD);
+ *   snn_eprop_update(APPLY) with Adam step it + 1, L1 l1, DEEP R noise (temperature,
+ *     Philox counter it);
+ *   snn_rewire_deepr on the input then the recurrent projection with rewire index it,
+ *     counts added to stats[0] and stats[1];
+ *   *iter = it + 1.
+ * The results are bit-identical to those calls (same device functions). */
+typedef struct {
+    snn_classifier* cls;
+    snn_batch batch;                /* B = 1, T <= min(max_T, 8192); state, records and workspace
+                                       (no trial_T) in caller memory */
+    const int32_t* label_table;     /* device [n_label] */
+    int32_t n_label;
+    const int32_t* bin_table;       /* device [n_bin]: steps per template bin */
+    int32_t n_bin;
+    int64_t* iter;                  /* device: iterations done (advanced by each run) */
+    double lr, beta1, beta2, eps, l1, temperature;
+    snn_rewire_stats* stats;        /* device [2] (input, recurrent), accumulated; or NULL */
+} snn_multi_instance;
+
+typedef struct snn_multi snn_multi;
+
+/* Build the work plan of n instances (n distinct classifiers) and allocate its queue,
+ * the instance table and a small mapped-host mailbox; synchronises.  SNN_EINVAL for an
+ * unsupported instance. */
+snn_status snn_multi_create(const snn_multi_instance* inst, int32_t n, snn_multi** out);
+snn_status snn_multi_destroy(snn_multi* m);
+
+#define SNN_MULTI_HOST_POSTS 1
+/* One training iteration of every instance in ONE kernel launch on `stream`: a
+ * persistent grid (as many CTAs as fit on the GPU) takes work items (instance, phase,
+ * index) from a device queue; an instance's phases (input and packing, the trial's
+ * forward, readout scan, adjoint scan, gradient gather, L1 + Adam, DEEP R elimination,
+ * redistribution and formation) follow one another and interleave with the other
+ * instances'.  Every wait of the kernel (for queue work, and for the mailbox) gives up
+ * after wait_limit_ns (0 < limit <= 60 s): the kernel then leaves, the iteration is
+ * incomplete and snn_multi_status returns SNN_ETIMEOUT.
+ * flags = SNN_MULTI_HOST_POSTS: the kernel starts no instance by itself; it waits for a
+ * host producer to name the instances of this iteration with snn_multi_post (called
+ * after snn_multi_run; such runs cannot be replayed from a captured graph).  Without the
+ * flag every instance runs (graph capture allowed: the run's queue stamp lives on the
+ * device).  Runs of one plan must not overlap on the GPU. */
+snn_status snn_multi_run(snn_multi* m, int32_t flags, int64_t wait_limit_ns, snn_stream stream);
+/* Host producer for a SNN_MULTI_HOST_POSTS run: the instances (indices into the array
+ * given to snn_multi_create, no repeats) that the running iteration should train.
+ * Writes the plan's mapped mailbox; the kernel picks it up while it runs. */
+snn_status snn_multi_post(snn_multi* m, const int32_t* instances, int32_t n);
+/* Wait for `stream`, then return and clear the plan's status: SNN_ETIMEOUT if a wait
+ * gave up, SNN_ESTATE for an invalid post, else SNN_OK.  The instances' own device
+ * errors stay in their ragged handles' status words. */
+snn_status snn_multi_status(snn_multi* m, snn_stream stream);
 
 /* ==================================================================================
  * Topographic map (Sec. 2.1.3, Sec. 2.2.2, Tab. 1-2): conductance LIF target sheet,

@@ -19,6 +19,8 @@ SNN_F32, SNN_F64 = 0, 1
 SNN_EPROP_GRAD, SNN_EPROP_APPLY = 0, 1
 SNN_FIXED_FRAC_BITS = 40
 SNN_STEP_INPUTS_READY = 1
+SNN_ROWS_PAIRS, SNN_ROWS_PER_WARP, SNN_ROWS_PER_BLOCK = 0, 1, 2
+SNN_MULTI_HOST_POSTS = 1
 
 EXPORTED = [
     "snn_last_error", "snn_abi_version", "snn_create_ragged", "snn_destroy_ragged", "snn_ragged_status",
@@ -27,6 +29,8 @@ EXPORTED = [
     "snn_philox", "snn_rewire_deepr_noalloc", "snn_classifier_set_schedule", "snn_rewire_deepr_dev",
     "snn_draw_inputs", "snn_step_neurons_ex", "snn_topo_connectivity", "snn_ragged_set_deepr_guide",
     "snn_test_wait_timeout", "snn_ragged_add_row", "snn_ragged_remove_row", "snn_adam_bias", "snn_topo_derive",
+    "snn_classifier_set_row_schedule", "snn_multi_create", "snn_multi_destroy", "snn_multi_run", "snn_multi_post",
+    "snn_multi_status",
 ]
 
 
@@ -71,6 +75,12 @@ class Batch(C.Structure):
 class Adam(C.Structure):
     _fields_ = [("lr", f64), ("beta1", f64), ("beta2", f64), ("eps", f64), ("step", i64), ("step_dev", vp),
                 ("l1", f64), ("temperature", f64), ("noise_idx", i64), ("noise_idx_dev", vp)]
+
+
+class MultiInstance(C.Structure):
+    _fields_ = [("cls", vp), ("batch", Batch), ("label_table", vp), ("n_label", i32), ("bin_table", vp),
+                ("n_bin", i32), ("iter", vp), ("lr", f64), ("beta1", f64), ("beta2", f64), ("eps", f64), ("l1", f64),
+                ("temperature", f64), ("stats", vp)]
 
 
 class DeeprGuide(C.Structure):
@@ -142,6 +152,12 @@ def load() -> C.CDLL:
         "snn_ragged_remove_row": (i32, [vp, vp, vp, vp]),
         "snn_adam_bias": (i32, [f64, f64, i64, P(f64)]),
         "snn_topo_derive": (i32, [P(TopoParams), P(TopoDerived)]),
+        "snn_classifier_set_row_schedule": (i32, [vp, i32]),
+        "snn_multi_create": (i32, [P(MultiInstance), i32, P(vp)]),
+        "snn_multi_destroy": (i32, [vp]),
+        "snn_multi_run": (i32, [vp, i32, i64, vp]),
+        "snn_multi_post": (i32, [vp, P(i32), i32]),
+        "snn_multi_status": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -298,3 +314,32 @@ def snn_topo_derive(p: TopoParams) -> TopoDerived:
     out = TopoDerived()
     check(load().snn_topo_derive(C.byref(p), C.byref(out)))
     return out
+
+
+def snn_classifier_set_row_schedule(h: int, mode: int) -> None:
+    check(load().snn_classifier_set_row_schedule(h, mode))
+
+
+def snn_multi_create(instances: "list[MultiInstance]") -> int:
+    arr = (MultiInstance * len(instances))(*instances)
+    h = vp()
+    check(load().snn_multi_create(arr, len(instances), C.byref(h)))
+    return h.value
+
+
+def snn_multi_destroy(h: int) -> None:
+    check(load().snn_multi_destroy(h))
+
+
+def snn_multi_run(h: int, flags: int = 0, wait_limit_ns: int = 2_000_000_000, stream=None) -> None:
+    check(load().snn_multi_run(h, flags, wait_limit_ns, stream_ptr(stream)))
+
+
+def snn_multi_post(h: int, instances) -> None:
+    ids = list(instances)
+    arr = (i32 * max(1, len(ids)))(*ids)
+    check(load().snn_multi_post(h, arr, len(ids)))
+
+
+def snn_multi_status(h: int, stream=None) -> int:
+    return load().snn_multi_status(h, stream_ptr(stream))

@@ -150,38 +150,11 @@ __global__ void k_reduce_out(const real* __restrict__ part, int N, int K, int KS
     G_out[(size_t)k * N + j] = g;
 }
 
-// beta1^t, beta2^t for a step count read from device memory, kept in the handle's device
-// state: one multiplication per call when t advances by one (graph replay), a fresh
-// running product otherwise.  At most 2^24 multiplications per call: a larger jump sets
-// the invalid-state flag and keeps the partial product (a later call continues it).
 __global__ void k_adam_bias(const long long* __restrict__ step_dev, double beta1, double beta2, AdamBias* st,
                             int32_t* status) {
-    long long t = *step_dev;
-    if (t < 1) {
-        atomicOr(status, ST_STATE);
-        t = 1;
-    }
-    if (st->t == t && st->beta1 == beta1 && st->beta2 == beta2) return;
-    double b1 = 1.0, b2 = 1.0;
-    long long t0 = 0;
-    if (st->beta1 == beta1 && st->beta2 == beta2 && st->t >= 0 && st->t < t) {
-        b1 = st->b1t;
-        b2 = st->b2t;
-        t0 = st->t;
-    }
-    const long long lim = 1ll << 24;
-    adam_bias_advance(beta1, beta2, t0, b1, b2, t, lim);
-    long long reached = t;
-    if (t - t0 > lim && (b1 != 0.0 || b2 != 0.0)) {
-        atomicOr(status, ST_STATE);
-        reached = t0 + lim;
-    }
-    st->b1t = b1;
-    st->b2t = b2;
-    st->beta1 = beta1;
-    st->beta2 = beta2;
-    st->t = reached;
+    adam_bias_step(*step_dev, beta1, beta2, st, status);
 }
+
 
 // ------------------------------------------------------------------ host side
 static size_t fwd_smem(int n_in, int N, int Win, int Wh) {
@@ -302,6 +275,7 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.trial_T = bt->trial_T;
     p.colsum = c->colsum;
     p.status = d.w_in->status;
+    p.sched = c->row_sched;
     const size_t smem = fwd_smem(d.n_in, d.N, Win, Wh);
     snn_status st = refresh_fixed<real>(c, s);
     if (st != SNN_OK) return st;
@@ -686,6 +660,15 @@ snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_tria
                 "snn_classifier_set_schedule: warps_per_trial must be 4, 8 or 16");
     SNN_REQUIRE(c->d.N <= 8 * 32 * warps_per_trial, "snn_classifier_set_schedule: N = %d needs more warps", c->d.N);
     c->fwd_threads = 32 * warps_per_trial;
+    return SNN_OK;
+}
+
+snn_status snn_classifier_set_row_schedule(snn_classifier* c, int32_t mode) {
+    clear_error();
+    SNN_REQUIRE(c, "snn_classifier_set_row_schedule: NULL classifier");
+    SNN_REQUIRE(mode == SNN_ROWS_PAIRS || mode == SNN_ROWS_PER_WARP || mode == SNN_ROWS_PER_BLOCK,
+                "snn_classifier_set_row_schedule: unknown mode %d", mode);
+    c->row_sched = mode;
     return SNN_OK;
 }
 

@@ -37,6 +37,7 @@ struct FwdParams {
     const int32_t* trial_T;   // per-trial lengths or NULL
     const unsigned long long* colsum;   // [N + 64] |weight| sums per accumulator (k_pack)
     int32_t* status;
+    int sched;                // phase A row schedule: SNN_ROWS_PAIRS, SNN_ROWS_PER_WARP or SNN_ROWS_PER_BLOCK
 };
 
 // An accumulator's sums are exact while their magnitude stays below 2^11 (2^51 in fixed
@@ -135,7 +136,61 @@ __device__ __forceinline__ void input_group(const InputParams& p, const long lon
 //  (B) each thread updates its NPT neurons (state in registers) and writes psi; warp 1
 //      advances the leaky readout y^t = alpha y^{t-1} + W_out z^{t-1} + b (one lane per
 //      output, sequential in t) and records y^t into the d record (softmax comes later).
-constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time
+constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time (default schedule)
+
+// Phase A row schedules (all add the same integers, so the sums do not depend on them).
+// Row per warp: warp w takes rows w, w + nwarps, ... of the spike list, FR rows at a time,
+// their 128-slot blocks loaded together (FR = 2: SNN_ROWS_PAIRS, 1: SNN_ROWS_PER_WARP).
+template <int FR, int nwarps>
+__device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lprv, int n_rows, const int* lens,
+                                                    const unsigned long long* pk, int Cf, int R, int warp, int lane) {
+    for (int k = warp; k < n_rows; k += FR * nwarps) {
+        int nr[FR];
+        const unsigned long long* pr[FR];
+        int nmax = 0;
+#pragma unroll
+        for (int u = 0; u < FR; ++u) {
+            const int r = (k + u * nwarps < n_rows) ? lprv[k + u * nwarps] : R;   // R: empty row
+            nr[u] = lens[r];
+            pr[u] = pk + (size_t)(r < R ? r : 0) * Cf;
+            nmax = nr[u] > nmax ? nr[u] : nmax;
+        }
+        for (int s0 = 0; s0 < nmax; s0 += 128) {
+            unsigned long long wv[FR][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int u = 0; u < FR; ++u)   // warp-uniform chunk tests; slots past a
+                    wv[u][q] = s0 + q * 32 < nr[u] ? pr[u][s0 + q * 32 + lane] : 0ull;   // length are padding
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int u = 0; u < FR; ++u)
+                    if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q]);
+        }
+    }
+}
+
+// Row per block: every warp works on every spiking row, warp w taking the row's 32-slot
+// chunks w, w + nwarps, ...; two rows in flight (suits few long rows).
+template <int nwarps>
+__device__ __forceinline__ void propagate_rows_block(unsigned* acc, const int* lprv, int n_rows, const int* lens,
+                                                     const unsigned long long* pk, int Cf, int warp, int lane) {
+    for (int k = 0; k < n_rows; k += 2) {
+        const int r0 = lprv[k];
+        const int r1 = k + 1 < n_rows ? lprv[k + 1] : -1;
+        const int n0 = lens[r0], n1 = r1 >= 0 ? lens[r1] : 0;
+        const unsigned long long* p0 = pk + (size_t)r0 * Cf;
+        const unsigned long long* p1 = pk + (size_t)(r1 >= 0 ? r1 : 0) * Cf;
+        const int nmax = n0 > n1 ? n0 : n1;
+        for (int s0 = warp * 32; s0 < nmax; s0 += nwarps * 32) {
+            const unsigned long long a = s0 < n0 ? p0[s0 + lane] : 0ull;
+            const unsigned long long b = s0 < n1 ? p1[s0 + lane] : 0ull;
+            if (s0 < n0) acc_add(acc, a);
+            if (s0 < n1) acc_add(acc, b);
+        }
+    }
+}
 
 template <typename real, int NPT, int TH>
 __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const int b, unsigned char* smem) {
@@ -214,32 +269,9 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             zcur[w] = 0u;
         }
         if (tid == 32) lcnt[cur] = 0;
-        for (int k = warp; k < n_rows; k += FWD_ROWS * nwarps) {
-            // FWD_ROWS rows per warp at a time, their packed chunks loaded together
-            int nr[FWD_ROWS];
-            const unsigned long long* pr[FWD_ROWS];
-            int nmax = 0;
-#pragma unroll
-            for (int u = 0; u < FWD_ROWS; ++u) {
-                const int r = (k + u * nwarps < n_rows) ? lprv[k + u * nwarps] : R;   // R: empty row
-                nr[u] = lens[r];
-                pr[u] = p.pk + (size_t)(r < R ? r : 0) * p.Cf;
-                nmax = nr[u] > nmax ? nr[u] : nmax;
-            }
-            for (int s0 = 0; s0 < nmax; s0 += 128) {
-                unsigned long long wv[FWD_ROWS][4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int u = 0; u < FWD_ROWS; ++u)   // warp-uniform chunk tests; slots past a
-                        wv[u][q] = s0 + q * 32 < nr[u] ? pr[u][s0 + q * 32 + lane] : 0ull;   // length are padding
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int u = 0; u < FWD_ROWS; ++u)
-                        if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q]);
-            }
-        }
+        if (p.sched == SNN_ROWS_PER_BLOCK) propagate_rows_block<nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, warp, lane);
+        else if (p.sched == SNN_ROWS_PER_WARP) propagate_rows_warp<1, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+        else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
         __syncthreads();
         // ---------------- phase B: neurons; spike lists of step t
         if (warp == 0 && lane < Win) {
@@ -826,6 +858,38 @@ __global__ void __launch_bounds__(BWD_THREADS)
                   float* __restrict__ delta, int T, int N, int K, float alpha, float rho, float beta) {
     __shared__ __align__(16) float D_s[2 * BWD2_TCH * 4 * KV];
     backward_x2_block<KV, BWD_THREADS>(psi, Dg, W_out, delta, T, N, K, alpha, rho, beta, blockIdx.x, blockIdx.y, D_s);
+}
+
+// beta1^t, beta2^t for the step count t, kept in device state: one multiplication per
+// call when t advances by one (graph replay), a fresh running product otherwise.  At most
+// 2^24 multiplications per call: a larger jump sets the invalid-state flag and keeps the
+// partial product (a later call continues it).  One thread.
+__device__ __forceinline__ void adam_bias_step(long long t, double beta1, double beta2, AdamBias* st,
+                                               int32_t* status) {
+    if (t < 1) {
+        atomicOr(status, ST_STATE);
+        t = 1;
+    }
+    if (st->t == t && st->beta1 == beta1 && st->beta2 == beta2) return;
+    double b1 = 1.0, b2 = 1.0;
+    long long t0 = 0;
+    if (st->beta1 == beta1 && st->beta2 == beta2 && st->t >= 0 && st->t < t) {
+        b1 = st->b1t;
+        b2 = st->b2t;
+        t0 = st->t;
+    }
+    const long long lim = 1ll << 24;
+    adam_bias_advance(beta1, beta2, t0, b1, b2, t, lim);
+    long long reached = t;
+    if (t - t0 > lim && (b1 != 0.0 || b2 != 0.0)) {
+        atomicOr(status, ST_STATE);
+        reached = t0 + lim;
+    }
+    st->b1t = b1;
+    st->b2t = b2;
+    st->beta1 = beta1;
+    st->beta2 = beta2;
+    st->t = reached;
 }
 
 }  // namespace snn

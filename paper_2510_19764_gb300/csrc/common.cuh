@@ -229,6 +229,7 @@ struct snn_ragged {
 struct snn_classifier {
     snn_classifier_desc d;
     int32_t fwd_threads;     // row schedule of the forward: threads sharing one trial
+    int32_t row_sched;       // SNN_ROWS_PAIRS / SNN_ROWS_PER_WARP / SNN_ROWS_PER_BLOCK
     double alpha, rho;
     int32_t KS;              // K-splits of the e-prop gather
     void* part_in;           // [KS][P_in*C_in] partial gradients

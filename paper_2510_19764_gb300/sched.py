@@ -3,22 +3,26 @@
 Each instance is its own sparse ALIF classifier (700 inputs -> N hidden -> 20 readouts,
 its own ragged matrices, connectivity and Philox seeds) training with one trial per
 iteration and DEEP R after every trial.  Instances differ in hidden size and trial
-length, so no two share a kernel launch; two execution forms use the same kernels:
+length.  Three execution forms run the same device code:
 
-* plain:   one instance after another on one stream, one `snn_step_neurons` launch per
-           simulated step, then the gradient, Adam and DEEP R calls; no graph.
-* batched: the whole iteration of every instance — state reset, the full trial in one
-           forward launch, gradient, Adam, DEEP R — captured once in a CUDA graph over
-           several streams and replayed.  Everything that changes between iterations
-           (trial id, label, Adam's beta powers, the DEEP R rewiring index) lives in
-           device memory and is advanced by the graph itself.
+* plain:   one instance after another on one stream, no graph: either one
+           `snn_step_neurons` launch per simulated step (`per_step=True`) or one
+           launch for the whole trial, then the gradient, Adam and DEEP R calls.
+* graph:   the whole iteration of every instance (per-call launches) captured once in
+           a CUDA graph over several streams and replayed.
+* multi:   ONE persistent kernel launch per iteration (`snn_multi_run`): a device work
+           queue of (instance, phase, item) entries that all CTAs of the GPU drain; an
+           instance's phases (inputs, forward, readout scan, adjoint, gather, Adam, DEEP
+           R) follow one another while the instances interleave.  Iterations can be
+           captured in a CUDA graph as well.
 
-Results are identical in both forms (integer spike accumulation; same kernels and
-order per instance), which tests/test_gpu_sched.py checks bit for bit.
+Everything that changes between iterations (trial id, label, time warp, Adam's step,
+the DEEP R rewiring index) is derived on the device from the instance's iteration
+counter, so all forms give bit-identical results (tests/test_gpu_sched.py).
 
-The row schedule of the forward (warps sharing one trial's spiking rows) is picked per
-(hidden size, mean row length, spike rate) class by `Autotuner`, which times the
-candidate schedules on a sample trial of a representative instance.
+The row schedule of the forward (how a trial's warps share the spiking rows of a step)
+is picked per (hidden size, mean row length, spike rate) class by `Autotuner`, which
+times the candidate schedules on a sample trial of a representative instance.
 """
 from __future__ import annotations
 
@@ -74,6 +78,7 @@ class Instance:
         self.bin_table = torch.as_tensor(
             np.maximum(1, np.rint(rng.uniform(0.8, 1.2, 64) * T / N_BINS)).astype(np.int32), device=device)
         self.batch = net.DeviceBatch(self.cls, [0], [int(self.bin_table[0])], [0], T, device=device)
+        self.label_table = torch.arange(N_CLASSES, dtype=torch.int32, device=device)
         self.step = torch.zeros(1, dtype=torch.int64, device=device)          # iterations done
         self.adam_t = torch.zeros(1, dtype=torch.int64, device=device)        # Adam step count of this iteration
         self.stats = torch.zeros((2, 4), dtype=torch.int64, device=device)
@@ -88,9 +93,9 @@ class Instance:
         time warp from it, Adam step count advanced, state reset."""
         bt = self.batch
         bt.trial_ids.copy_(self.step)
-        bt.labels.copy_((self.step % N_CLASSES).to(torch.int32))
+        bt.labels.copy_(self.label_table.index_select(0, self.step % self.label_table.numel()))
         bt.bin_len.copy_(self.bin_table.index_select(0, self.step % self.bin_table.numel()))
-        self.adam_t.add_(1)
+        self.adam_t.copy_(self.step + 1)
         for t in (bt.v, bt.a, bt.y, bt.ysum, bt.x_bits, bt.z_bits):
             t.zero_()
 
@@ -111,6 +116,20 @@ class Instance:
         with torch.cuda.stream(stream):
             self.step.add_(1)
 
+    def multi_instance(self) -> abi.MultiInstance:
+        """This instance's entry of a persistent multi-instance plan (same iteration
+        semantics as enqueue)."""
+        m = abi.MultiInstance()
+        m.cls = self.cls.handle
+        m.batch = self.batch.desc
+        m.label_table, m.n_label = abi.ptr(self.label_table), self.label_table.numel()
+        m.bin_table, m.n_bin = abi.ptr(self.bin_table), self.bin_table.numel()
+        m.iter = abi.ptr(self.step)
+        m.lr, m.beta1, m.beta2, m.eps = self.adam.lr, self.adam.beta1, self.adam.beta2, self.adam.eps
+        m.l1, m.temperature = self.adam.l1, self.adam.temperature
+        m.stats = abi.ptr(self.stats)
+        return m
+
     def snapshot(self) -> dict:
         out = {}
         for name, d in (("in", self.d_in), ("rec", self.d_rec)):
@@ -122,15 +141,17 @@ class Instance:
 
 
 class PlainRunner:
-    """One instance at a time, per-step launches, one stream, no graph."""
+    """One instance at a time on one stream, no graph: per-step forward launches
+    (per_step=True) or one forward launch per trial."""
 
-    def __init__(self, instances, stream=None):
+    def __init__(self, instances, stream=None, per_step: bool = True):
         self.instances = instances
         self.stream = stream or torch.cuda.current_stream()
+        self.per_step = per_step
 
     def iterate(self):
         for inst in self.instances:
-            inst.enqueue(self.stream, per_step=True)
+            inst.enqueue(self.stream, per_step=self.per_step)
 
 
 class BatchedRunner:
@@ -159,15 +180,58 @@ class BatchedRunner:
         self.graph.replay()
 
 
+class MultiRunner:
+    """All instances' iterations in one persistent kernel launch each (snn_multi_run);
+    capture() puts `n_iter` such launches into one CUDA graph."""
+
+    def __init__(self, instances, wait_limit_ns: int = 2_000_000_000):
+        self.instances = instances
+        self.handle = abi.snn_multi_create([inst.multi_instance() for inst in instances])
+        self.wait_limit_ns = wait_limit_ns
+        self.graph = None
+        self.graph_iters = 0
+
+    def iterate(self, stream=None, flags: int = 0):
+        abi.snn_multi_run(self.handle, flags, self.wait_limit_ns, stream)
+
+    def capture(self, n_iter: int = 1):
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(n_iter):
+                abi.snn_multi_run(self.handle, 0, self.wait_limit_ns, s)
+        self.graph, self.graph_iters = g, n_iter
+
+    def replay(self):
+        self.graph.replay()
+
+    def status(self, stream=None) -> int:
+        return abi.snn_multi_status(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            abi.snn_multi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Autotuner:
     """Row-schedule table keyed on (hidden size, mean row length, spike rate): for each
     class, time the forward of a representative instance's trial with every admissible
-    warps-per-trial choice and keep the fastest."""
+    (warps per trial, row schedule) choice and keep the fastest.  The persistent kernel
+    runs 8 warps per trial, so for it only the row schedule is tuned (warps=(8,))."""
 
-    CANDIDATES = (4, 8, 16)
+    MODES = (abi.SNN_ROWS_PAIRS, abi.SNN_ROWS_PER_WARP, abi.SNN_ROWS_PER_BLOCK)
 
-    def __init__(self):
-        self.table: dict[tuple, int] = {}
+    def __init__(self, warps=(4, 8, 16)):
+        self.warps = tuple(warps)
+        self.table: dict[tuple, tuple] = {}
         self.timings: dict[tuple, dict] = {}
 
     @staticmethod
@@ -180,8 +244,13 @@ class Autotuner:
         z = net.spikes_from_bits(inst.batch.z_rec[0].cpu().numpy().view(np.uint32), inst.spec.N)
         return float(z.mean())
 
-    def _time(self, inst: Instance, warps: int, reps: int = 3) -> float:
-        abi.snn_classifier_set_schedule(inst.cls.handle, warps)
+    @staticmethod
+    def _apply(inst: Instance, choice: tuple):
+        abi.snn_classifier_set_schedule(inst.cls.handle, choice[0])
+        abi.snn_classifier_set_row_schedule(inst.cls.handle, choice[1])
+
+    def _time(self, inst: Instance, choice: tuple, reps: int = 3) -> float:
+        self._apply(inst, choice)
         s = torch.cuda.current_stream()
         best = float("inf")
         for _ in range(reps):
@@ -199,12 +268,12 @@ class Autotuner:
     def tune(self, instances) -> dict:
         for inst in instances:
             # a sample trial at the default schedule gives the spike rate of the class
-            abi.snn_classifier_set_schedule(inst.cls.handle, 8)
-            self._time(inst, 8, reps=1)
+            self._time(inst, (8, abi.SNN_ROWS_PAIRS), reps=1)
             k = self.key(inst, self.spike_rate(inst))
             if k not in self.table:
-                times = {w: self._time(inst, w) for w in self.CANDIDATES if inst.spec.N <= 8 * 32 * w}
+                times = {(w, mode): self._time(inst, (w, mode)) for w in self.warps for mode in self.MODES
+                         if inst.spec.N <= 8 * 32 * w}
                 self.table[k] = min(times, key=times.get)
                 self.timings[k] = times
-            abi.snn_classifier_set_schedule(inst.cls.handle, self.table[k])
+            self._apply(inst, self.table[k])
         return self.table

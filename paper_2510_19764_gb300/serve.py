@@ -8,12 +8,16 @@ Adam + DEEP R step on a private copy of their model's weights.
 
 Engine.run() is the serving loop.  Each pass it
   * admits requests that have arrived, while batch slots and the memory budget allow
-    (each in-flight launch reserves the bytes of its buffers),
+    (each in-flight launch reserves the bytes of its buffers; a fine-tuning job takes a
+    pre-allocated fine-tuning slot of its model, whose byte count is known before it
+    starts),
   * groups admitted inference requests by model into one multi-trial forward launch
     (one CTA per trial, each trial stopping at its own length) on a free stream, so
     launches for different models — and new launches for a busy model — overlap on the
     device,
-  * starts admitted fine-tuning jobs on their own stream,
+  * starts admitted fine-tuning jobs on their own stream: the slot's trainable copy is
+    refreshed from the model's weights by device-to-device copies (no allocation, no
+    handle creation and no synchronisation inside the loop), then trained,
   * polls completion events and records each request's latency (arrival to result on
     the host).
 Results depend only on the request (integer spike accumulation, per-trial CTAs), so a
@@ -78,6 +82,7 @@ class Model:
     def __init__(self, mid: int, N: int, task, device="cuda", p: float = 0.1, max_batch: int = 32):
         import synth
         self.mid, self.N, self.task, self.device = mid, N, task, device
+        self.in_seed = 9003 + 7 * mid
         self.host_in = synth.random_ragged(9000 + 7 * mid, N_IN, N, p)
         self.host_rec = synth.random_ragged(9001 + 7 * mid, N, N, p, no_autapse=True)
         self.W_out, self.b = synth.dense_readout(9002 + 7 * mid, K_OUT, N)
@@ -97,6 +102,49 @@ class Model:
         cls = net.DeviceClassifier(N_IN, self.N, K_OUT, d_in, d_rec, self.W_out, self.b, self.task.thr,
                                    9003 + 7 * self.mid, net.NeuronCfg(), max_B=1, max_T=T_MAX, device=self.device)
         return cls
+
+
+class _FineTuneSlot:
+    """A model's pre-allocated fine-tuning copy: trainable ragged matrices with Adam
+    moments and DEEP R bitfields, a classifier handle and one-trial buffers of T_MAX
+    steps, plus the copy's initial contents (the model's weights with freshly initialised
+    bitfields), which refresh() restores before each job."""
+
+    def __init__(self, model: Model, device):
+        self.model = model
+        self.cls = model.private_copy()
+        self.batch = net.DeviceBatch(self.cls, [0], [1], [0], T_MAX, device=device)
+        self.h_ysum = torch.zeros((1, K_OUT), dtype=torch.float32).pin_memory()
+        self.h_lab = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.h_bin = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.h_tid = torch.zeros(1, dtype=torch.int64).pin_memory()
+        live = []
+        for r in (self.cls.w_in, self.cls.w_rec):
+            live += [r.row_len, r.ind, r.w, r.sign_bits, r.conn_bits]
+        live += [self.cls.W_out, self.cls.b_out]
+        self.live = live
+        self.init = [t.clone() for t in live]
+        self.zero = [t for r in (self.cls.w_in, self.cls.w_rec) for t in (r.m, r.v)] + \
+            [self.cls.W_out_m, self.cls.W_out_v, self.cls.b_m, self.cls.b_v]
+        tensors = live + self.init + self.zero + [getattr(self.batch, k) for k in (
+            "v", "a", "y", "ysum", "x_bits", "z_bits", "x_rec", "z_rec", "psi_rec", "d_rec", "delta", "Dout")]
+        tensors += [r.grad for r in (self.cls.w_in, self.cls.w_rec)] + [self.cls.G_out, self.cls.G_b]
+        self.bytes = sum(t.numel() * t.element_size() for t in tensors)
+        self.busy = False
+
+    def refresh(self, stream):
+        with torch.cuda.stream(stream):
+            for dst, src in zip(self.live, self.init):
+                dst.copy_(src, non_blocking=True)
+            for t in self.zero:
+                t.zero_()
+
+
+class _BatchView:
+    """A DeviceBatch descriptor with its own step count (what train_batch reads)."""
+
+    def __init__(self, desc, T: int):
+        self.desc, self.T = desc, T
 
 
 class _Slot:
@@ -133,10 +181,12 @@ class _Flight:
 
 class Engine:
     def __init__(self, models: list[Model], max_batch: int = 32, slots_per_model: int = 2, n_streams: int = 8,
-                 mem_budget: int = 8 << 30, max_finetune: int = 4, device="cuda"):
+                 mem_budget: int = 8 << 30, max_finetune: int = 4, device="cuda", ft_slots_per_model: int = 2):
         self.models = models
         self.max_batch = max_batch
         self.slots = {m.mid: [_Slot(m, max_batch, device) for _ in range(slots_per_model)] for m in models}
+        # fine-tuning copies are created here, once: run() allocates nothing
+        self.ft_slots = {m.mid: [_FineTuneSlot(m, device) for _ in range(ft_slots_per_model)] for m in models}
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.mem_budget = mem_budget
         self.max_finetune = max_finetune
@@ -167,18 +217,26 @@ class Engine:
         slot.busy = True
         return _Flight("infer", reqs, ev, stream, slot=slot, h_ysum=slot.h_ysum, bytes=slot.bytes)
 
-    def _launch_finetune(self, r: Request, stream) -> _Flight:
-        m = self.models[r.model]
-        cls = m.private_copy()
-        batch = net.DeviceBatch(cls, [r.label], [r.bin_len], [r.rid], r.T, device=self.device)
-        h_ysum = torch.zeros((1, K_OUT), dtype=torch.float32).pin_memory()
-        net.train_batch(cls, batch, net.adam_params(1e-3, 1, l1=1e-5), r.rid, stream=stream)
+    def _launch_finetune(self, slot: _FineTuneSlot, r: Request, stream) -> _Flight:
+        slot.refresh(stream)
+        slot.h_lab[0], slot.h_bin[0], slot.h_tid[0] = r.label, r.bin_len, r.rid
+        bt = slot.batch
         with torch.cuda.stream(stream):
-            h_ysum.copy_(batch.ysum, non_blocking=True)
+            bt.labels.copy_(slot.h_lab, non_blocking=True)
+            bt.bin_len.copy_(slot.h_bin, non_blocking=True)
+            bt.trial_ids.copy_(slot.h_tid, non_blocking=True)
+            for t in (bt.v, bt.a, bt.y, bt.ysum, bt.x_bits, bt.z_bits):
+                t.zero_()
+        desc = abi.Batch.from_buffer_copy(bt.desc)
+        desc.T = r.T                       # one trial: its records are the first T rows of the buffers
+        view = _BatchView(desc, r.T)
+        net.train_batch(slot.cls, view, net.adam_params(1e-3, 1, l1=1e-5), r.rid, stream=stream)
+        with torch.cuda.stream(stream):
+            slot.h_ysum.copy_(bt.ysum, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
-        nbytes = sum(t.numel() * t.element_size() for t in (batch.psi_rec, batch.delta, cls.w_in.w, cls.w_rec.w)) * 3
-        return _Flight("finetune", [r], ev, stream, cls=cls, batch=batch, h_ysum=h_ysum, bytes=nbytes)
+        slot.busy = True
+        return _Flight("finetune", [r], ev, stream, slot=slot, h_ysum=slot.h_ysum, bytes=slot.bytes)
 
     # --- serving loops ------------------------------------------------------
     def run(self, requests: list[Request], realtime: bool = True) -> list[Result]:
@@ -220,8 +278,9 @@ class Engine:
                 by_model: dict[int, list[Request]] = {}
                 for r in pending:
                     if r.finetune:
-                        if n_ft < self.max_finetune and used + (64 << 20) <= self.mem_budget:
-                            f = self._launch_finetune(r, self.streams[si % len(self.streams)])
+                        slot = next((x for x in self.ft_slots[r.model] if not x.busy), None)
+                        if slot is not None and n_ft < self.max_finetune and used + slot.bytes <= self.mem_budget:
+                            f = self._launch_finetune(slot, r, self.streams[si % len(self.streams)])
                             si += 1
                             n_ft += 1
                             used += f.bytes
@@ -247,7 +306,8 @@ class Engine:
                 pending = rest
                 if pending and not flights:
                     # nothing in flight will free a slot or memory: these requests can never start
-                    need = max((64 << 20) if r.finetune else self.slots[r.model][0].bytes for r in pending)
+                    need = max(self.ft_slots[r.model][0].bytes if r.finetune else self.slots[r.model][0].bytes
+                               for r in pending)
                     raise AdmissionError(f"{len(pending)} request(s) cannot be admitted: one needs {need} bytes "
                                          f"of device memory, the budget is {self.mem_budget} bytes")
             self.stats["max_in_flight"] = max(self.stats["max_in_flight"], len(flights))
@@ -268,7 +328,7 @@ class Engine:
                 if wait > 0:
                     time.sleep(wait)
             if r.finetune:
-                f = self._launch_finetune(r, stream)
+                f = self._launch_finetune(self.ft_slots[r.model][0], r, stream)
             else:
                 slot = self.slots[r.model][0]
                 f = self._launch_infer(slot, [r], stream)

@@ -65,3 +65,28 @@ def classifier(seed=0, n_in=32, N=64, K=4, p_in=0.1, p_rec=0.1, lif=True, v_thr=
 
 def oracle_bitfields(rag: synth.Ragged, Q: int, seed: int):
     return od.init_bitfields(rag.row_len, rag.ind, rag.w, Q, seed)
+
+
+_POOL = None
+
+
+def oracle_pool(n: int = 8):
+    """Process pool for oracle trials (spawned processes: they never touch the GPU)."""
+    global _POOL
+    if _POOL is None:
+        import multiprocessing as mp
+        import os
+        _POOL = mp.get_context("spawn").Pool(max(1, min(n, (os.cpu_count() or 2) - 1)))
+    return _POOL
+
+
+def oracle_trial(args):
+    """Pool worker: one trial's forward and e-prop gradients in the oracle.  args =
+    (ClassifierNet constructor arrays, neuron params, thresholds, label, bin_len,
+    trial id, input seed, T).  Returns (z raster uint8 [T, N], prediction, ysum,
+    (G_in, G_rec, G_out, G_b))."""
+    arrays, neuron, thr, label, bin_len, trial_id, seed, T = args
+    net = oc.ClassifierNet(*arrays, neuron)
+    r = oc.forward_trial(net, thr, label, bin_len, trial_id, seed, T)
+    g = oc.eprop_gradients(net, r["x"], r["z"], r["psi"], r["d"])
+    return r["z"].astype(np.uint8), r["pred"], r["ysum"], g

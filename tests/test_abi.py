@@ -59,7 +59,10 @@ def test_argument_errors_are_synchronous_and_need_no_gpu(lib_path):
                  lambda: abi.snn_ragged_set_deepr_guide(None, abi.DeeprGuide()),
                  lambda: abi.snn_ragged_add_row(None, None),
                  lambda: abi.snn_ragged_remove_row(None, None),
-                 lambda: abi.snn_test_wait_timeout(None, False, 16)):
+                 lambda: abi.snn_test_wait_timeout(None, False, 16),
+                 lambda: abi.snn_multi_run(None),
+                 lambda: abi.snn_multi_post(None, [0]),
+                 lambda: abi.snn_classifier_set_row_schedule(None, 0)):
         with pytest.raises(abi.SnnError) as e:
             call()
         assert e.value.status == abi.SNN_EINVAL
@@ -68,7 +71,7 @@ def test_argument_errors_are_synchronous_and_need_no_gpu(lib_path):
 _STRUCTS = {"RaggedDesc": "snn_ragged_desc", "RewireStats": "snn_rewire_stats", "Adam": "snn_adam",
             "ClassifierDesc": "snn_classifier_desc", "Batch": "snn_batch", "TopoParams": "snn_topo_params",
             "TopoRewire": "snn_topo_rewire", "TopoState": "snn_topo_state", "DeeprGuide": "snn_deepr_guide",
-            "TopoDerived": "snn_topo_derived"}
+            "TopoDerived": "snn_topo_derived", "MultiInstance": "snn_multi_instance"}
 
 
 def test_struct_layouts_match_header(tmp_path):

@@ -64,3 +64,28 @@ def test_admission_failure_is_reported_not_hung():
     res = eng.run(reqs, realtime=False)
     assert [r.rid for r in res] == list(range(len(reqs)))
     assert eng.stats["max_in_flight"] == 1
+
+
+def test_serving_loop_allocates_nothing_and_admits_finetunes_by_their_bytes():
+    """Fine-tuning copies are created with the engine: run() makes no device allocation
+    (torch's allocator counts none) and admits a fine-tuning job by the exact byte count
+    of its model's copy; a budget below that count is refused at once."""
+    from paper_2510_19764_gb300 import serve
+    task = synth.spoken_digit_task(5, n_in=serve.N_IN, n_classes=serve.N_CLASSES, T=serve.T_MAX, n_bins=serve.N_BINS)
+    models = [serve.Model(0, 128, task, max_batch=8), serve.Model(1, 64, task, max_batch=8)]
+    reqs = serve.poisson_requests(40, 1000.0, len(models), seed=8, finetune_frac=0.3, t_range=(20, 100))
+    assert sum(r.finetune for r in reqs) >= 5
+    eng = serve.Engine(models, max_batch=8, slots_per_model=2, n_streams=4, ft_slots_per_model=2)
+    eng.run(reqs[:4], realtime=False)                       # first calls outside the count
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_stats()["allocation.all.allocated"]
+    res = eng.run(reqs, realtime=False)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == before
+    assert len(res) == len(reqs)
+    ft = eng.ft_slots[0][0]
+    assert ft.bytes > eng.slots[0][0].bytes
+    eng.mem_budget = ft.bytes - 1
+    with pytest.raises(serve.AdmissionError) as e:
+        eng.run([r for r in reqs if r.finetune and r.model == 0][:1], realtime=False)
+    assert str(ft.bytes) in str(e.value)
