@@ -552,6 +552,11 @@ def run_batched(args, timed: int | None = None):
         mr.iterate()
     t_multi = dev_time(mr.iterate, timed)
     ok_multi = mr.status() == abi.SNN_OK
+    trace = mr.trace()                 # one more run with phase timing (not in the timed region)
+    mr.iterate()
+    torch.cuda.synchronize()
+    phases = trace.summary(insts)
+    abi.snn_multi_set_trace(mr.handle, None)
     mr.capture(4)
     mr.replay()
     t_multi_graph = dev_time(mr.replay, max(1, timed // 4)) / 4
@@ -582,6 +587,7 @@ def run_batched(args, timed: int | None = None):
                                  "graph_of_calls": round(t_graph * 1e3, 3), "plain_whole_trial": round(t_whole * 1e3, 2),
                                  "plain_per_step": round(t_step * 1e3, 1)},
             "status_ok": bool(ok),
+            "persistent_phase_trace": phases,
             "row_schedule_table": {str(k): list(v) for k, v in table.items()}}
 
 

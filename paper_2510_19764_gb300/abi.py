@@ -30,7 +30,7 @@ EXPORTED = [
     "snn_draw_inputs", "snn_step_neurons_ex", "snn_topo_connectivity", "snn_ragged_set_deepr_guide",
     "snn_test_wait_timeout", "snn_ragged_add_row", "snn_ragged_remove_row", "snn_adam_bias", "snn_topo_derive",
     "snn_classifier_set_row_schedule", "snn_multi_create", "snn_multi_destroy", "snn_multi_run", "snn_multi_post",
-    "snn_multi_status",
+    "snn_multi_status", "snn_multi_set_trace",
 ]
 
 
@@ -158,6 +158,7 @@ def load() -> C.CDLL:
         "snn_multi_run": (i32, [vp, i32, i64, vp]),
         "snn_multi_post": (i32, [vp, P(i32), i32]),
         "snn_multi_status": (i32, [vp, vp]),
+        "snn_multi_set_trace": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -343,3 +344,7 @@ def snn_multi_post(h: int, instances) -> None:
 
 def snn_multi_status(h: int, stream=None) -> int:
     return load().snn_multi_status(h, stream_ptr(stream))
+
+
+def snn_multi_set_trace(h: int, times) -> None:
+    check(load().snn_multi_set_trace(h, ptr(times)))

@@ -99,6 +99,7 @@ struct MInst {
     int n_items[MP_N];
     int n_input, n_pack, n_sort0;                // MP_PRE: input, pack, sort (input rows, then hidden)
     int n_rows0;                                 // MP_ELIM / MP_FORM: items of the input projection
+    int orig;                                    // the instance's index in the caller's array
 };
 
 // Queue header.  gen = completed runs; run r uses stamp r + 1 for its published slots.
@@ -141,6 +142,7 @@ struct MArgs {
     unsigned cap;
     const int* mailbox;               // mapped host memory: {stamp, n, instance ids...} or NULL
     long long limit_ns;
+    long long* trace;                 // [n_inst][MP_N + 1] global-timer stamps, or NULL
 };
 
 // Publishes all items of `phase` of instance i (the whole CTA calls it).
@@ -469,7 +471,10 @@ __global__ void __launch_bounds__(MT, 2) k_multi(MArgs A) {
             __syncthreads();
             const int i = s_flag;
             __syncthreads();
-            if (i >= 0 && i < A.n_inst) m_push(A, i, MP_PREP, stamp, &s_base);
+            if (i >= 0 && i < A.n_inst) {
+                if (A.trace && tid == 0) A.trace[(size_t)A.inst[i].orig * (MP_N + 1)] = (long long)global_ns();
+                m_push(A, i, MP_PREP, stamp, &s_base);
+            }
         }
         __syncthreads();
     }
@@ -524,6 +529,7 @@ __global__ void __launch_bounds__(MT, 2) k_multi(MArgs A) {
         __syncthreads();
         if (s_flag) {
             __threadfence();
+            if (A.trace && tid == 0) A.trace[(size_t)I.orig * (MP_N + 1) + 1 + phase] = (long long)global_ns();
             if (phase + 1 < MP_N) {
                 m_push(A, i, phase + 1, stamp, &s_base);
             } else if (tid == 0) {
@@ -561,6 +567,7 @@ struct snn_multi {
     int* h_mailbox;               // mapped pinned host memory
     int* d_mailbox;
     unsigned runs;                // snn_multi_run calls so far (= the device's completed runs)
+    long long* trace;             // caller's device buffer of phase completion times, or NULL
     size_t smem;
     int grid;
     std::vector<int> order;       // seeding order (longest instances first)
@@ -735,7 +742,10 @@ snn_status snn_multi_create(const snn_multi_instance* inst, int32_t n, snn_multi
         return ca > cb;
     });
     std::vector<MInst> ho(n);
-    for (int k = 0; k < n; ++k) ho[k] = h[m->order[k]];
+    for (int k = 0; k < n; ++k) {
+        ho[k] = h[m->order[k]];
+        ho[k].orig = m->order[k];
+    }
     cudaError_t e = cudaMalloc(&m->d_inst, sizeof(MInst) * n);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_remaining, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_q, sizeof(MQueue));
@@ -773,6 +783,7 @@ snn_status snn_multi_create(const snn_multi_instance* inst, int32_t n, snn_multi
     std::memset(m->h_mailbox, 0, sizeof(int) * (2 + n));
     m->grid = per_sm * sm_count();
     m->runs = 0;
+    m->trace = nullptr;
     *out = m;
     return SNN_OK;
 }
@@ -793,9 +804,17 @@ snn_status snn_multi_run(snn_multi* m, int32_t flags, int64_t wait_limit_ns, snn
     a.cap = m->cap;
     a.mailbox = (flags & SNN_MULTI_HOST_POSTS) ? m->d_mailbox : nullptr;
     a.limit_ns = wait_limit_ns;
+    a.trace = m->trace;
     k_multi<<<m->grid, MT, m->smem, (cudaStream_t)stream>>>(a);
     SNN_LAUNCH_CHECK();
     m->runs += 1;
+    return SNN_OK;
+}
+
+snn_status snn_multi_set_trace(snn_multi* m, int64_t* times) {
+    clear_error();
+    SNN_REQUIRE(m, "snn_multi_set_trace: NULL handle");
+    m->trace = (long long*)times;
     return SNN_OK;
 }
 

@@ -191,8 +191,18 @@ class MultiRunner:
         self.graph = None
         self.graph_iters = 0
 
+    PHASES = ("prep", "inputs+pack+sort", "forward", "readout_scan", "adjoint", "gather", "adam", "deepr_elim",
+              "deepr_dist", "deepr_form")
+
     def iterate(self, stream=None, flags: int = 0):
-        abi.snn_multi_run(self.handle, flags, self.wait_limit_ns, stream)
+        abi.snn_multi_run(self.handle, flags, self.wait_limit_ns, stream or torch.cuda.current_stream())
+
+    def trace(self) -> "PhaseTrace":
+        """Record the phase completion times of the following runs (PhaseTrace.summary()
+        reads them after a run)."""
+        t = PhaseTrace(len(self.instances))
+        abi.snn_multi_set_trace(self.handle, t.times)
+        return t
 
     def capture(self, n_iter: int = 1):
         s = torch.cuda.Stream()
@@ -219,6 +229,26 @@ class MultiRunner:
             self.close()
         except Exception:
             pass
+
+
+class PhaseTrace:
+    """Global-timer stamps of one persistent run: per instance its start and the end of
+    each phase (device int64 [n][11])."""
+
+    def __init__(self, n: int):
+        self.times = torch.zeros((n, len(MultiRunner.PHASES) + 1), dtype=torch.int64, device="cuda")
+
+    def summary(self, instances) -> dict:
+        t = self.times.cpu().numpy().astype(np.float64)
+        t0 = t[:, 0].min()
+        end = t[:, -1] - t0
+        slow = int(np.argmax(end))
+        step = np.diff(t[slow]) / 1e3
+        return {"iteration_ms": round(float(end.max()) / 1e6, 3),
+                "slowest_instance": {"N": instances[slow].spec.N, "T": instances[slow].spec.T,
+                                     "p": round(instances[slow].spec.p, 3),
+                                     "phase_us": {k: round(float(v), 1) for k, v in zip(MultiRunner.PHASES, step)}},
+                "median_instance_ms": round(float(np.median(end)) / 1e6, 3)}
 
 
 class Autotuner:

@@ -29,69 +29,126 @@ def _arrays(n, st, W, b):
     return (n.n_in, n.N, n.K, st["in"][0], st["in"][1], st["in"][2], st["rec"][0], st["rec"][1], st["rec"][2], W, b)
 
 
+def _oracle_update(st, sign, conn, W, b, mom, G, i, lr, l1, seeds, N):
+    """L1 + Adam on both projections and the readout, then DEEP R (rewire index i)."""
+    b1t, b2t = oc.adam_bias(0.9, i + 1), oc.adam_bias(0.999, i + 1)
+    post = {}
+    for name, Gm in (("in", G[0]), ("rec", G[1])):
+        rl, ind, w, m, v = st[name]
+        Gl = oc.l1_on_sign(Gm, rl, ind, sign[name], l1)
+        w, m, v = oc.adam_ragged(w, m, v, Gl, rl, lr, b1t, b2t)
+        post[name] = (w, m, v)
+        out = od.rewire(rl, ind, w, m, v, sign[name], conn[name], w.shape[1], N, name == "rec", seeds[name], i)
+        st[name] = [out["row_len"], out["ind"], out["w"], out["m"], out["v"]]
+        conn[name] = out["conn"]
+    W, mom[0], mom[1] = oc.adam(W, mom[0], mom[1], G[2], lr, b1t, b2t)
+    b, mom[2], mom[3] = oc.adam(b, mom[2], mom[3], G[3], lr, b1t, b2t)
+    return W, b, post
+
+
 @pytest.mark.parametrize("dtype", [F32, F64])
 def test_training_run_reduced_classifier(dtype):
     """700 inputs -> 128 ALIF -> 20 readouts, 10 %, 400 steps, batch 8, 20 batches of
-    e-prop + L1 + Adam + DEEP R, against the FP64 oracle trained from the same start
-    (its trials in parallel processes, gradients summed in trial order).  FP32: >= 99.9 %
-    of spikes agree over all 160 trials and the accuracy is within 0.5 points; FP64:
-    every raster and the final connectivity are the oracle's."""
+    e-prop + L1 + Adam + DEEP R.
+
+    FP64: the oracle trained from the same start on its own (its trials in parallel
+    processes, gradients summed in trial order) gives every raster, every prediction and
+    the final connectivity exactly.
+
+    FP32: judged batch by batch from the GPU's own state (the oracle takes the GPU's
+    weights, moments and connectivity before each batch): >= 99.9 % of all spikes of the
+    run agree, the accuracy over the run is within 0.5 points, each batch's gradient
+    agrees with the oracle's within the gradient tolerance, L1 + Adam from the GPU's
+    gradient within FP32 rounding, and DEEP R from the GPU's post-Adam state bit-exactly.
+    (Adam's first steps divide by |g|, so gradients near its eps would magnify the FP32
+    gradient error; the update is compared from the same gradient, as for a single step.)
+    (Trained on its own, the FP64 oracle drifts from the FP32 run once a sign test or a
+    threshold crossing is decided differently by rounding: in the measured run, all
+    spikes agreed for 10 batches, then agreement fell to ~92 %; every step from the same
+    state agreed.)"""
     from paper_2510_19764_gb300 import abi, net
     T, B, n_batches, lr, l1 = 400, 8, 20, 1e-3, 1e-5
     s = _setups.classifier(seed=5, n_in=700, N=128, K=20, lif=False, v_thr=0.6, T=T, n_classes=20, n_bins=10,
                            spoken=True, max_B=B, dtype=dtype)
     batches = [synth.trial_batch(s.task, 5, i, B) for i in range(n_batches)]
     batch = net.DeviceBatch(s.dev, batches[0].labels, batches[0].bin_len, batches[0].trial_ids, T)
-    g_rasters, g_preds = [], []
-    for i, tb in enumerate(batches):
-        batch.set_trials(tb.labels, tb.bin_len, tb.trial_ids)
-        net.train_batch(s.dev, batch, net.adam_params(lr, i + 1, l1=l1), i)
-        torch.cuda.synchronize()
-        z = net.spikes_from_bits(net.u32_to_numpy(batch.z_rec), 128)
-        g_rasters += [z[k].astype(np.uint8) for k in range(B)]
-        g_preds += list(np.argmax(batch.ysum.double().cpu().numpy(), axis=1))
-    assert s.dev.w_in.status() == abi.SNN_OK and s.dev.w_rec.status() == abi.SNN_OK
-    # oracle run
-    n = s.onet
-    seeds = {"in": s.dev.w_in.desc.seed, "rec": s.dev.w_rec.desc.seed}
+    n, pool, dev = s.onet, _setups.oracle_pool(), s.dev
+    seeds = {"in": dev.w_in.desc.seed, "rec": dev.w_rec.desc.seed}
     st = {"in": [n.in_len.copy(), n.in_ind.copy(), n.w_in.copy(), 0 * n.w_in, 0 * n.w_in],
           "rec": [n.rec_len.copy(), n.rec_ind.copy(), n.w_rec.copy(), 0 * n.w_rec, 0 * n.w_rec]}
     sign, conn = {}, {}
     for name, (rl, ind, w) in (("in", (n.in_len, n.in_ind, n.w_in)), ("rec", (n.rec_len, n.rec_ind, n.w_rec))):
         sign[name], conn[name] = od.init_bitfields(rl, ind, w, n.N, seeds[name])
     W, b = n.W_out.copy(), n.b_out.copy()
-    mW, vW, mb, vb = 0 * W, 0 * W, 0 * b, 0 * b
-    o_rasters, o_preds = [], []
-    pool = _setups.oracle_pool()
+    mom = [0 * W, 0 * W, 0 * b, 0 * b]
+    agree, total_spikes, g_preds, o_preds, rewired = [], 0, [], [], 0
     for i, tb in enumerate(batches):
+        if dtype == F32:            # the oracle starts the batch from the GPU's state
+            for name, d in (("in", dev.w_in), ("rec", dev.w_rec)):
+                h = d.host()
+                st[name] = [h["row_len"], h["ind"], h["w"], h["m"], h["v"]]
+                conn[name] = h["conn_bits"]
+            W, b = dev.W_out.double().cpu().numpy(), dev.b_out.double().cpu().numpy()
+            mom = [t.double().cpu().numpy() for t in (dev.W_out_m, dev.W_out_v, dev.b_m, dev.b_v)]
+        batch.set_trials(tb.labels, tb.bin_len, tb.trial_ids)
+        abi.snn_step_neurons(dev.handle, batch.desc, 0, T)
+        abi.snn_eprop_update(dev.handle, batch.desc, abi.SNN_EPROP_GRAD, None)
+        abi.snn_eprop_update(dev.handle, batch.desc, abi.SNN_EPROP_APPLY, net.adam_params(lr, i + 1, l1=l1))
+        torch.cuda.synchronize()
+        g_post = {name: d.host() for name, d in (("in", dev.w_in), ("rec", dev.w_rec))}
+        stats = torch.zeros((2, 4), dtype=torch.int64, device="cuda")
+        abi.snn_rewire_deepr(dev.w_in.handle, i, stats[0])
+        abi.snn_rewire_deepr(dev.w_rec.handle, i, stats[1])
+        torch.cuda.synchronize()
+        rewired += int(stats[:, 0].sum())
+        z = net.spikes_from_bits(net.u32_to_numpy(batch.z_rec), 128).astype(np.uint8)
+        g_preds += list(np.argmax(batch.ysum.double().cpu().numpy(), axis=1))
         arrays = _arrays(n, st, W, b)
         jobs = [(arrays, n.neuron, s.task.thr, tb.labels[k], tb.bin_len[k], tb.trial_ids[k], s.in_seed, T)
                 for k in range(B)]
-        res = pool.map(_setups.oracle_trial, jobs)
         G = [0, 0, 0, 0]
-        for z, pred, _, g in res:
-            o_rasters.append(z)
+        for k, (zo, pred, _, g) in enumerate(pool.map(_setups.oracle_trial, jobs)):
             o_preds.append(pred)
             G = [a + c for a, c in zip(G, g)]
-        b1t, b2t = oc.adam_bias(0.9, i + 1), oc.adam_bias(0.999, i + 1)
-        for name, Gm in (("in", G[0]), ("rec", G[1])):
-            rl, ind, w, m, v = st[name]
-            Gl = oc.l1_on_sign(Gm, rl, ind, sign[name], l1)
-            w, m, v = oc.adam_ragged(w, m, v, Gl, rl, lr, b1t, b2t)
-            out = od.rewire(rl, ind, w, m, v, sign[name], conn[name], w.shape[1], n.N, name == "rec", seeds[name], i)
-            st[name] = [out["row_len"], out["ind"], out["w"], out["m"], out["v"]]
-            conn[name] = out["conn"]
-        W, mW, vW = oc.adam(W, mW, vW, G[2], lr, b1t, b2t)
-        b, mb, vb = oc.adam(b, mb, vb, G[3], lr, b1t, b2t)
-    spikes = sum(int(r.sum()) for r in o_rasters)
-    assert spikes > 1000
+            total_spikes += int(zo.sum())
+            if dtype == F64:
+                np.testing.assert_array_equal(z[k], zo, err_msg=f"batch {i} trial {k}")
+            agree.append((z[k] == zo).ravel())
+        pre_w = {name: [a.copy() for a in st[name]] for name in ("in", "rec")}
+        W, b, post = _oracle_update(st, sign, conn, W, b, mom, G, i, lr, l1, seeds, n.N)
+        for k_, (name, d) in enumerate((("in", dev.w_in), ("rec", dev.w_rec))):
+            live = np.arange(d.C)[None] < g_post[name]["row_len"][:, None]
+            if dtype == F32:
+                # the batch's gradient (summed over its trials) against the oracle's
+                Gg, Go = g_post[name]["grad"][live], G[k_][live]
+                gmax = np.abs(Go).max()
+                assert np.all(np.abs(Gg - Go) <= 2e-5 * np.maximum(np.abs(Go), 1e-3 * gmax) + 1e-6 * gmax)
+                # L1 + Adam from the GPU's own gradient: FP32 rounding of the FP64 update
+                rl, ind, w0, m0, v0 = pre_w[name]
+                Gl = oc.l1_on_sign(g_post[name]["grad"], rl, ind, sign[name], l1)
+                w1, _, _ = oc.adam_ragged(w0, m0, v0, Gl, rl, lr, oc.adam_bias(0.9, i + 1), oc.adam_bias(0.999, i + 1))
+                np.testing.assert_allclose(g_post[name]["w"][live], w1[live], rtol=1e-6, atol=1e-7)
+                # DEEP R from the GPU's own post-Adam state: bit-exact
+                h = g_post[name]
+                out = od.rewire(h["row_len"], h["ind"], h["w"], h["m"], h["v"], h["sign_bits"], h["conn_bits"], d.C,
+                                n.N, name == "rec", seeds[name], i)
+                got = d.host()
+                np.testing.assert_array_equal(got["row_len"], out["row_len"])
+                live2 = np.arange(d.C)[None] < out["row_len"][:, None]
+                np.testing.assert_array_equal(got["ind"][live2], out["ind"][live2])
+                np.testing.assert_array_equal(got["w"][live2], out["w"][live2])
+                np.testing.assert_array_equal(got["conn_bits"], out["conn"])
+    assert dev.w_in.status() == abi.SNN_OK and dev.w_rec.status() == abi.SNN_OK
+    assert total_spikes > 1000 and rewired > 0
     labels = np.concatenate([tb.labels for tb in batches])
     acc_g = np.mean(np.array(g_preds) == labels)
     acc_o = np.mean(np.array(o_preds) == labels)
+    frac = float(np.mean(np.concatenate(agree)))
+    assert frac >= 0.999, frac
+    assert abs(acc_g - acc_o) <= 0.005 + 1e-12, (acc_g, acc_o)
     if dtype == F64:
-        for k, (gr, r) in enumerate(zip(g_rasters, o_rasters)):
-            np.testing.assert_array_equal(gr, r, err_msg=f"trial {k}")
-        for name, d in (("in", s.dev.w_in), ("rec", s.dev.w_rec)):
+        assert g_preds == o_preds
+        for name, d in (("in", dev.w_in), ("rec", dev.w_rec)):
             h = d.host()
             rl = st[name][0]
             np.testing.assert_array_equal(h["row_len"], rl)
@@ -99,11 +156,6 @@ def test_training_run_reduced_classifier(dtype):
             np.testing.assert_array_equal(h["ind"][mask], st[name][1][mask])
             np.testing.assert_allclose(h["w"][mask], st[name][2][mask], rtol=1e-9, atol=1e-12)
             np.testing.assert_array_equal(h["conn_bits"], conn[name])
-        assert g_preds == o_preds
-    else:
-        agree = np.mean(np.concatenate([(gr == r).ravel() for gr, r in zip(g_rasters, o_rasters)]))
-        assert agree >= 0.999, agree
-    assert abs(acc_g - acc_o) <= 0.005 + 1e-12, (acc_g, acc_o)
 
 
 def test_batched_instance_at_largest_shape():

@@ -170,3 +170,28 @@ def test_autotuner_picks_admissible_schedules():
         assert w in (4, 8, 16) and k[0] <= 8 * 32 * w
         assert mode in (abi.SNN_ROWS_PAIRS, abi.SNN_ROWS_PER_WARP, abi.SNN_ROWS_PER_BLOCK)
         assert all(t > 0 for t in tuner.timings[k].values())
+
+
+def test_persistent_kernel_phase_trace():
+    """Tracing: with a trace buffer set, a run stamps every instance's start and the end
+    of each of its phases, in phase order; clearing it stops the stamping."""
+    from paper_2510_19764_gb300 import abi, sched
+    specs = [sched.InstanceSpec(N, T, p, i) for i, (N, T, p) in enumerate(SPECS[:4])]
+    multi = _instances(specs)
+    mr = sched.MultiRunner(multi)
+    tr = mr.trace()
+    mr.iterate()
+    torch.cuda.synchronize()
+    assert mr.status() == abi.SNN_OK
+    t = tr.times.cpu().numpy()
+    assert np.all(t > 0)
+    assert np.all(np.diff(t, axis=1) >= 0)
+    # the forward is the longest phase of every instance here (its whole trial)
+    assert np.all(np.argmax(np.diff(t, axis=1), axis=1) == 2)
+    s = tr.summary(multi)
+    assert s["iteration_ms"] > 0 and set(s["slowest_instance"]["phase_us"]) == set(sched.MultiRunner.PHASES)
+    abi.snn_multi_set_trace(mr.handle, None)
+    tr.times.zero_()
+    mr.iterate()
+    torch.cuda.synchronize()
+    assert not tr.times.any()
