@@ -414,7 +414,7 @@ __device__ void m_form(const MInst& I, int k, unsigned char* smem) {
 }
 
 // ---------------------------------------------------------------- the persistent kernel
-__global__ void __launch_bounds__(MT, 2) k_multi(MArgs A) {
+__global__ void __launch_bounds__(MT, 1) k_multi(MArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_item;
     __shared__ int s_flag;

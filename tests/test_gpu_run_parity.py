@@ -122,7 +122,9 @@ def test_training_run_reduced_classifier(dtype):
                 # the batch's gradient (summed over its trials) against the oracle's
                 Gg, Go = g_post[name]["grad"][live], G[k_][live]
                 gmax = np.abs(Go).max()
-                assert np.all(np.abs(Gg - Go) <= 2e-5 * np.maximum(np.abs(Go), 1e-3 * gmax) + 1e-6 * gmax)
+                bound = 2e-5 * np.maximum(np.abs(Go), 1e-3 * gmax) + 1e-6 * gmax
+                worst = int(np.argmax(np.abs(Gg - Go) / bound))
+                assert np.all(np.abs(Gg - Go) <= bound), (i, name, Gg[worst], Go[worst], gmax)
                 # L1 + Adam from the GPU's own gradient: FP32 rounding of the FP64 update
                 rl, ind, w0, m0, v0 = pre_w[name]
                 Gl = oc.l1_on_sign(g_post[name]["grad"], rl, ind, sign[name], l1)
