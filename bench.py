@@ -528,7 +528,7 @@ def run_batched(args, timed: int | None = None):
     task = synth.spoken_digit_task(args.seed, n_in=sched.N_IN, n_classes=sched.N_CLASSES, T=1000,
                                    n_bins=sched.N_BINS)
     insts = [sched.Instance(s, task) for s in specs]
-    tuner = sched.Autotuner(warps=(8,))
+    tuner = sched.Autotuner(target="multi")
     table = tuner.tune(insts)
 
     def dev_time(fn, n):
@@ -589,7 +589,8 @@ def run_batched(args, timed: int | None = None):
                                  "plain_per_step": round(t_step * 1e3, 1)},
             "status_ok": bool(ok),
             "persistent_phase_trace": phases,
-            "row_schedule_table": {str(k): list(v) for k, v in table.items()}}
+            "row_schedule_table": {str(k): list(v) for k, v in table.items()},
+            "row_schedule_ms": {str(k): {str(m[1]): round(t, 3) for m, t in v.items()} for k, v in tuner.timings.items()}}
 
 
 def run_serve(args, quick: bool = False):

@@ -315,13 +315,18 @@ snn_status snn_create_classifier(const snn_classifier_desc* desc, snn_classifier
  * accumulation); an autotuner picks it per (N, row length, spike rate). */
 snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_trial);
 /* How the warps of a trial share the spiking rows of a step (results do not depend on
- * it): SNN_ROWS_PAIRS (default) a warp per row, two rows in flight per warp;
- * SNN_ROWS_PER_WARP a warp per row, one row at a time (many short rows);
- * SNN_ROWS_PER_BLOCK all warps on each row, a 32-slot chunk each (few long rows).  Used
- * by snn_step_neurons and by the persistent multi-instance kernel (snn_multi_run). */
+ * it): SNN_ROWS_PAIRS (default) a warp per row, two rows in flight per warp, 128 slots
+ * of each per round trip; SNN_ROWS_PER_WARP one row at a time; SNN_ROWS_PER_BLOCK all
+ * warps on each row, a 32-slot chunk each; SNN_ROWS_WIDE two rows, 256 slots of each per
+ * round trip (long rows); SNN_ROWS_QUAD four rows, 128 slots each.  The last two keep 16
+ * loads per thread in flight and exist in the persistent multi-instance kernel only
+ * (its CTAs have the registers): snn_step_neurons runs them as SNN_ROWS_PAIRS.  The
+ * persistent kernel reads the mode when its plan is created (snn_multi_create). */
 #define SNN_ROWS_PAIRS     0
 #define SNN_ROWS_PER_WARP  1
 #define SNN_ROWS_PER_BLOCK 2
+#define SNN_ROWS_WIDE      3
+#define SNN_ROWS_QUAD      4
 snn_status snn_classifier_set_row_schedule(snn_classifier* c, int32_t mode);
 snn_status snn_destroy_classifier(snn_classifier* c);
 

@@ -19,7 +19,7 @@ SNN_F32, SNN_F64 = 0, 1
 SNN_EPROP_GRAD, SNN_EPROP_APPLY = 0, 1
 SNN_FIXED_FRAC_BITS = 40
 SNN_STEP_INPUTS_READY = 1
-SNN_ROWS_PAIRS, SNN_ROWS_PER_WARP, SNN_ROWS_PER_BLOCK = 0, 1, 2
+SNN_ROWS_PAIRS, SNN_ROWS_PER_WARP, SNN_ROWS_PER_BLOCK, SNN_ROWS_WIDE, SNN_ROWS_QUAD = 0, 1, 2, 3, 4
 SNN_MULTI_HOST_POSTS = 1
 
 EXPORTED = [

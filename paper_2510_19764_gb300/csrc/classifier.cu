@@ -666,8 +666,8 @@ snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_tria
 snn_status snn_classifier_set_row_schedule(snn_classifier* c, int32_t mode) {
     clear_error();
     SNN_REQUIRE(c, "snn_classifier_set_row_schedule: NULL classifier");
-    SNN_REQUIRE(mode == SNN_ROWS_PAIRS || mode == SNN_ROWS_PER_WARP || mode == SNN_ROWS_PER_BLOCK,
-                "snn_classifier_set_row_schedule: unknown mode %d", mode);
+    SNN_REQUIRE(mode >= SNN_ROWS_PAIRS && mode <= SNN_ROWS_QUAD, "snn_classifier_set_row_schedule: unknown mode %d",
+                mode);
     c->row_sched = mode;
     return SNN_OK;
 }

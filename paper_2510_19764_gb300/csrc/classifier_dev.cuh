@@ -140,8 +140,11 @@ constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time (defau
 
 // Phase A row schedules (all add the same integers, so the sums do not depend on them).
 // Row per warp: warp w takes rows w, w + nwarps, ... of the spike list, FR rows at a time,
-// their 128-slot blocks loaded together (FR = 2: SNN_ROWS_PAIRS, 1: SNN_ROWS_PER_WARP).
-template <int FR, int nwarps>
+// their blocks of CH 32-slot chunks loaded together (FR = 2, CH = 4: SNN_ROWS_PAIRS;
+// 1, 4: SNN_ROWS_PER_WARP; 2, 8: SNN_ROWS_WIDE for long rows; 4, 4: SNN_ROWS_QUAD).  The
+// wide forms hold 16 loads per lane in flight (fewer round trips per step, more
+// registers: they suit the persistent kernel, whose CTAs have room for them).
+template <int FR, int nwarps, int CH = 4>
 __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lprv, int n_rows, const int* lens,
                                                     const unsigned long long* pk, int Cf, int R, int warp, int lane) {
     for (int k = warp; k < n_rows; k += FR * nwarps) {
@@ -155,15 +158,15 @@ __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lp
             pr[u] = pk + (size_t)(r < R ? r : 0) * Cf;
             nmax = nr[u] > nmax ? nr[u] : nmax;
         }
-        for (int s0 = 0; s0 < nmax; s0 += 128) {
-            unsigned long long wv[FR][4];
+        for (int s0 = 0; s0 < nmax; s0 += 32 * CH) {
+            unsigned long long wv[FR][CH];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < CH; ++q)
 #pragma unroll
                 for (int u = 0; u < FR; ++u)   // warp-uniform chunk tests; slots past a
                     wv[u][q] = s0 + q * 32 < nr[u] ? pr[u][s0 + q * 32 + lane] : 0ull;   // length are padding
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < CH; ++q)
 #pragma unroll
                 for (int u = 0; u < FR; ++u)
                     if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q]);
@@ -192,7 +195,9 @@ __device__ __forceinline__ void propagate_rows_block(unsigned* acc, const int* l
     }
 }
 
-template <typename real, int NPT, int TH>
+// WIDE: compile the register-hungry row schedules in (the persistent kernel); without
+// them SNN_ROWS_WIDE / SNN_ROWS_QUAD run as SNN_ROWS_PAIRS (the same sums).
+template <typename real, int NPT, int TH, bool WIDE = false>
 __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const int b, unsigned char* smem) {
     const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh, n_in = p.n_in;
     const int R = n_in + N;
@@ -269,9 +274,19 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             zcur[w] = 0u;
         }
         if (tid == 32) lcnt[cur] = 0;
-        if (p.sched == SNN_ROWS_PER_BLOCK) propagate_rows_block<nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, warp, lane);
-        else if (p.sched == SNN_ROWS_PER_WARP) propagate_rows_warp<1, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
-        else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+        switch (p.sched) {
+            case SNN_ROWS_PER_BLOCK: propagate_rows_block<nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, warp, lane); break;
+            case SNN_ROWS_PER_WARP: propagate_rows_warp<1, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+            case SNN_ROWS_WIDE:
+                if (WIDE) propagate_rows_warp<2, nwarps, 8>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                break;
+            case SNN_ROWS_QUAD:
+                if (WIDE) propagate_rows_warp<4, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                break;
+            default: propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+        }
         __syncthreads();
         // ---------------- phase B: neurons; spike lists of step t
         if (warp == 0 && lane < Win) {

@@ -242,7 +242,7 @@ __device__ void m_pre(const MInst& I, int k, unsigned char* smem) {
 
 template <int NPT>
 __device__ void m_fwd_npt(const FwdParams<float>& p, unsigned char* smem) {
-    forward_trial<float, NPT, MT>(p, 0, smem);
+    forward_trial<float, NPT, MT, true>(p, 0, smem);
 }
 
 __device__ void m_fwd(const MInst& I, unsigned char* smem) {

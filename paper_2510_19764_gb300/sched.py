@@ -253,14 +253,18 @@ class PhaseTrace:
 
 class Autotuner:
     """Row-schedule table keyed on (hidden size, mean row length, spike rate): for each
-    class, time the forward of a representative instance's trial with every admissible
-    (warps per trial, row schedule) choice and keep the fastest.  The persistent kernel
-    runs 8 warps per trial, so for it only the row schedule is tuned (warps=(8,))."""
+    class, time a representative instance with every admissible schedule and keep the
+    fastest.  target="plain": the per-call forward of one trial for every (warps per
+    trial, row schedule) pair; target="multi": one-instance runs of the persistent
+    kernel (8 warps per trial) for every row schedule, the wide ones included."""
 
     MODES = (abi.SNN_ROWS_PAIRS, abi.SNN_ROWS_PER_WARP, abi.SNN_ROWS_PER_BLOCK)
+    MULTI_MODES = MODES + (abi.SNN_ROWS_WIDE, abi.SNN_ROWS_QUAD)
 
-    def __init__(self, warps=(4, 8, 16)):
-        self.warps = tuple(warps)
+    def __init__(self, warps=(4, 8, 16), target: str = "plain"):
+        assert target in ("plain", "multi")
+        self.warps = tuple(warps) if target == "plain" else (8,)
+        self.target = target
         self.table: dict[tuple, tuple] = {}
         self.timings: dict[tuple, dict] = {}
 
@@ -283,6 +287,18 @@ class Autotuner:
         self._apply(inst, choice)
         s = torch.cuda.current_stream()
         best = float("inf")
+        if self.target == "multi":
+            mr = MultiRunner([inst])             # the plan reads the schedule when created
+            mr.iterate(s)
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                mr.iterate(s)
+                b.record(s)
+                b.synchronize()
+                best = min(best, a.elapsed_time(b))
+            mr.close()
+            return best
         for _ in range(reps):
             for t in (inst.batch.v, inst.batch.a, inst.batch.y, inst.batch.ysum, inst.batch.x_bits,
                       inst.batch.z_bits):
@@ -296,12 +312,13 @@ class Autotuner:
         return best
 
     def tune(self, instances) -> dict:
+        modes = self.MULTI_MODES if self.target == "multi" else self.MODES
         for inst in instances:
             # a sample trial at the default schedule gives the spike rate of the class
             self._time(inst, (8, abi.SNN_ROWS_PAIRS), reps=1)
             k = self.key(inst, self.spike_rate(inst))
             if k not in self.table:
-                times = {(w, mode): self._time(inst, (w, mode)) for w in self.warps for mode in self.MODES
+                times = {(w, mode): self._time(inst, (w, mode)) for w in self.warps for mode in modes
                          if inst.spec.N <= 8 * 32 * w}
                 self.table[k] = min(times, key=times.get)
                 self.timings[k] = times

@@ -119,10 +119,14 @@ def test_training_run_reduced_classifier(dtype):
         for k_, (name, d) in enumerate((("in", dev.w_in), ("rec", dev.w_rec))):
             live = np.arange(d.C)[None] < g_post[name]["row_len"][:, None]
             if dtype == F32:
-                # the batch's gradient (summed over its trials) against the oracle's
+                # the batch's gradient (summed over its trials) against the oracle's.  Each
+                # entry sums ~10^2 adjoint values of either sign, each carrying up to T x 2^-24
+                # relative FP32 error from the reverse-time scan; an entry that cancels keeps
+                # the absolute error of its terms, hence the absolute term (of the largest
+                # entry, whose terms rarely cancel)
                 Gg, Go = g_post[name]["grad"][live], G[k_][live]
                 gmax = np.abs(Go).max()
-                bound = 2e-5 * np.maximum(np.abs(Go), 1e-3 * gmax) + 1e-6 * gmax
+                bound = 2e-5 * np.maximum(np.abs(Go), 1e-3 * gmax) + 5e-6 * gmax
                 worst = int(np.argmax(np.abs(Gg - Go) / bound))
                 assert np.all(np.abs(Gg - Go) <= bound), (i, name, Gg[worst], Go[worst], gmax)
                 # L1 + Adam from the GPU's own gradient: FP32 rounding of the FP64 update

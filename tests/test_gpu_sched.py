@@ -159,6 +159,27 @@ def test_persistent_kernel_wait_gives_up_when_nothing_is_posted():
     _assert_same(plain, multi, 1)
 
 
+def test_autotuner_for_the_persistent_kernel_and_wide_schedules():
+    """The persistent kernel's autotuner times one-instance runs for every row schedule
+    (wide ones included); whatever it picks, the results stay those of the plain path."""
+    from paper_2510_19764_gb300 import abi, sched
+    specs = [sched.InstanceSpec(N, T, p, i) for i, (N, T, p) in enumerate([(2048, 60, 0.2), (256, 50, 0.05)])]
+    tuned = _instances(specs)
+    tuner = sched.Autotuner(target="multi")
+    table = tuner.tune(tuned)
+    assert all(len(v) == len(sched.Autotuner.MULTI_MODES) for v in tuner.timings.values())
+    assert all(mode in sched.Autotuner.MULTI_MODES for _, mode in table.values())
+    # each wide schedule on its own: persistent equals plain
+    for mode in (abi.SNN_ROWS_WIDE, abi.SNN_ROWS_QUAD):
+        plain = _instances(specs, modes=[mode, mode])
+        pr = sched.PlainRunner(plain, per_step=False)
+        pr.iterate()
+        multi = _instances(specs, modes=[mode, mode])
+        sched.MultiRunner(multi).iterate()
+        torch.cuda.synchronize()
+        _assert_same(plain, multi, 1)
+
+
 def test_autotuner_picks_admissible_schedules():
     from paper_2510_19764_gb300 import abi, sched
     specs = [sched.InstanceSpec(N, 60, 0.1, i) for i, N in enumerate([128, 512, 2048])]
