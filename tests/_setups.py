@@ -90,3 +90,12 @@ def oracle_trial(args):
     r = oc.forward_trial(net, thr, label, bin_len, trial_id, seed, T)
     g = oc.eprop_gradients(net, r["x"], r["z"], r["psi"], r["d"])
     return r["z"].astype(np.uint8), r["pred"], r["ysum"], g
+
+
+def oracle_grad_from_records(args):
+    """Pool worker: the oracle's e-prop gradients (forward-trace form) of one trial from
+    given records.  args = (ClassifierNet constructor arrays, neuron params, x [T, n_in],
+    z [T, N], psi [T, N], d [T, K]).  Returns (G_in, G_rec, G_out, G_b)."""
+    arrays, neuron, x, z, psi, d = args
+    net = oc.ClassifierNet(*arrays, neuron)
+    return oc.eprop_gradients(net, x, z, psi, d)

@@ -48,8 +48,8 @@ def _oracle_update(st, sign, conn, W, b, mom, G, i, lr, l1, seeds, N):
 
 @pytest.mark.parametrize("dtype", [F32, F64])
 def test_training_run_reduced_classifier(dtype):
-    """700 inputs -> 128 ALIF -> 20 readouts, 10 %, 400 steps, batch 8, 20 batches of
-    e-prop + L1 + Adam + DEEP R.
+    """700 inputs -> 128 ALIF -> 20 readouts, 10 %, 400 steps, batch 16, 20 batches of
+    e-prop + L1 + Adam + DEEP R (320 trials).
 
     FP64: the oracle trained from the same start on its own (its trials in parallel
     processes, gradients summed in trial order) gives every raster, every prediction and
@@ -57,9 +57,11 @@ def test_training_run_reduced_classifier(dtype):
 
     FP32: judged batch by batch from the GPU's own state (the oracle takes the GPU's
     weights, moments and connectivity before each batch): >= 99.9 % of all spikes of the
-    run agree, the accuracy over the run is within 0.5 points, each batch's gradient
-    agrees with the oracle's within the gradient tolerance, L1 + Adam from the GPU's
-    gradient within FP32 rounding, and DEEP R from the GPU's post-Adam state bit-exactly.
+    run agree (each trial simulated by the oracle on its own from the GPU's weights), the
+    accuracy over the run is within 0.5 points, each batch's gradient agrees with the
+    oracle's from the GPU's records within the gradient tolerance, L1 + Adam from the
+    GPU's gradient within FP32 rounding, and DEEP R from the GPU's post-Adam state
+    bit-exactly.
     (Adam's first steps divide by |g|, so gradients near its eps would magnify the FP32
     gradient error; the update is compared from the same gradient, as for a single step.)
     (Trained on its own, the FP64 oracle drifts from the FP32 run once a sign test or a
@@ -67,7 +69,7 @@ def test_training_run_reduced_classifier(dtype):
     spikes agreed for 10 batches, then agreement fell to ~92 %; every step from the same
     state agreed.)"""
     from paper_2510_19764_gb300 import abi, net
-    T, B, n_batches, lr, l1 = 400, 8, 20, 1e-3, 1e-5
+    T, B, n_batches, lr, l1 = 400, 16, 20, 1e-3, 1e-5
     s = _setups.classifier(seed=5, n_in=700, N=128, K=20, lif=False, v_thr=0.6, T=T, n_classes=20, n_bins=10,
                            spoken=True, max_B=B, dtype=dtype)
     batches = [synth.trial_batch(s.task, 5, i, B) for i in range(n_batches)]
@@ -104,6 +106,15 @@ def test_training_run_reduced_classifier(dtype):
         z = net.spikes_from_bits(net.u32_to_numpy(batch.z_rec), 128).astype(np.uint8)
         g_preds += list(np.argmax(batch.ysum.double().cpu().numpy(), axis=1))
         arrays = _arrays(n, st, W, b)
+        if dtype == F32:
+            # the oracle's gradient from the GPU's own records (a trial whose raster a
+            # rounding flip sent elsewhere would otherwise compare different spikes)
+            x = net.spikes_from_bits(net.u32_to_numpy(batch.x_rec), 700).astype(np.float64)
+            psi, dd = batch.psi_rec.double().cpu().numpy(), batch.d_rec.double().cpu().numpy()
+            g_jobs = [(arrays, n.neuron, x[k], z[k].astype(np.float64), psi[k], dd[k]) for k in range(B)]
+            G_rec = [0, 0, 0, 0]
+            for g in pool.map(_setups.oracle_grad_from_records, g_jobs):
+                G_rec = [a + c for a, c in zip(G_rec, g)]
         jobs = [(arrays, n.neuron, s.task.thr, tb.labels[k], tb.bin_len[k], tb.trial_ids[k], s.in_seed, T)
                 for k in range(B)]
         G = [0, 0, 0, 0]
@@ -119,12 +130,12 @@ def test_training_run_reduced_classifier(dtype):
         for k_, (name, d) in enumerate((("in", dev.w_in), ("rec", dev.w_rec))):
             live = np.arange(d.C)[None] < g_post[name]["row_len"][:, None]
             if dtype == F32:
-                # the batch's gradient (summed over its trials) against the oracle's.  Each
-                # entry sums ~10^2 adjoint values of either sign, each carrying up to T x 2^-24
-                # relative FP32 error from the reverse-time scan; an entry that cancels keeps
-                # the absolute error of its terms, hence the absolute term (of the largest
-                # entry, whose terms rarely cancel)
-                Gg, Go = g_post[name]["grad"][live], G[k_][live]
+                # the batch's gradient (summed over its trials) against the oracle's from the
+                # same records.  Each entry sums ~10^2 adjoint values of either sign, each
+                # carrying up to T x 2^-24 relative FP32 error from the reverse-time scan; an
+                # entry that cancels keeps the absolute error of its terms, hence the
+                # absolute term (of the largest entry, whose terms rarely cancel)
+                Gg, Go = g_post[name]["grad"][live], G_rec[k_][live]
                 gmax = np.abs(Go).max()
                 bound = 2e-5 * np.maximum(np.abs(Go), 1e-3 * gmax) + 5e-6 * gmax
                 worst = int(np.argmax(np.abs(Gg - Go) / bound))
