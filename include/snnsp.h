@@ -347,11 +347,7 @@ snn_status snn_destroy_classifier(snn_classifier* c);
  * (40 fractional bits) while they stay below 2^11 in magnitude: a neuron or readout
  * whose incoming |weight| sum (input, recurrent and readout weights, the bound on any
  * step's sum) reaches 2^11 also sets SNN_ESTATE, since its sums could wrap.  Weights
- * below 2^-17 in magnitude are rounded to the fixed-point grid (2^-40).  FP32: while the
- * largest such |weight| sum S is below 2^9, each weight is added rounded to the grid
- * 2^(b - 70) (b = bit length of S in 40-fractional-bit fixed point; 2^-25 for S = 16),
- * with one 32-bit atomic instead of two; the sums stay exact on that grid, so results
- * still do not depend on the order of the additions. */
+ * below 2^-17 in magnitude are rounded to the fixed-point grid (2^-40). */
 snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
                             snn_stream stream);
 

@@ -7,8 +7,6 @@
 
 #include "common.cuh"
 
-#include <type_traits>
-
 namespace snn {
 
 constexpr int BWD_THREADS = 128;
@@ -44,6 +42,7 @@ struct FwdParams {
 
 // An accumulator's sums are exact while their magnitude stays below 2^11 (2^51 in fixed
 // point); the sum of |weight| over every slot aimed at it bounds any step's sum.
+constexpr unsigned long long FIX_SUM_LIMIT = 1ull << 51;
 
 struct InputParams {
     int n_in, Win, T, t0, n_steps, n_bins, n_classes, B;
@@ -66,38 +65,20 @@ __device__ __forceinline__ double exp_real(double x) { return exp(x); }
 // shared-memory atomics and are exact: L takes at most one addend (< 2^20) per spiking
 // row, rows hold no repeated target and n_in + N <= 3072 < 4096; H wraps modulo 2^32
 // like the 52-bit weights.  The total is 2^20 H + L.
-//
-// Narrow form (FP32 only): with S the largest |weight| sum over the accumulators (the
-// bound of any step's sum) and e its bit length in fixed point, each weight is added as
-// one 32-bit atomic of round(w 2^40 / 2^sh), sh = max(0, e - 30), into H alone: the sum
-// then stays exact in 32 bits (|sum| <= 2^30 + 3072 / 2) and is H 2^(sh - 40).  It halves
-// the shared-memory atomics of the propagation; each addend is off by at most
-// 2^(sh - 41) <= S 2^-31 (S = 16: 7.5e-9), comparable to the FP32 rounding of the sum
-// itself.  Used while S < 2^9 (sh <= 19).
-template <bool NARROW>
-__device__ __forceinline__ void acc_add(unsigned* acc, unsigned long long w, int sh = 0) {
+__device__ __forceinline__ void acc_add(unsigned* acc, unsigned long long w) {
     const unsigned lo = (unsigned)w, hi = (unsigned)(w >> 32);
     unsigned* a = acc + 2 * (hi >> 20);                   // target index: bits 63..52
-    if (NARROW) {
-        const long long f = (long long)(w << 12) >> 12;   // the 52-bit weight, sign-extended
-        const long long r = sh > 0 ? (f + (1ll << (sh - 1))) >> sh : f;
-        atomicAdd(a, (unsigned)(int)r);
-    } else {
-        atomicAdd(a, __funnelshift_r(lo, hi, 20));        // bits 51..20
-        atomicAdd(a + 1, lo & 0xFFFFFu);                  // bits 19..0
-    }
+    atomicAdd(a, __funnelshift_r(lo, hi, 20));            // bits 51..20
+    atomicAdd(a + 1, lo & 0xFFFFFu);                      // bits 19..0
 }
 // The accumulated sum 2^20 H + L in real units (40 fractional bits): H 2^-20 + L 2^-40,
 // each product exact, one rounding in the sum (for double the same value as converting
-// the 64-bit integer first); narrow: H 2^-28.
+// the 64-bit integer first).
 template <typename real>
-__device__ __forceinline__ real acc_real(const long long* acc, bool narrow, real nscale) {
+__device__ __forceinline__ real acc_real(const long long* acc) {
     const unsigned* a = (const unsigned*)acc;
-    if (narrow) return (real)(int)a[0] * nscale;
     return (real)(int)a[0] * (real)9.5367431640625e-07 + (real)a[1] * (real)9.094947017729282e-13;
 }
-// Bit length of the largest |weight| sum (fixed point) that the narrow form accepts: S < 2^9.
-constexpr int FIX_NARROW_BITS = 49;
 
 // Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
 // only, so they are drawn ahead of the sequential simulation.  Thread = 8 channels (one
@@ -163,10 +144,9 @@ constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time (defau
 // 1, 4: SNN_ROWS_PER_WARP; 2, 8: SNN_ROWS_WIDE for long rows; 4, 4: SNN_ROWS_QUAD).  The
 // wide forms hold 16 loads per lane in flight (fewer round trips per step, more
 // registers: they suit the persistent kernel, whose CTAs have room for them).
-template <bool NARROW, int FR, int nwarps, int CH = 4>
+template <int FR, int nwarps, int CH = 4>
 __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lprv, int n_rows, const int* lens,
-                                                    const unsigned long long* pk, int Cf, int R, int warp, int lane,
-                                                    int sh) {
+                                                    const unsigned long long* pk, int Cf, int R, int warp, int lane) {
     for (int k = warp; k < n_rows; k += FR * nwarps) {
         int nr[FR];
         const unsigned long long* pr[FR];
@@ -189,16 +169,16 @@ __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lp
             for (int q = 0; q < CH; ++q)
 #pragma unroll
                 for (int u = 0; u < FR; ++u)
-                    if (s0 + q * 32 < nr[u]) acc_add<NARROW>(acc, wv[u][q], sh);
+                    if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q]);
         }
     }
 }
 
 // Row per block: every warp works on every spiking row, warp w taking the row's 32-slot
 // chunks w, w + nwarps, ...; two rows in flight (suits few long rows).
-template <bool NARROW, int nwarps>
+template <int nwarps>
 __device__ __forceinline__ void propagate_rows_block(unsigned* acc, const int* lprv, int n_rows, const int* lens,
-                                                     const unsigned long long* pk, int Cf, int warp, int lane, int sh) {
+                                                     const unsigned long long* pk, int Cf, int warp, int lane) {
     for (int k = 0; k < n_rows; k += 2) {
         const int r0 = lprv[k];
         const int r1 = k + 1 < n_rows ? lprv[k + 1] : -1;
@@ -209,35 +189,9 @@ __device__ __forceinline__ void propagate_rows_block(unsigned* acc, const int* l
         for (int s0 = warp * 32; s0 < nmax; s0 += nwarps * 32) {
             const unsigned long long a = s0 < n0 ? p0[s0 + lane] : 0ull;
             const unsigned long long b = s0 < n1 ? p1[s0 + lane] : 0ull;
-            if (s0 < n0) acc_add<NARROW>(acc, a, sh);
-            if (s0 < n1) acc_add<NARROW>(acc, b, sh);
+            if (s0 < n0) acc_add(acc, a);
+            if (s0 < n1) acc_add(acc, b);
         }
-    }
-}
-
-// Phase A of one step with the trial's row schedule.
-template <bool NARROW, bool WIDE, int nwarps>
-__device__ __forceinline__ void propagate_step(int sched, unsigned* acc, const int* lprv, int n_rows, const int* lens,
-                                               const unsigned long long* pk, int Cf, int R, int warp, int lane,
-                                               int sh) {
-    switch (sched) {
-        case SNN_ROWS_PER_BLOCK:
-            propagate_rows_block<NARROW, nwarps>(acc, lprv, n_rows, lens, pk, Cf, warp, lane, sh);
-            break;
-        case SNN_ROWS_PER_WARP:
-            propagate_rows_warp<NARROW, 1, nwarps>(acc, lprv, n_rows, lens, pk, Cf, R, warp, lane, sh);
-            break;
-        case SNN_ROWS_WIDE:
-            if (WIDE) propagate_rows_warp<NARROW, 2, nwarps, 8>(acc, lprv, n_rows, lens, pk, Cf, R, warp, lane, sh);
-            else propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, pk, Cf, R, warp, lane, sh);
-            break;
-        case SNN_ROWS_QUAD:
-            if (WIDE) propagate_rows_warp<NARROW, 4, nwarps>(acc, lprv, n_rows, lens, pk, Cf, R, warp, lane, sh);
-            else propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, pk, Cf, R, warp, lane, sh);
-            break;
-        default:
-            propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, pk, Cf, R, warp, lane, sh);
-            break;
     }
 }
 
@@ -292,27 +246,12 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
         ysk = p.ysum[(size_t)b * K + lane];
         bk = p.b_out[lane];
     }
-    // A neuron or readout whose |weight| sum reaches 2^11 could wrap its fixed-point sum
-    // (flagged); the bit length of the largest sum picks the narrow form's shift (FP32):
-    // the same decision in every CTA, from the sums the packing accumulated.
-    __shared__ int s_bits;
-    if (tid == 0) s_bits = 0;
-    __syncthreads();
-    {
-        unsigned long long cmax = 0;
-        for (int j = tid; j < N + 64; j += TH) {
-            const unsigned long long c = p.colsum[j];
-            cmax = c > cmax ? c : cmax;
-        }
-        const int bits = 64 - __clzll((long long)cmax);
-        atomicMax(&s_bits, __reduce_max_sync(0xffffffffu, (unsigned)bits));
+    if (b == 0) {
+        // a neuron or readout whose |weight| sum reaches 2^11 could wrap its fixed-point sum
+        bool over = false;
+        for (int j = tid; j < N + 64; j += TH) over |= p.colsum[j] >= FIX_SUM_LIMIT;
+        if (__syncthreads_or(over) && tid == 0) atomicOr(p.status, ST_STATE);
     }
-    __syncthreads();
-    const int max_bits = s_bits;
-    if (max_bits > 51 && b == 0 && tid == 0) atomicOr(p.status, ST_STATE);      // a sum >= 2^51
-    const bool narrow = std::is_same<real, float>::value && max_bits <= FIX_NARROW_BITS;
-    const int nsh = max_bits > 30 ? max_bits - 30 : 0;
-    const real nscale = (real)ldexp(1.0, nsh - 40);
     const uint32_t* xrec_b = p.x_rec + (size_t)b * p.T * Win;
     uint32_t* zrec_b = p.z_rec + (size_t)b * p.T * Wh;
     real* psi_b = p.psi_rec ? p.psi_rec + (size_t)b * p.T * N : nullptr;   // NULL: inference, no records
@@ -335,8 +274,19 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             zcur[w] = 0u;
         }
         if (tid == 32) lcnt[cur] = 0;
-        if (narrow) propagate_step<true, WIDE, nwarps>(p.sched, acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane, nsh);
-        else propagate_step<false, WIDE, nwarps>(p.sched, acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane, 0);
+        switch (p.sched) {
+            case SNN_ROWS_PER_BLOCK: propagate_rows_block<nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, warp, lane); break;
+            case SNN_ROWS_PER_WARP: propagate_rows_warp<1, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+            case SNN_ROWS_WIDE:
+                if (WIDE) propagate_rows_warp<2, nwarps, 8>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                break;
+            case SNN_ROWS_QUAD:
+                if (WIDE) propagate_rows_warp<4, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                break;
+            default: propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+        }
         __syncthreads();
         // ---------------- phase B: neurons; spike lists of step t
         if (warp == 0 && lane < Win) {
@@ -347,7 +297,7 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             xw[lane] = 0u;
         }
         if (warp == RO_WARP && lane < K) {         // y^t from the readout sums W_out z^{t-1}
-            yk = p.alpha * yk + acc_real<real>(Iacc + N + 32 + lane, narrow, nscale) + bk;
+            yk = p.alpha * yk + acc_real<real>(Iacc + N + 32 + lane) + bk;
             Iacc[N + 32 + lane] = 0;
             ysk += yk;
             if (d_b) d_b[(size_t)t * K + lane] = yk;
@@ -359,7 +309,7 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             const int j = tid + q * TH;
             bool spk = false;
             if (j < N) {
-                const real I = acc_real<real>(Iacc + j, narrow, nscale);
+                const real I = acc_real<real>(Iacc + j);
                 Iacc[j] = 0;
                 const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
                 const real v = p.alpha * (zp ? vr[q] - p.v_thr : vr[q]) + I;
