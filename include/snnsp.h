@@ -360,11 +360,24 @@ snn_status snn_draw_inputs(snn_classifier* c, const snn_batch* b, int32_t t0, in
                            snn_stream stream);
 
 #define SNN_STEP_INPUTS_READY 1   /* x_rec already holds the steps' inputs (snn_draw_inputs) */
-/* snn_step_neurons with flags: SNN_STEP_INPUTS_READY skips the input draw; every other
- * flag bit is SNN_EINVAL.  Results are identical to snn_step_neurons when x_rec holds
- * what snn_draw_inputs wrote for the same batch and steps. */
+#define SNN_STEP_PACKED_READY 2   /* the packed forward rows are current (snn_classifier_pack) */
+/* snn_step_neurons with flags: SNN_STEP_INPUTS_READY skips the input draw;
+ * SNN_STEP_PACKED_READY skips rebuilding the handle's packed forward rows from the
+ * weights (the caller ran snn_classifier_pack after the last change of the weights);
+ * every other flag bit is SNN_EINVAL.  Results are identical to snn_step_neurons when
+ * x_rec holds what snn_draw_inputs wrote for the same batch and steps and the packed
+ * rows are current.
+ * Concurrency: a classifier handle's scratch (packed rows, their |weight| sums, gather
+ * order, gradient partials) is written by snn_step_neurons and snn_eprop_update, so calls
+ * on one handle must not overlap on the GPU -- except forward calls with
+ * SNN_STEP_PACKED_READY, which only read it (e.g. several batches of requests of one
+ * served model on different streams). */
 snn_status snn_step_neurons_ex(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
                                int32_t flags, snn_stream stream);
+/* Rebuild the handle's packed forward rows (and the |weight| sums of the range check)
+ * from the current weights on `stream`; what every snn_step_neurons call does first
+ * unless it passes SNN_STEP_PACKED_READY. */
+snn_status snn_classifier_pack(snn_classifier* c, snn_stream stream);
 
 /* e-prop learning (Sec. 2.2.1 eligibility-trace equations, summed over trials).
  * SNN_EPROP_GRAD: from the records of a finished batch (all T steps) computes

@@ -19,6 +19,7 @@ SNN_F32, SNN_F64 = 0, 1
 SNN_EPROP_GRAD, SNN_EPROP_APPLY = 0, 1
 SNN_FIXED_FRAC_BITS = 40
 SNN_STEP_INPUTS_READY = 1
+SNN_STEP_PACKED_READY = 2
 SNN_ROWS_PAIRS, SNN_ROWS_PER_WARP, SNN_ROWS_PER_BLOCK, SNN_ROWS_WIDE, SNN_ROWS_QUAD = 0, 1, 2, 3, 4
 SNN_MULTI_HOST_POSTS = 1
 
@@ -30,7 +31,7 @@ EXPORTED = [
     "snn_draw_inputs", "snn_step_neurons_ex", "snn_topo_connectivity", "snn_ragged_set_deepr_guide",
     "snn_test_wait_timeout", "snn_ragged_add_row", "snn_ragged_remove_row", "snn_adam_bias", "snn_topo_derive",
     "snn_classifier_set_row_schedule", "snn_multi_create", "snn_multi_destroy", "snn_multi_run", "snn_multi_post",
-    "snn_multi_status", "snn_multi_set_trace",
+    "snn_multi_status", "snn_multi_set_trace", "snn_classifier_pack",
 ]
 
 
@@ -159,6 +160,7 @@ def load() -> C.CDLL:
         "snn_multi_post": (i32, [vp, P(i32), i32]),
         "snn_multi_status": (i32, [vp, vp]),
         "snn_multi_set_trace": (i32, [vp, vp]),
+        "snn_classifier_pack": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -348,3 +350,7 @@ def snn_multi_status(h: int, stream=None) -> int:
 
 def snn_multi_set_trace(h: int, times) -> None:
     check(load().snn_multi_set_trace(h, ptr(times)))
+
+
+def snn_classifier_pack(h: int, stream=None) -> None:
+    check(load().snn_classifier_pack(h, stream_ptr(stream)))

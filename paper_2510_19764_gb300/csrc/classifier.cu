@@ -230,7 +230,7 @@ static snn_status draw_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
 
 template <typename real>
 static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int n_steps, bool inputs_ready,
-                            cudaStream_t s) {
+                            bool packed_ready, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
     const int Win = (d.n_in + 31) / 32, Wh = (d.N + 31) / 32;
     if (!inputs_ready) {
@@ -277,7 +277,7 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.status = d.w_in->status;
     p.sched = c->row_sched;
     const size_t smem = fwd_smem(d.n_in, d.N, Win, Wh);
-    snn_status st = refresh_fixed<real>(c, s);
+    snn_status st = packed_ready ? SNN_OK : refresh_fixed<real>(c, s);
     if (st != SNN_OK) return st;
     SNN_REQUIRE(smem <= 227 * 1024, "snn_step_neurons: n_in = %d, N = %d need %zu bytes of shared memory (max 227 KB)",
                 d.n_in, d.N, smem);
@@ -704,12 +704,21 @@ snn_status snn_step_neurons_ex(snn_classifier* c, const snn_batch* b, int32_t t0
     if (st != SNN_OK) return st;
     SNN_REQUIRE(t0 >= 0 && n_steps >= 0 && t0 + n_steps <= b->T, "snn_step_neurons: steps [%d, %d) outside [0, %d)",
                 t0, t0 + n_steps, b->T);
-    SNN_REQUIRE((flags & ~SNN_STEP_INPUTS_READY) == 0, "snn_step_neurons_ex: unknown flags 0x%x", flags);
+    SNN_REQUIRE((flags & ~(SNN_STEP_INPUTS_READY | SNN_STEP_PACKED_READY)) == 0,
+                "snn_step_neurons_ex: unknown flags 0x%x", flags);
     if (n_steps == 0) return SNN_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const bool ready = (flags & SNN_STEP_INPUTS_READY) != 0;
-    return c->d.dtype == SNN_F32 ? step_impl<float>(c, b, t0, n_steps, ready, s)
-                                 : step_impl<double>(c, b, t0, n_steps, ready, s);
+    const bool packed = (flags & SNN_STEP_PACKED_READY) != 0;
+    return c->d.dtype == SNN_F32 ? step_impl<float>(c, b, t0, n_steps, ready, packed, s)
+                                 : step_impl<double>(c, b, t0, n_steps, ready, packed, s);
+}
+
+snn_status snn_classifier_pack(snn_classifier* c, snn_stream stream) {
+    clear_error();
+    SNN_REQUIRE(c, "snn_classifier_pack: NULL classifier");
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->d.dtype == SNN_F32 ? refresh_fixed<float>(c, s) : refresh_fixed<double>(c, s);
 }
 
 snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps, snn_stream stream) {

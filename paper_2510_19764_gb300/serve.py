@@ -91,6 +91,10 @@ class Model:
                                       no_autapse=True, device=device)
         self.cls = net.DeviceClassifier(N_IN, N, K_OUT, self.d_in, self.d_rec, self.W_out, self.b, task.thr,
                                         9003 + 7 * mid, net.NeuronCfg(), max_B=max_batch, max_T=T_MAX, device=device)
+        # the served weights do not change: pack the forward rows once, so that concurrent
+        # launches of this model only read the handle's scratch
+        abi.snn_classifier_pack(self.cls.handle, None)
+        torch.cuda.synchronize()
 
     def private_copy(self):
         """Trainable copy (own ragged matrices, Adam state, DEEP R bitfields) for a
@@ -209,7 +213,7 @@ class Engine:
                 t[:n].zero_()
         desc = abi.Batch.from_buffer_copy(bt.desc)
         desc.B = n
-        abi.snn_step_neurons(slot.model.cls.handle, desc, 0, Tmax, stream)
+        abi.snn_step_neurons_ex(slot.model.cls.handle, desc, 0, Tmax, abi.SNN_STEP_PACKED_READY, stream)
         with torch.cuda.stream(stream):
             slot.h_ysum[:n].copy_(bt.ysum[:n], non_blocking=True)
             ev = torch.cuda.Event()

@@ -89,3 +89,34 @@ def test_serving_loop_allocates_nothing_and_admits_finetunes_by_their_bytes():
     with pytest.raises(serve.AdmissionError) as e:
         eng.run([r for r in reqs if r.finetune and r.model == 0][:1], realtime=False)
     assert str(ft.bytes) in str(e.value)
+
+
+def test_concurrent_forward_launches_on_one_model_read_only_scratch():
+    """Several batches of one served model's requests launched on different streams at
+    once, with the packed rows built beforehand (SNN_STEP_PACKED_READY): each batch's
+    results equal the same batch run alone, and the handle reports no error."""
+    from paper_2510_19764_gb300 import abi, net, serve
+    task = synth.spoken_digit_task(5, n_in=serve.N_IN, n_classes=serve.N_CLASSES, T=serve.T_MAX, n_bins=serve.N_BINS)
+    m = serve.Model(0, 512, task, max_batch=16)
+    rng = np.random.default_rng(3)
+    batches = []
+    for k in range(6):
+        lab = rng.integers(0, serve.N_CLASSES, 16)
+        b = net.DeviceBatch(m.cls, lab, np.full(16, 30), np.arange(16) + 100 * k, 300, workspace=False, records=False)
+        batches.append(b)
+    alone = []
+    for b in batches:
+        abi.snn_step_neurons_ex(m.cls.handle, b.desc, 0, 300, abi.SNN_STEP_PACKED_READY)
+        torch.cuda.synchronize()
+        alone.append(b.ysum.clone())
+        b.reset_state()
+    streams = [torch.cuda.Stream() for _ in batches]
+    torch.cuda.synchronize()
+    for b, s in zip(batches, streams):
+        abi.snn_step_neurons_ex(m.cls.handle, b.desc, 0, 300, abi.SNN_STEP_PACKED_READY, s)
+    torch.cuda.synchronize()
+    for b, y in zip(batches, alone):
+        assert torch.equal(b.ysum, y)
+    assert m.d_in.status() == abi.SNN_OK
+    with pytest.raises(abi.SnnError):
+        abi.snn_step_neurons_ex(m.cls.handle, batches[0].desc, 0, 300, 4)
