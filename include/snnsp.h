@@ -446,9 +446,9 @@ snn_status snn_multi_run(snn_multi* m, int32_t flags, int64_t wait_limit_ns, snn
 /* Phase timing of later runs (tracing): times = device int64 [n][11] (NULL: off).  Each
  * run writes, per instance in the order given to snn_multi_create, the global timer (ns)
  * when its iteration was seeded ([i][0]) and when each of its 10 phases completed
- * ([i][1 + phase]: inputs / packing / gather order, forward, readout scan, adjoint
- * scan, gather, Adam, DEEP R elimination, redistribution, formation; [i][1] is the
- * bookkeeping phase).  The caller keeps the buffer alive while it is set. */
+ * ([i][1 + phase]: bookkeeping, inputs and packing, forward (with the gather order
+ * beside it), readout scan, adjoint scan, gather, Adam, DEEP R elimination,
+ * redistribution, formation).  The caller keeps the buffer alive while it is set. */
 snn_status snn_multi_set_trace(snn_multi* m, int64_t* times);
 /* Host producer for a SNN_MULTI_HOST_POSTS run: the instances (indices into the array
  * given to snn_multi_create, no repeats) that the running iteration should train.

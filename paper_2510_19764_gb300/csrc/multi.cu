@@ -6,8 +6,9 @@
 // (bookkeeping, snn_step_neurons over the whole trial, snn_eprop_update GRAD and APPLY,
 // snn_rewire_deepr on both projections), split into phases whose work is cut into items:
 //   PREP    1 item       trial id / label / time warp of the iteration, state reset
-//   PRE     n items      input spikes of the trial, packed forward rows, gather order
-//   FWD     1 item       the whole trial (forward_trial)
+//   PRE     n items      input spikes of the trial, packed forward rows
+//   FWD     1 + n items  the whole trial (forward_trial), and beside it the gather order
+//                        of every row (needed only by GATHER)
 //   SCAN    1 item       softmax of the readout, filtered readout error, bias gradient,
 //                        Adam's running products
 //   BWD     N/512 items  the adjoint scan, 512 hidden neurons per item
@@ -97,7 +98,7 @@ struct MInst {
     double lr, beta1, beta2, eps, l1, temperature;
     MRag rg[2];
     int n_items[MP_N];
-    int n_input, n_pack, n_sort0;                // MP_PRE: input, pack, sort (input rows, then hidden)
+    int n_input, n_pack, n_sort0;                // MP_PRE: input, pack; MP_FWD: sort items of input rows first
     int n_rows0;                                 // MP_ELIM / MP_FORM: items of the input projection
     int orig;                                    // the instance's index in the caller's array
 };
@@ -227,7 +228,11 @@ __device__ void m_pre(const MInst& I, int k, unsigned char* smem) {
         }
         return;
     }
-    k -= I.n_pack;
+}
+
+// Gather order of 32 rows (item k of the FWD phase's sort items).
+__device__ void m_sort(const MInst& I, int k, unsigned char* smem) {
+    const int tid = threadIdx.x;
     const int proj = k < I.n_sort0 ? 0 : 1;
     const int kk = proj == 0 ? k : k - I.n_sort0;
     const MRag& r = I.rg[proj];
@@ -512,7 +517,10 @@ __global__ void __launch_bounds__(MT, 1) k_multi(MArgs A) {
         switch (phase) {
             case MP_PREP: m_prep(I); break;
             case MP_PRE: m_pre(I, k, smem); break;
-            case MP_FWD: m_fwd(I, smem); break;
+            case MP_FWD:
+                if (k == 0) m_fwd(I, smem);
+                else m_sort(I, k - 1, smem);
+                break;
             case MP_SCAN: m_scan(I, smem); break;
             case MP_BWD: m_bwd(I, k, smem); break;
             case MP_GATHER: m_gather(I, k, smem); break;
@@ -688,8 +696,8 @@ static snn_status multi_fill(const snn_multi_instance& s, MInst& I, size_t& smem
     I.n_sort0 = rows0;
     I.n_rows0 = rows0;
     I.n_items[MP_PREP] = 1;
-    I.n_items[MP_PRE] = I.n_input + I.n_pack + rows0 + rows1;
-    I.n_items[MP_FWD] = 1;
+    I.n_items[MP_PRE] = I.n_input + I.n_pack;
+    I.n_items[MP_FWD] = 1 + rows0 + rows1;
     I.n_items[MP_SCAN] = 1;
     I.n_items[MP_BWD] = ceil_div(d.N, M_BWD_PER_ITEM);
     I.n_items[MP_GATHER] = I.Win + I.Wh;

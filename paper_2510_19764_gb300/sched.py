@@ -191,7 +191,7 @@ class MultiRunner:
         self.graph = None
         self.graph_iters = 0
 
-    PHASES = ("prep", "inputs+pack+sort", "forward", "readout_scan", "adjoint", "gather", "adam", "deepr_elim",
+    PHASES = ("prep", "inputs+pack", "forward+sort", "readout_scan", "adjoint", "gather", "adam", "deepr_elim",
               "deepr_dist", "deepr_form")
 
     def iterate(self, stream=None, flags: int = 0):

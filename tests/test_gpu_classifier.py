@@ -324,8 +324,8 @@ def test_training_run_tiny_config(dtype, temperature):
 
 def test_predrawn_inputs_give_identical_records():
     """snn_draw_inputs (on another stream) + snn_step_neurons_ex(INPUTS_READY) give the
-    same records, bit for bit, as snn_step_neurons drawing its own inputs; unknown flag
-    bits are rejected."""
+    same records, bit for bit, as snn_step_neurons drawing its own inputs; so does
+    SNN_STEP_PACKED_READY after snn_classifier_pack; unknown flag bits are rejected."""
     from paper_2510_19764_gb300 import abi, net
     T, B = 300, 6
     s = _setups.classifier(seed=3, n_in=64, N=128, K=4, lif=False, v_thr=0.6, T=T, max_B=B, spoken=True,
@@ -343,8 +343,15 @@ def test_predrawn_inputs_give_identical_records():
     for k in ("x_rec", "z_rec", "psi_rec", "d_rec", "v_rec", "a_rec", "y_rec", "ysum", "v", "a"):
         assert torch.equal(getattr(ref, k), getattr(got, k)), k
     assert int(net.spikes_from_bits(net.u32_to_numpy(got.z_rec), 128).sum()) > 0
+    packed = net.DeviceBatch(s.dev, tb.labels, tb.bin_len, tb.trial_ids, T, record_state=True)
+    abi.snn_classifier_pack(s.dev.handle)
+    abi.snn_draw_inputs(s.dev.handle, packed.desc, 0, T)
+    abi.snn_step_neurons_ex(s.dev.handle, packed.desc, 0, T, abi.SNN_STEP_INPUTS_READY | abi.SNN_STEP_PACKED_READY)
+    torch.cuda.synchronize()
+    for k in ("x_rec", "z_rec", "psi_rec", "d_rec", "v_rec", "a_rec", "y_rec", "ysum", "v", "a"):
+        assert torch.equal(getattr(ref, k), getattr(packed, k)), k
     with pytest.raises(abi.SnnError):
-        abi.snn_step_neurons_ex(s.dev.handle, got.desc, 0, T, 2)
+        abi.snn_step_neurons_ex(s.dev.handle, got.desc, 0, T, 4)
 
 
 def test_gradient_of_a_split_batch_is_the_sum_of_its_halves():
