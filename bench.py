@@ -928,7 +928,61 @@ def run_kernels(args):
                                          "frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 4),
                                          "peak_source": pk["source"]}}
     out["deepr_guided_vs_uniform"] = deepr_guided_timing(args, dev)
+    out["snn_rewire_topo"] = topo_rewire_timing(args, dev, pk)
     return out
+
+
+def topo_rewire_timing(args, dev, pk):
+    """Topographic rewiring (Sec. 2.2's elimination and distance-dependent formation) of
+    the lateral projection alone: a 112 x 112 sheet with 490 attempts per rewiring (one
+    CTA) and a 256 x 256 sheet with 65536 attempts (rows spread over the grid).  Mean
+    CUDA-event time per call after warm-up; algorithmic bytes = per row with attempts its
+    length word and 8 B per synapse read, per changed row its length and 8 B per synapse
+    written back.  The candidate bitfields live in shared memory and move no HBM bytes."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2510_19764_gb300 import abi, net
+    res = {}
+    for L, C, n_att in ((112, 32, 490), (256, 32, 65536)):
+        N = L * L
+        rag = synth.topo_initial(args.seed + 7, L, 1.0, 1.0, C, 0.2)
+        g = np.where(rag.ind >= 0, np.random.default_rng(args.seed).uniform(0, 0.2, rag.w.shape), 0.0)
+        r = net.DeviceRagged(rag.row_len, rag.ind, g.astype(np.float32), N, dtype=0, seed=args.seed + 8)
+        rw = net.topo_rewire(L, 1.0, 1.0, n_att, g_max=0.2)
+        stats = torch.zeros(4, dtype=torch.int64, device=dev)
+        times, bys, nrw = [], [], []
+        for rep in range(8):
+            before_len = r.row_len.long().clone()
+            before_ind = r.ind.clone()
+            stats.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            abi.snn_rewire_topo(r.handle, rw, rep, stats)
+            b.record()
+            b.synchronize()
+            st = stats.cpu().tolist()
+            changed = (r.row_len.long() != before_len) | (r.ind != before_ind).any(1)
+            # rows with attempts: the expected number of distinct rows among n_att uniform draws
+            touched = N * (1.0 - (1.0 - 1.0 / N) ** n_att)
+            by = touched * (4 + 8 * float(before_len.float().mean())) + \
+                int((4 + 8 * r.row_len.long()[changed]).sum())
+            if rep >= 3:
+                times.append(a.elapsed_time(b))
+                bys.append(by)
+                nrw.append(st[0] + st[1])
+        assert r.status() == abi.SNN_OK
+        ms = sum(times) / len(times)
+        by = sum(bys) / len(bys)
+        res[f"{L}x{L}"] = {"attempts": n_att, "ms": round(ms, 4), "form": "one CTA" if n_att <= 4096 else "grid",
+                           "rewired_synapses_per_call": round(sum(nrw) / len(nrw), 1),
+                           "attempts_per_s": round(n_att / (ms / 1e3), 1), "algorithmic_bytes": int(by),
+                           "roofline": {"bound": "hbm", "achieved": round(by / (ms / 1e3) / 1e9, 2),
+                                        "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                        "frac": round(by / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 5),
+                                        "peak_source": pk["source"]}}
+    return res
 
 
 def deepr_guided_timing(args, dev):

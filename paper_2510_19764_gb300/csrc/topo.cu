@@ -4,6 +4,7 @@
 // parallel rewiring rule (distance-dependent formation, weight-dependent elimination).
 #include "common.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -250,11 +251,133 @@ __device__ __forceinline__ int torus_d2(int i, int j, int L) {
     return dx * dx + dy * dy;
 }
 
-// One CTA.  Histogram of attempt rows, then one warp per row with attempts: candidate
-// selection without replacement in a warp-private shared-memory bitfield, stable
-// elimination by ballot compaction, and formation of the remaining candidates in
-// ascending target order.  Row data are read through L2 (ld.global.cg): inside the
-// fused step loop other CTAs of the cluster write them between calls.
+// One warp: the rewiring of row i with a attempts (Sec. 2.1.3): candidate selection
+// without replacement in the warp's shared-memory bitfield cand [Qw] (zero on entry and
+// on exit), stable elimination by ballot compaction, and formation of the remaining
+// candidates in ascending target order.  Counts are added to the lanes' registers.
+__device__ __forceinline__ void topo_rewire_row(const RewireK& k, const int i, const int a, int32_t* __restrict__ len,
+                                                int32_t* __restrict__ ind, float* __restrict__ w,
+                                                const uint64_t* __restrict__ thr_form, int32_t* status,
+                                                uint32_t* cand, long long& removed, long long& formed,
+                                                long long& overflow) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t tail_mask = (k.Q & 31) ? ~((1u << (k.Q & 31)) - 1u) : 0u;
+    for (int wi = lane; wi < k.Qw; wi += 32) cand[wi] = 0u;
+    __syncwarp();
+    // candidates without replacement: the kk-th is the m-th unselected target
+    for (int kk = 0; kk < a; ++kk) {
+        const u64x4 u = philox(k.seed, PH_TOPO_CAND, k.rewire, (uint64_t)i, (uint64_t)kk, 0);
+        const int mth = (int)mulhi_index(u.x, (uint64_t)(k.Q - kk));
+        int seen = 0, target = -1;
+        for (int wb = 0; wb < k.Qw && target < 0; wb += 32) {
+            const int wi = wb + lane;
+            uint32_t word = 0xffffffffu;
+            if (wi < k.Qw) {
+                word = cand[wi];
+                if (wi == k.Qw - 1) word |= tail_mask;
+            }
+            const int zeros = __popc(~word);
+            const int incl = warp_incl_scan(zeros);
+            const int excl = incl - zeros;
+            const uint32_t hm = __ballot_sync(0xffffffffu, mth >= seen + excl && mth < seen + incl);
+            if (hm) {
+                const int src = __ffs(hm) - 1;
+                int tg = -1;
+                if (lane == src) tg = wi * 32 + nth_set_bit(~word, mth - seen - excl);
+                target = __shfl_sync(0xffffffffu, tg, src);
+            }
+            seen += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0 && target >= 0) cand[target >> 5] |= 1u << (target & 31);
+        if (target < 0 && lane == 0) atomicOr(status, ST_STATE);
+        __syncwarp();
+    }
+    // elimination of existing synapses on candidates
+    const int n = __ldcg(len + i);
+    const size_t row = (size_t)i * k.C;
+    int wp = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int s = base + lane;
+        const bool valid = s < n;
+        int j = 0;
+        float g = 0.0f;
+        bool is_c = false, rm = false;
+        if (valid) {
+            j = __ldcg(ind + row + s);
+            g = __ldcg(w + row + s);
+            is_c = (cand[j >> 5] >> (j & 31)) & 1u;
+            if (is_c) {
+                const u64x4 u = philox(k.seed, PH_TOPO_DRAW, k.rewire, (uint64_t)i, (uint64_t)j, 0);
+                rm = u.x < (g < k.g_theta ? k.thr_dep : k.thr_pot);
+            }
+        }
+        const bool keep = valid && !rm;
+        const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+        removed += rm ? 1 : 0;
+        if (rm && k.elim_d2) atomicAdd(&k.elim_d2[torus_d2(i, j, k.L)], 1ull);
+        __syncwarp();
+        if (is_c) atomicAnd(&cand[j >> 5], ~(1u << (j & 31)));
+        if (keep) {
+            const int pos = wp + __popc(mask & lanemask_lt());
+            ind[row + pos] = j;
+            w[row + pos] = g;
+        }
+        wp += __popc(mask);
+        __syncwarp();
+    }
+    // formation of the remaining candidates, ascending target order
+    for (int wb = 0; wb < k.Qw; wb += 32) {
+        const int wi = wb + lane;
+        uint32_t word = (wi < k.Qw) ? cand[wi] : 0u;
+        uint32_t pass = 0;
+        for (uint32_t rest = word; rest; rest &= rest - 1u) {
+            const int bpos = __ffs(rest) - 1;
+            const int j = wi * 32 + bpos;
+            const u64x4 u = philox(k.seed, PH_TOPO_DRAW, k.rewire, (uint64_t)i, (uint64_t)j, 0);
+            if (u.x < thr_form[torus_d2(i, j, k.L)]) pass |= 1u << bpos;
+        }
+        const int cnt = __popc(pass);
+        const int incl = warp_incl_scan(cnt);
+        int rank = incl - cnt;
+        for (uint32_t rest = pass; rest; rest &= rest - 1u, ++rank) {
+            const int j = wi * 32 + __ffs(rest) - 1;
+            const int slot = wp + rank;
+            if (slot < k.C) {
+                ind[row + slot] = j;
+                w[row + slot] = k.g_new;
+                ++formed;
+                if (k.form_d2) atomicAdd(&k.form_d2[torus_d2(i, j, k.L)], 1ull);
+            } else {
+                ++overflow;
+            }
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        wp = min(wp + total, k.C);
+        if (wi < k.Qw) cand[wi] = 0u;
+        __syncwarp();
+    }
+    if (lane == 0) len[i] = wp;
+}
+
+// Warp totals of the rewiring counts added to stats (lane 0 of every warp).
+__device__ __forceinline__ void topo_flush_counts(snn_rewire_stats* stats, long long removed, long long formed,
+                                                  long long overflow, long long attempts, int lane) {
+    removed = warp_sum(removed);
+    formed = warp_sum(formed);
+    overflow = warp_sum(overflow);
+    attempts = lane == 0 ? attempts : 0;
+    attempts = warp_sum(attempts);
+    if (lane == 0 && stats && (removed | formed | overflow | attempts)) {
+        atomicAdd((unsigned long long*)&stats->removed, (unsigned long long)removed);
+        atomicAdd((unsigned long long*)&stats->formed, (unsigned long long)formed);
+        atomicAdd((unsigned long long*)&stats->overflow, (unsigned long long)overflow);
+        atomicAdd((unsigned long long*)&stats->attempts, (unsigned long long)attempts);
+    }
+}
+
+// One CTA.  Histogram of attempt rows, then one warp per row with attempts
+// (topo_rewire_row).  Row data are read through L2 (ld.global.cg): inside the fused step
+// loop other CTAs of the cluster write them between calls.
 __device__ void topo_rewire_cta(const RewireK& k, int32_t* __restrict__ len, int32_t* __restrict__ ind,
                                 float* __restrict__ w, const uint64_t* __restrict__ thr_form, int32_t* status,
                                 snn_rewire_stats* stats, unsigned char* smem) {
@@ -278,119 +401,14 @@ __device__ void topo_rewire_cta(const RewireK& k, int32_t* __restrict__ len, int
     __syncthreads();
     const int nr = *n_rows;
     uint32_t* cand = cand_all + (size_t)warp * k.Qw;
-    const uint32_t tail_mask = (k.Q & 31) ? ~((1u << (k.Q & 31)) - 1u) : 0u;
     long long removed = 0, formed = 0, overflow = 0, attempts = 0;
     for (int li = warp; li < nr; li += nwarps) {
         const int i = list[li];
         const int a = min(att[i], k.Q);
         attempts += a;
-        for (int wi = lane; wi < k.Qw; wi += 32) cand[wi] = 0u;
-        __syncwarp();
-        // candidates without replacement: the kk-th is the m-th unselected target
-        for (int kk = 0; kk < a; ++kk) {
-            const u64x4 u = philox(k.seed, PH_TOPO_CAND, k.rewire, (uint64_t)i, (uint64_t)kk, 0);
-            const int mth = (int)mulhi_index(u.x, (uint64_t)(k.Q - kk));
-            int seen = 0, target = -1;
-            for (int wb = 0; wb < k.Qw && target < 0; wb += 32) {
-                const int wi = wb + lane;
-                uint32_t word = 0xffffffffu;
-                if (wi < k.Qw) {
-                    word = cand[wi];
-                    if (wi == k.Qw - 1) word |= tail_mask;
-                }
-                const int zeros = __popc(~word);
-                const int incl = warp_incl_scan(zeros);
-                const int excl = incl - zeros;
-                const uint32_t hm = __ballot_sync(0xffffffffu, mth >= seen + excl && mth < seen + incl);
-                if (hm) {
-                    const int src = __ffs(hm) - 1;
-                    int tg = -1;
-                    if (lane == src) tg = wi * 32 + nth_set_bit(~word, mth - seen - excl);
-                    target = __shfl_sync(0xffffffffu, tg, src);
-                }
-                seen += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            if (lane == 0 && target >= 0) cand[target >> 5] |= 1u << (target & 31);
-            if (target < 0 && lane == 0) atomicOr(status, ST_STATE);
-            __syncwarp();
-        }
-        // elimination of existing synapses on candidates
-        const int n = __ldcg(len + i);
-        const size_t row = (size_t)i * k.C;
-        int wp = 0;
-        for (int base = 0; base < n; base += 32) {
-            const int s = base + lane;
-            const bool valid = s < n;
-            int j = 0;
-            float g = 0.0f;
-            bool is_c = false, rm = false;
-            if (valid) {
-                j = __ldcg(ind + row + s);
-                g = __ldcg(w + row + s);
-                is_c = (cand[j >> 5] >> (j & 31)) & 1u;
-                if (is_c) {
-                    const u64x4 u = philox(k.seed, PH_TOPO_DRAW, k.rewire, (uint64_t)i, (uint64_t)j, 0);
-                    rm = u.x < (g < k.g_theta ? k.thr_dep : k.thr_pot);
-                }
-            }
-            const bool keep = valid && !rm;
-            const uint32_t mask = __ballot_sync(0xffffffffu, keep);
-            removed += rm ? 1 : 0;
-            if (rm && k.elim_d2) atomicAdd(&k.elim_d2[torus_d2(i, j, k.L)], 1ull);
-            __syncwarp();
-            if (is_c) atomicAnd(&cand[j >> 5], ~(1u << (j & 31)));
-            if (keep) {
-                const int pos = wp + __popc(mask & lanemask_lt());
-                ind[row + pos] = j;
-                w[row + pos] = g;
-            }
-            wp += __popc(mask);
-            __syncwarp();
-        }
-        // formation of the remaining candidates, ascending target order
-        for (int wb = 0; wb < k.Qw; wb += 32) {
-            const int wi = wb + lane;
-            uint32_t word = (wi < k.Qw) ? cand[wi] : 0u;
-            uint32_t pass = 0;
-            for (uint32_t rest = word; rest; rest &= rest - 1u) {
-                const int bpos = __ffs(rest) - 1;
-                const int j = wi * 32 + bpos;
-                const u64x4 u = philox(k.seed, PH_TOPO_DRAW, k.rewire, (uint64_t)i, (uint64_t)j, 0);
-                if (u.x < thr_form[torus_d2(i, j, k.L)]) pass |= 1u << bpos;
-            }
-            const int cnt = __popc(pass);
-            const int incl = warp_incl_scan(cnt);
-            int rank = incl - cnt;
-            for (uint32_t rest = pass; rest; rest &= rest - 1u, ++rank) {
-                const int j = wi * 32 + __ffs(rest) - 1;
-                const int slot = wp + rank;
-                if (slot < k.C) {
-                    ind[row + slot] = j;
-                    w[row + slot] = k.g_new;
-                    ++formed;
-                    if (k.form_d2) atomicAdd(&k.form_d2[torus_d2(i, j, k.L)], 1ull);
-                } else {
-                    ++overflow;
-                }
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            wp = min(wp + total, k.C);
-            if (wi < k.Qw) cand[wi] = 0u;
-            __syncwarp();
-        }
-        if (lane == 0) len[i] = wp;
+        topo_rewire_row(k, i, a, len, ind, w, thr_form, status, cand, removed, formed, overflow);
     }
-    removed = warp_sum(removed);
-    formed = warp_sum(formed);
-    overflow = warp_sum(overflow);
-    attempts = lane == 0 ? attempts : 0;
-    attempts = warp_sum(attempts);
-    if (lane == 0 && stats && (removed | formed | overflow | attempts)) {
-        atomicAdd((unsigned long long*)&stats->removed, (unsigned long long)removed);
-        atomicAdd((unsigned long long*)&stats->formed, (unsigned long long)formed);
-        atomicAdd((unsigned long long*)&stats->overflow, (unsigned long long)overflow);
-        atomicAdd((unsigned long long*)&stats->attempts, (unsigned long long)attempts);
-    }
+    topo_flush_counts(stats, removed, formed, overflow, attempts, lane);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -398,6 +416,48 @@ __global__ void __launch_bounds__(1024)
                   const uint64_t* __restrict__ thr_form, int32_t* status, snn_rewire_stats* stats) {
     extern __shared__ __align__(16) unsigned char smem[];
     topo_rewire_cta(k, len, ind, w, thr_form, status, stats, smem);
+}
+
+// Many CTAs (maps too large for one CTA's shared memory, or many attempts): the attempt
+// histogram and the list of rows with attempts go to the handle's scratch in global
+// memory, then every warp of the grid takes rows from the list.  A row's rewiring does not
+// depend on which warp takes it or when, so the results equal the one-CTA path's.
+__global__ void k_topo_att(RewireK k, int32_t* __restrict__ att) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < (k.n_att + 3) / 4;
+         g += (long long)gridDim.x * blockDim.x) {
+        const u64x4 u = philox(k.seed, PH_TOPO_ATT, k.rewire, (uint64_t)g, 0, 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * g + q < k.n_att) atomicAdd(&att[(int)mulhi_index(u[q], (uint64_t)k.P)], 1);
+    }
+}
+
+__global__ void k_topo_list(RewireK k, const int32_t* __restrict__ att, int32_t* __restrict__ list,
+                            int32_t* __restrict__ n_rows) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.P; i += gridDim.x * blockDim.x)
+        if (att[i] > 0) list[atomicAdd(n_rows, 1)] = i;
+}
+
+constexpr int TOPO_ROW_THREADS = 256;
+
+__global__ void __launch_bounds__(TOPO_ROW_THREADS)
+    k_topo_rewire_rows(RewireK k, const int32_t* __restrict__ att, const int32_t* __restrict__ list,
+                       const int32_t* __restrict__ n_rows, int32_t* __restrict__ len, int32_t* __restrict__ ind,
+                       float* __restrict__ w, const uint64_t* __restrict__ thr_form, int32_t* status,
+                       snn_rewire_stats* stats) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* cand = (uint32_t*)smem + (size_t)warp * k.Qw;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int nr = *n_rows;
+    long long removed = 0, formed = 0, overflow = 0, attempts = 0;
+    for (int li = blockIdx.x * (blockDim.x >> 5) + warp; li < nr; li += nw) {
+        const int i = list[li];
+        const int a = min(att[i], k.Q);
+        attempts += a;
+        topo_rewire_row(k, i, a, len, ind, w, thr_form, status, cand, removed, formed, overflow);
+    }
+    topo_flush_counts(stats, removed, formed, overflow, attempts, lane);
 }
 
 static size_t rewire_smem(int P, int n_att, int Qw, int threads) {
@@ -454,9 +514,15 @@ static snn_status rewire_prepare(snn_ragged* r, const snn_topo_rewire* p, Rewire
     k.rewire = 0;
     k.elim_d2 = (unsigned long long*)p->elim_d2;
     k.form_d2 = (unsigned long long*)p->form_d2;
-    SNN_REQUIRE(rewire_smem(k.P, k.n_att, k.Qw, 1024) <= 227 * 1024, "snn_rewire_topo: P = %d too large for one CTA",
-                k.P);
+    SNN_REQUIRE((size_t)(TOPO_ROW_THREADS / 32) * k.Qw * 4 <= 227 * 1024, "snn_rewire_topo: Q = %d too large",
+                k.Q);
     return SNN_OK;
+}
+
+// The one-CTA form serves maps whose attempt histogram fits one CTA's shared memory and
+// few attempts (one launch, the paper's sizes); others spread the rows over the grid.
+static bool rewire_one_cta(const RewireK& k) {
+    return rewire_smem(k.P, k.n_att, k.Qw, 1024) <= 227 * 1024 && k.n_att <= 4096;
 }
 
 static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t rewire_idx, snn_rewire_stats* stats,
@@ -466,11 +532,30 @@ static snn_status rewire_launch(snn_ragged* r, const snn_topo_rewire* p, int64_t
     if (e != SNN_OK) return e;
     k.rewire = (uint64_t)rewire_idx;
     const snn_ragged_desc& d = r->d;
-    const int threads = 1024;
-    const size_t smem = rewire_smem(k.P, k.n_att, k.Qw, threads);
+    if (rewire_one_cta(k)) {
+        const int threads = 1024;
+        const size_t smem = rewire_smem(k.P, k.n_att, k.Qw, threads);
+        if (smem > 48 * 1024)
+            SNN_CUDA(cudaFuncSetAttribute(k_topo_rewire, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_topo_rewire<<<1, threads, smem, s>>>(k, d.row_len, d.ind, (float*)d.w, r->thr_form, r->status, stats);
+        SNN_LAUNCH_CHECK();
+        return SNN_OK;
+    }
+    int32_t* att = r->cnt;            // handle scratch [P] (also DEEP R's; calls on a handle are ordered)
+    int32_t* list = r->taken;         // [P]
+    int32_t* n_rows = r->scal;        // one word
+    SNN_CUDA(cudaMemsetAsync(att, 0, (size_t)k.P * sizeof(int32_t), s));
+    SNN_CUDA(cudaMemsetAsync(n_rows, 0, sizeof(int32_t), s));
+    k_topo_att<<<std::max(1, std::min(ceil_div((k.n_att + 3) / 4, 256), 4 * sm_count())), 256, 0, s>>>(k, att);
+    SNN_LAUNCH_CHECK();
+    k_topo_list<<<std::max(1, std::min(ceil_div(k.P, 256), 4 * sm_count())), 256, 0, s>>>(k, att, list, n_rows);
+    SNN_LAUNCH_CHECK();
+    const size_t smem = (size_t)(TOPO_ROW_THREADS / 32) * k.Qw * sizeof(uint32_t);
     if (smem > 48 * 1024)
-        SNN_CUDA(cudaFuncSetAttribute(k_topo_rewire, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_topo_rewire<<<1, threads, smem, s>>>(k, d.row_len, d.ind, (float*)d.w, r->thr_form, r->status, stats);
+        SNN_CUDA(cudaFuncSetAttribute(k_topo_rewire_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = std::max(1, std::min(ceil_div(std::min(k.n_att, k.P), TOPO_ROW_THREADS / 32), 4 * sm_count()));
+    k_topo_rewire_rows<<<grid, TOPO_ROW_THREADS, smem, s>>>(k, att, list, n_rows, d.row_len, d.ind, (float*)d.w,
+                                                             r->thr_form, r->status, stats);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }

@@ -25,7 +25,11 @@ def _rewire_args(p, L, name):
 
 
 @pytest.mark.parametrize("L,C,n_att,name", [(16, 16, 60, "ff"), (16, 16, 60, "lat"), (32, 64, 40, "ff"),
-                                            (32, 64, 40, "lat"), (8, 6, 500, "ff"), (16, 8, 3000, "lat")])
+                                            (32, 64, 40, "lat"), (8, 6, 500, "ff"), (16, 8, 3000, "lat"),
+                                            # many attempts, and a map too large for one CTA's
+                                            # shared memory: rows spread over the grid
+                                            (16, 8, 5000, "lat"), (64, 16, 6000, "ff"),
+                                            (256, 8, 20000, "lat")])
 def test_rewire_bit_exact(L, C, n_att, name):
     from paper_2510_19764_gb300 import abi, net
     p = ot.TopoParams(L=L, n_att=n_att)
@@ -37,7 +41,7 @@ def test_rewire_bit_exact(L, C, n_att, name):
     rw = net.topo_rewire(L, pf, sg, n_att, g_max=p.g_max)
     state = (rag.row_len.copy(), rag.ind.copy(), g.copy())
     changes = 0
-    for ridx in range(10):
+    for ridx in range(3 if L >= 256 else 10):
         stats = torch.zeros(4, dtype=torch.int64, device="cuda")
         abi.snn_rewire_topo(d.handle, rw, ridx, stats)
         torch.cuda.synchronize()
