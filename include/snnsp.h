@@ -60,7 +60,7 @@ typedef void* snn_stream;        /* cudaStream_t */
 /* Message for the most recent failing call on this host thread ("" if none). */
 const char* snn_last_error(void);
 /* ABI version of this header (bumped on any incompatible change). */
-int32_t snn_abi_version(void);   /* 7 */
+int32_t snn_abi_version(void);   /* 8 */
 
 /* ==================================================================================
  * Ragged sparse matrix (Sec. 2.1, Fig. 1; DEEP R bitfields Sec. 2.1.2, Fig. 2)
@@ -120,6 +120,32 @@ snn_status snn_ragged_status(snn_ragged* r, snn_stream stream);
  * accumulated into (the caller zeroes it).  Weights are shared by all instances. */
 snn_status snn_propagate(const snn_ragged* r, const uint32_t* pre_bits, int32_t B,
                          int64_t* post_acc, snn_stream stream);
+
+/* Target-tiled propagation (Fig. 1's operation, regrouped for shared-memory
+ * accumulation).  A plan holds a copy of a handle's synapses grouped by target tile (W
+ * consecutive targets; W chosen at create time so that the tiles spread over the GPU):
+ * within tile k, entry (row i << 12 | j - kW, w) for every synapse i -> j.  One CTA per
+ * (tile, group of 16 instances) reads its tile's entries once for all those instances,
+ * adds the weights of rows spiking in each instance into exact 64-bit shared-memory
+ * accumulators (two 32-bit reductions with an explicit carry) and adds them to post_acc
+ * once: the result is the same int64 value snn_propagate gives (fixed-point sums do not
+ * depend on order), with no global atomics.
+ *  snn_create_prop_plan: allocates the plan's arrays (P*C entries, per-tile offsets, a
+ *    per-row instance mask for max_B instances); P <= 2^20.  The plan refers to the
+ *    handle, which must outlive it.  SNN_EINVAL / SNN_ENOMEM.
+ *  snn_prop_plan_pack: rebuilds the tiles from the handle's current row_len, ind and w
+ *    (asynchronous, capturable; call again after anything changes the synapses: an
+ *    optimiser step, a rewiring, a caller edit).  A row length outside [0, C] or a
+ *    target outside [0, Q) is skipped and sets SNN_ESTATE in the handle's status word.
+ *  snn_propagate_tiled: as snn_propagate (same pre_bits, post_acc and result) from the
+ *    last pack; B <= max_B.
+ *  snn_destroy_prop_plan: frees the plan (NULL is a no-op). */
+typedef struct snn_prop_plan snn_prop_plan;
+snn_status snn_create_prop_plan(snn_ragged* r, int32_t max_B, snn_prop_plan** out);
+snn_status snn_prop_plan_pack(snn_prop_plan* plan, snn_stream stream);
+snn_status snn_propagate_tiled(const snn_prop_plan* plan, const uint32_t* pre_bits, int32_t B,
+                               int64_t* post_acc, snn_stream stream);
+snn_status snn_destroy_prop_plan(snn_prop_plan* plan);
 
 /* DEEP R rewiring after the optimiser step (Sec. 2.1.2, Fig. 2B-C).
  *  elimination: slot s of row i is removed iff its weight's sign is strictly opposite

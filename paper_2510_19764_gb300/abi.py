@@ -31,7 +31,8 @@ EXPORTED = [
     "snn_draw_inputs", "snn_step_neurons_ex", "snn_topo_connectivity", "snn_ragged_set_deepr_guide",
     "snn_test_wait_timeout", "snn_ragged_add_row", "snn_ragged_remove_row", "snn_adam_bias", "snn_topo_derive",
     "snn_classifier_set_row_schedule", "snn_multi_create", "snn_multi_destroy", "snn_multi_run", "snn_multi_post",
-    "snn_multi_status", "snn_multi_set_trace", "snn_classifier_pack",
+    "snn_multi_status", "snn_multi_set_trace", "snn_classifier_pack", "snn_create_prop_plan",
+    "snn_prop_plan_pack", "snn_propagate_tiled", "snn_destroy_prop_plan",
 ]
 
 
@@ -129,6 +130,10 @@ def load() -> C.CDLL:
         "snn_destroy_ragged": (i32, [vp]),
         "snn_ragged_status": (i32, [vp, vp]),
         "snn_propagate": (i32, [vp, vp, i32, vp, vp]),
+        "snn_create_prop_plan": (i32, [vp, i32, P(vp)]),
+        "snn_prop_plan_pack": (i32, [vp, vp]),
+        "snn_propagate_tiled": (i32, [vp, vp, i32, vp, vp]),
+        "snn_destroy_prop_plan": (i32, [vp]),
         "snn_rewire_deepr": (i32, [vp, i64, vp, vp]),
         "snn_create_classifier": (i32, [P(ClassifierDesc), P(vp)]),
         "snn_destroy_classifier": (i32, [vp]),
@@ -214,6 +219,24 @@ def snn_ragged_status(h: int, stream=None) -> int:
 
 def snn_propagate(h: int, pre_bits, B: int, post_acc, stream=None) -> None:
     check(load().snn_propagate(h, ptr(pre_bits), B, ptr(post_acc), stream_ptr(stream)))
+
+
+def snn_create_prop_plan(h: int, max_B: int) -> int:
+    out = vp()
+    check(load().snn_create_prop_plan(h, max_B, C.byref(out)))
+    return out.value
+
+
+def snn_prop_plan_pack(plan: int, stream=None) -> None:
+    check(load().snn_prop_plan_pack(plan, stream_ptr(stream)))
+
+
+def snn_propagate_tiled(plan: int, pre_bits, B: int, post_acc, stream=None) -> None:
+    check(load().snn_propagate_tiled(plan, ptr(pre_bits), B, ptr(post_acc), stream_ptr(stream)))
+
+
+def snn_destroy_prop_plan(plan: int) -> None:
+    check(load().snn_destroy_prop_plan(plan))
 
 
 def snn_rewire_deepr(h: int, rewire_idx: int, stats=None, stream=None) -> None:

@@ -289,12 +289,16 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
         }
         __syncthreads();
         // ---------------- phase B: neurons; spike lists of step t
-        if (warp == 0 && lane < Win) {
-            uint32_t word = xnext;                 // x^t
-            if (t + 1 < t_end) xnext = xrec_b[(size_t)(t + 1) * Win + lane];
-            const int pos = atomicAdd(&lcnt[cur], __popc(word));
-            for (int k = 0; word; ++k, word &= word - 1u) lcur[pos + k] = lane * 32 + __ffs(word) - 1;
-            xw[lane] = 0u;
+        if (warp == 0) {
+            // x^t: one list reservation for the warp, positions by a prefix sum of the counts
+            uint32_t word = lane < Win ? xnext : 0u;
+            if (lane < Win && t + 1 < t_end) xnext = xrec_b[(size_t)(t + 1) * Win + lane];
+            const int cnt = __popc(word);
+            const int incl = warp_incl_scan(cnt);
+            int base = 0;
+            if (lane == 31 && incl) base = atomicAdd(&lcnt[cur], incl);
+            base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+            for (int k = 0; word; ++k, word &= word - 1u) lcur[base + k] = lane * 32 + __ffs(word) - 1;
         }
         if (warp == RO_WARP && lane < K) {         // y^t from the readout sums W_out z^{t-1}
             yk = p.alpha * yk + acc_real<real>(Iacc + N + 32 + lane) + bk;

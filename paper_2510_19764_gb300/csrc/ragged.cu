@@ -220,7 +220,7 @@ using namespace snn;
 extern "C" {
 
 const char* snn_last_error(void) { return g_last_error.c_str(); }
-int32_t snn_abi_version(void) { return 7; }
+int32_t snn_abi_version(void) { return 8; }
 
 snn_status snn_create_ragged(const snn_ragged_desc* d, int32_t init_bits, snn_stream stream, snn_ragged** out) {
     clear_error();

@@ -38,7 +38,7 @@ def test_binding_covers_every_declared_symbol(lib_path):
     from paper_2510_19764_gb300 import abi
     assert sorted(abi.EXPORTED) == _declared_symbols()
     lib = abi.load()
-    assert lib.snn_abi_version() == 7
+    assert lib.snn_abi_version() == 8
     for name in abi.EXPORTED:
         assert callable(getattr(abi, name)), name
 
