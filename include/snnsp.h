@@ -124,7 +124,7 @@ snn_status snn_propagate(const snn_ragged* r, const uint32_t* pre_bits, int32_t 
 /* Target-tiled propagation (Fig. 1's operation, regrouped for shared-memory
  * accumulation).  A plan holds a copy of a handle's synapses grouped by target tile (W
  * consecutive targets; W chosen at create time so that the tiles spread over the GPU):
- * within tile k, entry (row i << 12 | j - kW, w) for every synapse i -> j.  One CTA per
+ * within tile k, entry (row i << 12 | j - kW, w_ij in fixed point) for every synapse i -> j.  One CTA per
  * (tile, group of 16 instances) reads its tile's entries once for all those instances,
  * adds the weights of rows spiking in each instance into exact 64-bit shared-memory
  * accumulators (two 32-bit reductions with an explicit carry) and adds them to post_acc

@@ -64,20 +64,27 @@ __device__ __forceinline__ double exp_real(double x) { return exp(x); }
 // slot as a signed 32-bit value, w_lo = bits 19..0): both sums use native 32-bit
 // shared-memory atomics and are exact: L takes at most one addend (< 2^20) per spiking
 // row, rows hold no repeated target and n_in + N <= 3072 < 4096; H wraps modulo 2^32
-// like the 52-bit weights.  The total is 2^20 H + L.
-__device__ __forceinline__ void acc_add(unsigned* acc, unsigned long long w) {
+// like the 52-bit weights.  The total is 2^20 H + L.  The H words of all accumulators
+// come first, then the L words (NA apart), so that lanes adding to consecutive targets
+// hit consecutive banks: interleaved pairs would put every H word on an even bank and
+// double the shared-memory wavefronts of a warp's scattered additions.
+__device__ __forceinline__ void acc_add(unsigned* acc, unsigned long long w, int NA) {
     const unsigned lo = (unsigned)w, hi = (unsigned)(w >> 32);
-    unsigned* a = acc + 2 * (hi >> 20);                   // target index: bits 63..52
+    unsigned* a = acc + (hi >> 20);                       // target index: bits 63..52
     atomicAdd(a, __funnelshift_r(lo, hi, 20));            // bits 51..20
-    atomicAdd(a + 1, lo & 0xFFFFFu);                      // bits 19..0
+    atomicAdd(a + NA, lo & 0xFFFFFu);                     // bits 19..0
 }
-// The accumulated sum 2^20 H + L in real units (40 fractional bits): H 2^-20 + L 2^-40,
-// each product exact, one rounding in the sum (for double the same value as converting
-// the 64-bit integer first).
+// The accumulated sum 2^20 H + L of accumulator a (L at a + NA) in real units (40
+// fractional bits): H 2^-20 + L 2^-40, each product exact, one rounding in the sum (for
+// double the same value as converting the 64-bit integer first).
 template <typename real>
-__device__ __forceinline__ real acc_real(const long long* acc) {
-    const unsigned* a = (const unsigned*)acc;
-    return (real)(int)a[0] * (real)9.5367431640625e-07 + (real)a[1] * (real)9.094947017729282e-13;
+__device__ __forceinline__ real acc_real(const unsigned* a, int NA) {
+    return (real)(int)a[0] * (real)9.5367431640625e-07 + (real)a[NA] * (real)9.094947017729282e-13;
+}
+// Clears accumulator a.
+__device__ __forceinline__ void acc_zero(unsigned* a, int NA) {
+    a[0] = 0u;
+    a[NA] = 0u;
 }
 
 // Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
@@ -145,8 +152,9 @@ constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time (defau
 // wide forms hold 16 loads per lane in flight (fewer round trips per step, more
 // registers: they suit the persistent kernel, whose CTAs have room for them).
 template <int FR, int nwarps, int CH = 4>
-__device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lprv, int n_rows, const int* lens,
-                                                    const unsigned long long* pk, int Cf, int R, int warp, int lane) {
+__device__ __forceinline__ void propagate_rows_warp(unsigned* acc, int NA, const int* lprv, int n_rows,
+                                                    const int* lens, const unsigned long long* pk, int Cf, int R,
+                                                    int warp, int lane) {
     for (int k = warp; k < n_rows; k += FR * nwarps) {
         int nr[FR];
         const unsigned long long* pr[FR];
@@ -169,7 +177,7 @@ __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lp
             for (int q = 0; q < CH; ++q)
 #pragma unroll
                 for (int u = 0; u < FR; ++u)
-                    if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q]);
+                    if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q], NA);
         }
     }
 }
@@ -177,7 +185,8 @@ __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, const int* lp
 // Row per block: every warp works on every spiking row, warp w taking the row's 32-slot
 // chunks w, w + nwarps, ...; two rows in flight (suits few long rows).
 template <int nwarps>
-__device__ __forceinline__ void propagate_rows_block(unsigned* acc, const int* lprv, int n_rows, const int* lens,
+__device__ __forceinline__ void propagate_rows_block(unsigned* acc, int NA, const int* lprv, int n_rows,
+                                                     const int* lens,
                                                      const unsigned long long* pk, int Cf, int warp, int lane) {
     for (int k = 0; k < n_rows; k += 2) {
         const int r0 = lprv[k];
@@ -189,8 +198,8 @@ __device__ __forceinline__ void propagate_rows_block(unsigned* acc, const int* l
         for (int s0 = warp * 32; s0 < nmax; s0 += nwarps * 32) {
             const unsigned long long a = s0 < n0 ? p0[s0 + lane] : 0ull;
             const unsigned long long b = s0 < n1 ? p1[s0 + lane] : 0ull;
-            if (s0 < n0) acc_add(acc, a);
-            if (s0 < n1) acc_add(acc, b);
+            if (s0 < n0) acc_add(acc, a, NA);
+            if (s0 < n1) acc_add(acc, b, NA);
         }
     }
 }
@@ -201,8 +210,9 @@ template <typename real, int NPT, int TH, bool WIDE = false>
 __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const int b, unsigned char* smem) {
     const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh, n_in = p.n_in;
     const int R = n_in + N;
-    long long* Iacc = (long long*)smem;           // [N + 64]: neurons, 32 per-lane spares, readouts
-    int* lens = (int*)(Iacc + N + 64);            // [R + 1] packed row lengths (row R: empty)
+    const int NA = N + 64;                        // accumulators: neurons, 32 per-lane spares, readouts
+    unsigned* acc = (unsigned*)smem;              // [2][NA]: H words, then L words
+    int* lens = (int*)(acc + 2 * NA);             // [R + 1] packed row lengths (row R: empty)
     int* list = lens + R + 1;                     // [2][R] spiking rows by step parity
     int* lcnt = list + 2 * R;                     // [2]
     uint32_t* xw = (uint32_t*)(lcnt + 2);         // [Win] input spike words of the current step
@@ -223,7 +233,7 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             vr[q] = j < N ? p.v[(size_t)b * N + j] : real(0);
             ar[q] = j < N ? p.a[(size_t)b * N + j] : real(0);
         }
-        for (int j = tid; j < N + 64; j += TH) Iacc[j] = 0;
+        for (int j = tid; j < 2 * NA; j += TH) acc[j] = 0u;
         for (int j = tid; j < N; j += TH) lens[n_in + j] = p.rec_len[j] + K;
         for (int i = tid; i < n_in; i += TH) lens[i] = p.in_len[i];
         if (tid == 0) lens[R] = 0;
@@ -258,7 +268,6 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
     real* d_b = p.d_rec ? p.d_rec + (size_t)b * p.T * K : nullptr;
     uint32_t xnext = (warp == 0 && lane < Win && t0 < t_end) ? xrec_b[(size_t)t0 * Win + lane] : 0u;
     __syncthreads();
-    unsigned* acc = (unsigned*)Iacc;
 
     for (int t = t0; t < t_end; ++t) {
         const int cur = t & 1, prv = cur ^ 1;
@@ -275,17 +284,17 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
         }
         if (tid == 32) lcnt[cur] = 0;
         switch (p.sched) {
-            case SNN_ROWS_PER_BLOCK: propagate_rows_block<nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, warp, lane); break;
-            case SNN_ROWS_PER_WARP: propagate_rows_warp<1, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+            case SNN_ROWS_PER_BLOCK: propagate_rows_block<nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, warp, lane); break;
+            case SNN_ROWS_PER_WARP: propagate_rows_warp<1, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
             case SNN_ROWS_WIDE:
-                if (WIDE) propagate_rows_warp<2, nwarps, 8>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
-                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                if (WIDE) propagate_rows_warp<2, nwarps, 8>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
                 break;
             case SNN_ROWS_QUAD:
-                if (WIDE) propagate_rows_warp<4, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
-                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                if (WIDE) propagate_rows_warp<4, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
                 break;
-            default: propagate_rows_warp<FWD_ROWS, nwarps>(acc, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+            default: propagate_rows_warp<FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
         }
         __syncthreads();
         // ---------------- phase B: neurons; spike lists of step t
@@ -301,8 +310,8 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             for (int k = 0; word; ++k, word &= word - 1u) lcur[base + k] = lane * 32 + __ffs(word) - 1;
         }
         if (warp == RO_WARP && lane < K) {         // y^t from the readout sums W_out z^{t-1}
-            yk = p.alpha * yk + acc_real<real>(Iacc + N + 32 + lane) + bk;
-            Iacc[N + 32 + lane] = 0;
+            yk = p.alpha * yk + acc_real<real>(acc + N + 32 + lane, NA) + bk;
+            acc_zero(acc + N + 32 + lane, NA);
             ysk += yk;
             if (d_b) d_b[(size_t)t * K + lane] = yk;
             if (p.y_rec) p.y_rec[((size_t)b * p.T + t) * K + lane] = yk;
@@ -313,8 +322,8 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             const int j = tid + q * TH;
             bool spk = false;
             if (j < N) {
-                const real I = acc_real<real>(Iacc + j);
-                Iacc[j] = 0;
+                const real I = acc_real<real>(acc + j, NA);
+                acc_zero(acc + j, NA);
                 const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
                 const real v = p.alpha * (zp ? vr[q] - p.v_thr : vr[q]) + I;
                 const real aa = p.rho * ar[q] + (zp ? real(1) : real(0));

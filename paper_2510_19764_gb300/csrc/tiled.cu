@@ -29,6 +29,7 @@ constexpr int PLAN_RB = 64;          // rows per row block of the counting sort
 constexpr int PLAN_IG = 16;          // instances per propagation CTA (one 16-bit mask per row)
 constexpr int PLAN_LT_BITS = 12;     // local target bits of an entry key (W <= 4096)
 constexpr int PLAN_THREADS = 512;
+constexpr int PLAN_U = 8;            // entries a propagation thread has in flight
 
 // A row's length, or -1 when it is outside [0, C] (the row is skipped and flagged).
 __device__ __forceinline__ int plan_row_len(const int32_t* row_len, int i, int C) {
@@ -123,12 +124,12 @@ __global__ void k_plan_scan_base(int32_t* __restrict__ tile_base, int ntiles) {
 }
 
 // Pass 4: each row block places its synapses in its reserved range of every tile (the
-// same skips as pass 1, so the counts match).
+// same skips as pass 1, so the counts match), weights converted to fixed point.
 template <typename real>
 __global__ void k_plan_scatter(const int32_t* __restrict__ row_len, const int32_t* __restrict__ ind,
                                const real* __restrict__ w, int P, int Q, int C, int W, int ntiles, int nrb,
                                const int32_t* __restrict__ cnt, const int32_t* __restrict__ tile_base,
-                               uint32_t* __restrict__ keys, real* __restrict__ wts) {
+                               uint32_t* __restrict__ keys, long long* __restrict__ fx) {
     extern __shared__ int pos[];
     const int rb = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) pos[t] = tile_base[t] + cnt[(size_t)t * nrb + rb];
@@ -142,46 +143,41 @@ __global__ void k_plan_scatter(const int32_t* __restrict__ row_len, const int32_
             const int t = j / W;
             const int e = atomicAdd(&pos[t], 1);
             keys[e] = ((uint32_t)i << PLAN_LT_BITS) | (uint32_t)(j - t * W);
-            wts[e] = w[g];
+            fx[e] = to_fixed(w[g]);
         }
     }
 }
 
-// Per call: mask[g][i] bit q = row i spiked in instance 16 g + q.  Thread = (group, word).
+// Per call: mask[g][i] bit q = row i spiked in instance 16 g + q.  Thread = (group, row);
+// the 32 threads of a warp share each instance's spike word.
 __global__ void k_plan_rowmask(const uint32_t* __restrict__ pre_bits, int B, int P, int Pw,
                                uint16_t* __restrict__ mask) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int groups = (B + PLAN_IG - 1) / PLAN_IG;
-    if (k >= (long long)groups * Pw) return;
-    const int g = (int)(k / Pw), wd = (int)(k % Pw);
-    uint32_t bits[PLAN_IG];
+    if (k >= (long long)groups * P) return;
+    const int g = (int)(k / P), i = (int)(k % P);
+    uint32_t v = 0;
 #pragma unroll
     for (int q = 0; q < PLAN_IG; ++q) {
         const int b = g * PLAN_IG + q;
-        bits[q] = b < B ? pre_bits[(size_t)b * Pw + wd] : 0u;
+        if (b < B) v |= ((pre_bits[(size_t)b * Pw + (i >> 5)] >> (i & 31)) & 1u) << q;
     }
-    uint16_t* m = mask + (size_t)g * P + (size_t)wd * 32;
-    const int nrow = min(32, P - wd * 32);
-    for (int r = 0; r < nrow; ++r) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int q = 0; q < PLAN_IG; ++q) v |= ((bits[q] >> r) & 1u) << q;
-        m[r] = (uint16_t)v;
-    }
+    mask[k] = (uint16_t)v;
 }
 
-// Exact 64-bit accumulation in shared memory from 32-bit atomics (see the file comment).
-__device__ __forceinline__ void acc64_add(uint32_t* a, unsigned long long x) {
+// Exact 64-bit accumulation in shared memory from 32-bit atomics (see the file comment):
+// low word at lo, high word at lo + n_acc.  The low and high words are separate arrays so
+// that lanes adding to consecutive accumulators hit consecutive banks.
+__device__ __forceinline__ void acc64_add(uint32_t* lo_w, int n_acc, unsigned long long x) {
     const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
-    const uint32_t old = atomicAdd(a, lo);
-    atomicAdd(a + 1, hi + (old + lo < lo ? 1u : 0u));
+    const uint32_t old = atomicAdd(lo_w, lo);
+    atomicAdd(lo_w + n_acc, hi + (old + lo < lo ? 1u : 0u));
 }
 
-// One CTA per (tile, instance group): accumulators acc[q][lt] (q < IG instances of the
-// group, lt < W local targets) as {low, high} 32-bit pairs.
-template <typename real>
+// One CTA per (tile, instance group): accumulator q * W + lt for instance q < IG of the
+// group and local target lt < W.
 __global__ void __launch_bounds__(PLAN_THREADS)
-    k_propagate_tiled(const uint32_t* __restrict__ keys, const real* __restrict__ wts,
+    k_propagate_tiled(const uint32_t* __restrict__ keys, const long long* __restrict__ fx,
                       const int32_t* __restrict__ tile_base, const uint16_t* __restrict__ mask, int P, int Q,
                       int W, int IG, int B, long long* __restrict__ post_acc) {
     extern __shared__ __align__(16) uint32_t accs[];
@@ -192,20 +188,34 @@ __global__ void __launch_bounds__(PLAN_THREADS)
     for (int k = threadIdx.x; k < 2 * n_acc; k += blockDim.x) accs[k] = 0u;
     __syncthreads();
     const uint16_t* mg = mask + (size_t)g * P;
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const uint32_t key = keys[e];
-        uint32_t m = mg[key >> PLAN_LT_BITS];
-        if (!m) continue;
-        const unsigned long long x = (unsigned long long)to_fixed(wts[e]);
-        uint32_t* a = accs + 2 * (key & ((1u << PLAN_LT_BITS) - 1u));
-        for (; m; m &= m - 1u) acc64_add(a + 2 * W * (__ffs(m) - 1), x);
+    // PLAN_U entries per thread in flight: their keys and weights are loaded together,
+    // then their masks, then the additions
+    const int stride = blockDim.x * PLAN_U;
+    for (int e = e0 + threadIdx.x; e < e1; e += stride) {
+        uint32_t key[PLAN_U];
+        long long xv[PLAN_U];
+#pragma unroll
+        for (int u = 0; u < PLAN_U; ++u) {
+            const int eu = e + u * blockDim.x;
+            key[u] = eu < e1 ? keys[eu] : 0u;
+            xv[u] = eu < e1 ? fx[eu] : 0ll;
+        }
+        uint32_t m[PLAN_U];
+#pragma unroll
+        for (int u = 0; u < PLAN_U; ++u) m[u] = e + u * blockDim.x < e1 ? mg[key[u] >> PLAN_LT_BITS] : 0u;
+#pragma unroll
+        for (int u = 0; u < PLAN_U; ++u) {
+            uint32_t* a = accs + (key[u] & ((1u << PLAN_LT_BITS) - 1u));
+            for (uint32_t mm = m[u]; mm; mm &= mm - 1u)
+                acc64_add(a + W * (__ffs(mm) - 1), n_acc, (unsigned long long)xv[u]);
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n_acc; k += blockDim.x) {
         const int q = k / W, lt = k - q * W;
         const int b = g * PLAN_IG + q, j = tile * W + lt;
         if (b < B && j < Q) {
-            const unsigned long long v = ((unsigned long long)accs[2 * k + 1] << 32) | accs[2 * k];
+            const unsigned long long v = ((unsigned long long)accs[n_acc + k] << 32) | accs[k];
             if (v) post_acc[(size_t)b * Q + j] += (long long)v;
         }
     }
@@ -217,7 +227,7 @@ struct snn_prop_plan {
     snn_ragged* r;
     int32_t W, ntiles, nrb, IG, max_B;
     uint32_t* keys;        // [P*C] entry keys, grouped by tile
-    void* wts;             // [P*C] entry weights (the handle's dtype)
+    long long* fx;         // [P*C] entry weights, fixed point (SNN_FIXED_FRAC_BITS)
     int32_t* cnt;          // [ntiles][nrb] row-block counts, then offsets within the tile
     int32_t* tile_base;    // [ntiles + 1] first entry of each tile
     uint16_t* mask;        // [ceil(max_B / 16)][P] per-row instance masks
@@ -230,7 +240,7 @@ extern "C" {
 snn_status snn_destroy_prop_plan(snn_prop_plan* p) {
     if (!p) return SNN_OK;
     cudaFree(p->keys);
-    cudaFree(p->wts);
+    cudaFree(p->fx);
     cudaFree(p->cnt);
     cudaFree(p->tile_base);
     cudaFree(p->mask);
@@ -260,11 +270,10 @@ snn_status snn_create_prop_plan(snn_ragged* r, int32_t max_B, snn_prop_plan** ou
     p->ntiles = (int)ceil_div(d.Q, W);
     p->nrb = (int)ceil_div(d.P, PLAN_RB);
     const size_t n = (size_t)d.P * d.C;
-    const size_t wsz = d.dtype == SNN_F32 ? sizeof(float) : sizeof(double);
     const int groups = (int)ceil_div(max_B, PLAN_IG);
     cudaError_t e = cudaSuccess;
     e = e != cudaSuccess ? e : cudaMalloc(&p->keys, n * sizeof(uint32_t));
-    e = e != cudaSuccess ? e : cudaMalloc(&p->wts, n * wsz);
+    e = e != cudaSuccess ? e : cudaMalloc(&p->fx, n * sizeof(long long));
     e = e != cudaSuccess ? e : cudaMalloc(&p->cnt, (size_t)p->ntiles * p->nrb * sizeof(int32_t));
     e = e != cudaSuccess ? e : cudaMalloc(&p->tile_base, (size_t)(p->ntiles + 1) * sizeof(int32_t));
     e = e != cudaSuccess ? e : cudaMalloc(&p->mask, (size_t)groups * d.P * sizeof(uint16_t));
@@ -284,8 +293,7 @@ snn_status snn_create_prop_plan(snn_ragged* r, int32_t max_B, snn_prop_plan** ou
     }
     const int accb = 8 * p->IG * W;
     if (accb > 48 * 1024) {
-        SNN_CUDA(cudaFuncSetAttribute(k_propagate_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, accb));
-        SNN_CUDA(cudaFuncSetAttribute(k_propagate_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, accb));
+        SNN_CUDA(cudaFuncSetAttribute(k_propagate_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, accb));
     }
     *out = p;
     return SNN_OK;
@@ -307,11 +315,11 @@ snn_status snn_prop_plan_pack(snn_prop_plan* p, snn_stream stream) {
     if (d.dtype == SNN_F32)
         k_plan_scatter<float><<<p->nrb, 256, hist, s>>>(d.row_len, d.ind, (const float*)d.w, d.P, d.Q, d.C, p->W,
                                                         p->ntiles, p->nrb, p->cnt, p->tile_base, p->keys,
-                                                        (float*)p->wts);
+                                                        p->fx);
     else
         k_plan_scatter<double><<<p->nrb, 256, hist, s>>>(d.row_len, d.ind, (const double*)d.w, d.P, d.Q, d.C, p->W,
                                                          p->ntiles, p->nrb, p->cnt, p->tile_base, p->keys,
-                                                         (double*)p->wts);
+                                                         p->fx);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -325,18 +333,12 @@ snn_status snn_propagate_tiled(const snn_prop_plan* p, const uint32_t* pre_bits,
     cudaStream_t s = (cudaStream_t)stream;
     const int Pw = (d.P + 31) / 32;
     const int groups = (int)ceil_div(B, PLAN_IG);
-    k_plan_rowmask<<<(int)ceil_div((long long)groups * Pw, 256), 256, 0, s>>>(pre_bits, B, d.P, Pw, p->mask);
+    k_plan_rowmask<<<(int)ceil_div((long long)groups * d.P, 256), 256, 0, s>>>(pre_bits, B, d.P, Pw, p->mask);
     SNN_LAUNCH_CHECK();
     const dim3 grid(p->ntiles, groups);
     const size_t accb = (size_t)8 * p->IG * p->W;
-    if (d.dtype == SNN_F32)
-        k_propagate_tiled<float><<<grid, PLAN_THREADS, accb, s>>>(p->keys, (const float*)p->wts, p->tile_base,
-                                                                   p->mask, d.P, d.Q, p->W, p->IG, B,
-                                                                   (long long*)post_acc);
-    else
-        k_propagate_tiled<double><<<grid, PLAN_THREADS, accb, s>>>(p->keys, (const double*)p->wts, p->tile_base,
-                                                                    p->mask, d.P, d.Q, p->W, p->IG, B,
-                                                                    (long long*)post_acc);
+    k_propagate_tiled<<<grid, PLAN_THREADS, accb, s>>>(p->keys, p->fx, p->tile_base, p->mask, d.P, d.Q, p->W,
+                                                       p->IG, B, (long long*)post_acc);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
