@@ -334,7 +334,8 @@ snn_status snn_adam_bias(double beta1, double beta2, int64_t step, double* out);
  * row capacities <= 2048) and allocates fixed scratch: the e-prop gradient partial sums
  * (sized from max_B, max_T and the two ragged handles), the packed forward rows and the
  * gather order of each row.  The forward sums each neuron's synaptic input of a step
- * exactly in fixed point while its magnitude stays below 2^11 (2048 in weight units). */
+ * exactly in integers (see snn_step_neurons for the grids) while its incoming |weight|
+ * sum stays below 2^11 (2048 in weight units). */
 snn_status snn_create_classifier(const snn_classifier_desc* desc, snn_classifier** out);
 /* Row schedule of snn_step_neurons: how many warps (4, 8 or 16) share one trial's
  * spiking rows and neurons (default 8).  Results do not depend on it (integer
@@ -369,11 +370,14 @@ snn_status snn_destroy_classifier(snn_classifier* c);
  *   y^t    : alpha y + W_out z^{t-1} + b ;  d^t = softmax(y^t) - onehot(label)
  * and records x, z, psi, d (and v, a, y when those pointers are set).  A label outside
  * [0, n_classes) or a bin_len < 1 sets SNN_ESTATE in w_in's status word and the trial
- * runs with the value clamped into range.  The synaptic sums are exact in fixed point
- * (40 fractional bits) while they stay below 2^11 in magnitude: a neuron or readout
- * whose incoming |weight| sum (input, recurrent and readout weights, the bound on any
- * step's sum) reaches 2^11 also sets SNN_ESTATE, since its sums could wrap.  Weights
- * below 2^-17 in magnitude are rounded to the fixed-point grid (2^-40). */
+ * runs with the value clamped into range.  The synaptic sums are exact integer sums,
+ * so their order does not matter: FP64 on the fixed-point grid 2^-40 (weights below
+ * 2^-17 in magnitude are rounded to it); FP32 in 32 bits on a grid per neuron or readout,
+ * 2^(sh - 40) with sh = max(0, bits(S 2^40) - 30) for its incoming |weight| sum S
+ * (input, recurrent and readout weights, the bound on any step's sum), each weight
+ * rounded (half up) to its target's grid: an error of at most S 2^-30 per weight (1.3e-8
+ * at S = 14).  A neuron or readout whose S reaches 2^11 sets SNN_ESTATE (beyond it the
+ * FP64 sums could wrap). */
 snn_status snn_step_neurons(snn_classifier* c, const snn_batch* b, int32_t t0, int32_t n_steps,
                             snn_stream stream);
 
@@ -469,12 +473,13 @@ snn_status snn_multi_destroy(snn_multi* m);
  * flag every instance runs (graph capture allowed: the run's queue stamp lives on the
  * device).  Runs of one plan must not overlap on the GPU. */
 snn_status snn_multi_run(snn_multi* m, int32_t flags, int64_t wait_limit_ns, snn_stream stream);
-/* Phase timing of later runs (tracing): times = device int64 [n][11] (NULL: off).  Each
+/* Phase timing of later runs (tracing): times = device int64 [n][12] (NULL: off).  Each
  * run writes, per instance in the order given to snn_multi_create, the global timer (ns)
- * when its iteration was seeded ([i][0]) and when each of its 10 phases completed
- * ([i][1 + phase]: bookkeeping, inputs and packing, forward (with the gather order
- * beside it), readout scan, adjoint scan, gather, Adam, DEEP R elimination,
- * redistribution, formation).  The caller keeps the buffer alive while it is set. */
+ * when its iteration was seeded ([i][0]) and when each of its 11 phases completed
+ * ([i][1 + phase]: bookkeeping, inputs and accumulator weight sums, packing, forward
+ * (with the gather order beside it), readout scan, adjoint scan, gather, Adam, DEEP R
+ * elimination, redistribution, formation).  The caller keeps the buffer alive while it
+ * is set. */
 snn_status snn_multi_set_trace(snn_multi* m, int64_t* times);
 /* Host producer for a SNN_MULTI_HOST_POSTS run: the instances (indices into the array
  * given to snn_multi_create, no repeats) that the running iteration should train.

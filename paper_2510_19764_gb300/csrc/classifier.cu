@@ -157,8 +157,10 @@ __global__ void k_adam_bias(const long long* __restrict__ step_dev, double beta1
 
 
 // ------------------------------------------------------------------ host side
-static size_t fwd_smem(int n_in, int N, int Win, int Wh) {
-    return (size_t)(N + 64) * 8 + (size_t)(n_in + N + 1) * 4 + (size_t)(n_in + N) * 4 * 2 + 8 +
+// Shared memory of the forward: accumulators (one word each for FP32, a pair for FP64),
+// row lengths, two spike lists, their counts, the spike words.
+static size_t fwd_smem(int n_in, int N, int Win, int Wh, bool narrow) {
+    return (size_t)(N + 64) * (narrow ? 4 : 8) + (size_t)(n_in + N + 1) * 4 + (size_t)(n_in + N) * 4 * 2 + 8 +
            (size_t)(Win + 2 * Wh) * 4;
 }
 
@@ -194,10 +196,18 @@ static snn_status refresh_fixed(snn_classifier* c, cudaStream_t s) {
     const snn_classifier_desc& d = c->d;
     const long long n = (long long)(d.n_in + d.N) * c->Cf;
     SNN_CUDA(cudaMemsetAsync(c->colsum, 0, (size_t)(d.N + 64) * sizeof(unsigned long long), s));
-    k_pack<real><<<ceil_div(n, 256), 256, 0, s>>>(
-        (const real*)d.w_in->d.w, d.w_in->d.ind, d.w_in->d.row_len, d.w_in->d.C, d.n_in, (const real*)d.w_rec->d.w,
-        d.w_rec->d.ind, d.w_rec->d.row_len, d.w_rec->d.C, (const real*)d.W_out, d.K, d.N, c->Cf,
-        (unsigned long long*)c->pk, n, c->colsum);
+#define SNN_PACK_SRC                                                                                               \
+    (const real*)d.w_in->d.w, d.w_in->d.ind, d.w_in->d.row_len, d.w_in->d.C, d.n_in, (const real*)d.w_rec->d.w, \
+        d.w_rec->d.ind, d.w_rec->d.row_len, d.w_rec->d.C, (const real*)d.W_out, d.K, d.N, c->Cf
+    if (sizeof(real) == 4) {
+        // narrow slots: every accumulator's |weight| sum first, then the slots on its grid
+        k_colsum<real><<<ceil_div(n, 256), 256, 0, s>>>(SNN_PACK_SRC, n, c->colsum);
+        SNN_LAUNCH_CHECK();
+        k_pack_narrow<real><<<ceil_div(n, 256), 256, 0, s>>>(SNN_PACK_SRC, (unsigned long long*)c->pk, n, c->colsum);
+    } else {
+        k_pack<real><<<ceil_div(n, 256), 256, 0, s>>>(SNN_PACK_SRC, (unsigned long long*)c->pk, n, c->colsum);
+    }
+#undef SNN_PACK_SRC
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -276,7 +286,7 @@ static snn_status step_impl(snn_classifier* c, const snn_batch* bt, int t0, int 
     p.colsum = c->colsum;
     p.status = d.w_in->status;
     p.sched = c->row_sched;
-    const size_t smem = fwd_smem(d.n_in, d.N, Win, Wh);
+    const size_t smem = fwd_smem(d.n_in, d.N, Win, Wh, sizeof(real) == 4);
     snn_status st = packed_ready ? SNN_OK : refresh_fixed<real>(c, s);
     if (st != SNN_OK) return st;
     SNN_REQUIRE(smem <= 227 * 1024, "snn_step_neurons: n_in = %d, N = %d need %zu bytes of shared memory (max 227 KB)",

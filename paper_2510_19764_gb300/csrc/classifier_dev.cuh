@@ -59,32 +59,58 @@ struct InputParams {
 __device__ __forceinline__ float exp_real(float x) { return expf(x); }
 __device__ __forceinline__ double exp_real(double x) { return exp(x); }
 
-// Forward accumulators: each is a pair of 32-bit words {H, L} summing the two parts of
-// every added fixed-point weight w = 2^20 w_hi + w_lo (w_hi = bits 51..20 of the packed
-// slot as a signed 32-bit value, w_lo = bits 19..0): both sums use native 32-bit
-// shared-memory atomics and are exact: L takes at most one addend (< 2^20) per spiking
-// row, rows hold no repeated target and n_in + N <= 3072 < 4096; H wraps modulo 2^32
-// like the 52-bit weights.  The total is 2^20 H + L.  The H words of all accumulators
-// come first, then the L words (NA apart), so that lanes adding to consecutive targets
-// hit consecutive banks: interleaved pairs would put every H word on an even bank and
-// double the shared-memory wavefronts of a warp's scattered additions.
+// Forward accumulators, FP64 build (wide slots): each is a pair of 32-bit words {H, L}
+// summing the two parts of every added fixed-point weight w = 2^20 w_hi + w_lo (w_hi =
+// bits 51..20 of the packed slot as a signed 32-bit value, w_lo = bits 19..0): both sums
+// use native 32-bit shared-memory atomics and are exact: L takes at most one addend
+// (< 2^20) per spiking row, rows hold no repeated target and n_in + N <= 3072 < 4096; H
+// wraps modulo 2^32 like the 52-bit weights.  The total is 2^20 H + L.  The H words of
+// all accumulators come first, then the L words (NA apart), so that lanes adding to
+// consecutive targets hit consecutive banks: interleaved pairs would put every H word on
+// an even bank and double the shared-memory wavefronts of a warp's scattered additions.
+//
+// FP32 build (narrow slots): one 32-bit word per accumulator and one atomic per slot.
+// Accumulator t has its own grid 2^(sh_t - 40), sh_t = max(0, e_t - 30) with e_t the bit
+// length of its |weight| sum in fixed point (40 fractional bits); each slot holds its
+// weight rounded to its target's grid, so |any step's sum| <= 2^30 + 3072 / 2 < 2^31 and
+// the 32-bit integer sums are exact on that grid.  A weight is off by at most half a grid
+// step, C_t 2^-30 for an incoming |weight| sum C_t (1.3e-8 at C_t = 14): below the FP32
+// rounding of the membrane update's operands at these magnitudes.  The slot carries the
+// target's byte offset, so an addition is one integer add and one atomic.
+template <bool NARROW>
 __device__ __forceinline__ void acc_add(unsigned* acc, unsigned long long w, int NA) {
     const unsigned lo = (unsigned)w, hi = (unsigned)(w >> 32);
-    unsigned* a = acc + (hi >> 20);                       // target index: bits 63..52
-    atomicAdd(a, __funnelshift_r(lo, hi, 20));            // bits 51..20
-    atomicAdd(a + NA, lo & 0xFFFFFu);                     // bits 19..0
+    if (NARROW) {
+        atomicAdd((unsigned*)((char*)acc + hi), lo);          // bits 63..32: byte offset
+    } else {
+        unsigned* a = acc + (hi >> 20);                       // target index: bits 63..52
+        atomicAdd(a, __funnelshift_r(lo, hi, 20));            // bits 51..20
+        atomicAdd(a + NA, lo & 0xFFFFFu);                     // bits 19..0
+    }
 }
-// The accumulated sum 2^20 H + L of accumulator a (L at a + NA) in real units (40
-// fractional bits): H 2^-20 + L 2^-40, each product exact, one rounding in the sum (for
-// double the same value as converting the 64-bit integer first).
-template <typename real>
-__device__ __forceinline__ real acc_real(const unsigned* a, int NA) {
+// The accumulated sum of accumulator a in real units.  Wide: 2^20 H + L (L at a + NA),
+// H 2^-20 + L 2^-40, each product exact, one rounding in the sum (for double the same
+// value as converting the 64-bit integer first).  Narrow: the 32-bit sum times its grid
+// step `scale` (a power of two: one rounding).
+template <bool NARROW, typename real>
+__device__ __forceinline__ real acc_real(const unsigned* a, int NA, real scale) {
+    if (NARROW) return (real)(int)a[0] * scale;
     return (real)(int)a[0] * (real)9.5367431640625e-07 + (real)a[NA] * (real)9.094947017729282e-13;
 }
 // Clears accumulator a.
+template <bool NARROW>
 __device__ __forceinline__ void acc_zero(unsigned* a, int NA) {
     a[0] = 0u;
-    a[NA] = 0u;
+    if (!NARROW) a[NA] = 0u;
+}
+// Narrow grid of an accumulator from its |weight| sum cs (fixed point): the shift sh and
+// the grid step 2^(sh - 40) as a float (exact).
+__device__ __forceinline__ int narrow_shift(unsigned long long cs) {
+    const int e = 64 - __clzll((long long)cs);
+    return e > 30 ? e - 30 : 0;
+}
+__device__ __forceinline__ float narrow_scale(unsigned long long cs) {
+    return __int_as_float((127 - 40 + narrow_shift(cs)) << 23);
 }
 
 // Input spikes of every (trial, step) in parallel: they depend on (trial, step, channel)
@@ -151,7 +177,7 @@ constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time (defau
 // 1, 4: SNN_ROWS_PER_WARP; 2, 8: SNN_ROWS_WIDE for long rows; 4, 4: SNN_ROWS_QUAD).  The
 // wide forms hold 16 loads per lane in flight (fewer round trips per step, more
 // registers: they suit the persistent kernel, whose CTAs have room for them).
-template <int FR, int nwarps, int CH = 4>
+template <bool NARROW, int FR, int nwarps, int CH = 4>
 __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, int NA, const int* lprv, int n_rows,
                                                     const int* lens, const unsigned long long* pk, int Cf, int R,
                                                     int warp, int lane) {
@@ -177,14 +203,14 @@ __device__ __forceinline__ void propagate_rows_warp(unsigned* acc, int NA, const
             for (int q = 0; q < CH; ++q)
 #pragma unroll
                 for (int u = 0; u < FR; ++u)
-                    if (s0 + q * 32 < nr[u]) acc_add(acc, wv[u][q], NA);
+                    if (s0 + q * 32 < nr[u]) acc_add<NARROW>(acc, wv[u][q], NA);
         }
     }
 }
 
 // Row per block: every warp works on every spiking row, warp w taking the row's 32-slot
 // chunks w, w + nwarps, ...; two rows in flight (suits few long rows).
-template <int nwarps>
+template <bool NARROW, int nwarps>
 __device__ __forceinline__ void propagate_rows_block(unsigned* acc, int NA, const int* lprv, int n_rows,
                                                      const int* lens,
                                                      const unsigned long long* pk, int Cf, int warp, int lane) {
@@ -198,8 +224,8 @@ __device__ __forceinline__ void propagate_rows_block(unsigned* acc, int NA, cons
         for (int s0 = warp * 32; s0 < nmax; s0 += nwarps * 32) {
             const unsigned long long a = s0 < n0 ? p0[s0 + lane] : 0ull;
             const unsigned long long b = s0 < n1 ? p1[s0 + lane] : 0ull;
-            if (s0 < n0) acc_add(acc, a, NA);
-            if (s0 < n1) acc_add(acc, b, NA);
+            if (s0 < n0) acc_add<NARROW>(acc, a, NA);
+            if (s0 < n1) acc_add<NARROW>(acc, b, NA);
         }
     }
 }
@@ -211,8 +237,9 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
     const int N = p.N, K = p.K, Win = p.Win, Wh = p.Wh, n_in = p.n_in;
     const int R = n_in + N;
     const int NA = N + 64;                        // accumulators: neurons, 32 per-lane spares, readouts
-    unsigned* acc = (unsigned*)smem;              // [2][NA]: H words, then L words
-    int* lens = (int*)(acc + 2 * NA);             // [R + 1] packed row lengths (row R: empty)
+    constexpr bool NARROW = sizeof(real) == 4;    // FP32: narrow slots, one word per accumulator
+    unsigned* acc = (unsigned*)smem;              // narrow [NA]; wide [2][NA]: H words, then L words
+    int* lens = (int*)(acc + (NARROW ? NA : 2 * NA));   // [R + 1] packed row lengths (row R: empty)
     int* list = lens + R + 1;                     // [2][R] spiking rows by step parity
     int* lcnt = list + 2 * R;                     // [2]
     uint32_t* xw = (uint32_t*)(lcnt + 2);         // [Win] input spike words of the current step
@@ -224,7 +251,7 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
     constexpr int RO_WARP = 1;                    // advances the readout in phase B
     const int t0 = p.t0;
     const int t_end = p.trial_T ? min(p.t0 + p.n_steps, max(p.trial_T[b], p.t0)) : p.t0 + p.n_steps;
-    real vr[NPT], ar[NPT];
+    real vr[NPT], ar[NPT], sc[NPT];               // sc: narrow grid step of each neuron's accumulator
     {
         const int prv = (t0 - 1) & 1;
 #pragma unroll
@@ -232,8 +259,9 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             const int j = tid + q * TH;
             vr[q] = j < N ? p.v[(size_t)b * N + j] : real(0);
             ar[q] = j < N ? p.a[(size_t)b * N + j] : real(0);
+            sc[q] = (NARROW && j < N) ? (real)narrow_scale(p.colsum[j]) : real(0);
         }
-        for (int j = tid; j < 2 * NA; j += TH) acc[j] = 0u;
+        for (int j = tid; j < (NARROW ? NA : 2 * NA); j += TH) acc[j] = 0u;
         for (int j = tid; j < N; j += TH) lens[n_in + j] = p.rec_len[j] + K;
         for (int i = tid; i < n_in; i += TH) lens[i] = p.in_len[i];
         if (tid == 0) lens[R] = 0;
@@ -250,11 +278,12 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             }
         }
     }
-    real yk = 0, ysk = 0, bk = 0;
+    real yk = 0, ysk = 0, bk = 0, sck = 0;
     if (warp == RO_WARP && lane < K) {
         yk = p.y[(size_t)b * K + lane];
         ysk = p.ysum[(size_t)b * K + lane];
         bk = p.b_out[lane];
+        if (NARROW) sck = (real)narrow_scale(p.colsum[N + 32 + lane]);
     }
     if (b == 0) {
         // a neuron or readout whose |weight| sum reaches 2^11 could wrap its fixed-point sum
@@ -284,17 +313,23 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
         }
         if (tid == 32) lcnt[cur] = 0;
         switch (p.sched) {
-            case SNN_ROWS_PER_BLOCK: propagate_rows_block<nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, warp, lane); break;
-            case SNN_ROWS_PER_WARP: propagate_rows_warp<1, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+            case SNN_ROWS_PER_BLOCK:
+                propagate_rows_block<NARROW, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, warp, lane);
+                break;
+            case SNN_ROWS_PER_WARP:
+                propagate_rows_warp<NARROW, 1, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                break;
             case SNN_ROWS_WIDE:
-                if (WIDE) propagate_rows_warp<2, nwarps, 8>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
-                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                if (WIDE) propagate_rows_warp<NARROW, 2, nwarps, 8>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
                 break;
             case SNN_ROWS_QUAD:
-                if (WIDE) propagate_rows_warp<4, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
-                else propagate_rows_warp<FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                if (WIDE) propagate_rows_warp<NARROW, 4, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
                 break;
-            default: propagate_rows_warp<FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane); break;
+            default:
+                propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                break;
         }
         __syncthreads();
         // ---------------- phase B: neurons; spike lists of step t
@@ -310,8 +345,8 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             for (int k = 0; word; ++k, word &= word - 1u) lcur[base + k] = lane * 32 + __ffs(word) - 1;
         }
         if (warp == RO_WARP && lane < K) {         // y^t from the readout sums W_out z^{t-1}
-            yk = p.alpha * yk + acc_real<real>(acc + N + 32 + lane, NA) + bk;
-            acc_zero(acc + N + 32 + lane, NA);
+            yk = p.alpha * yk + acc_real<NARROW, real>(acc + N + 32 + lane, NA, sck) + bk;
+            acc_zero<NARROW>(acc + N + 32 + lane, NA);
             ysk += yk;
             if (d_b) d_b[(size_t)t * K + lane] = yk;
             if (p.y_rec) p.y_rec[((size_t)b * p.T + t) * K + lane] = yk;
@@ -322,8 +357,8 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
             const int j = tid + q * TH;
             bool spk = false;
             if (j < N) {
-                const real I = acc_real<real>(acc + j, NA);
-                acc_zero(acc + j, NA);
+                const real I = acc_real<NARROW, real>(acc + j, NA, sc[q]);
+                acc_zero<NARROW>(acc + j, NA);
                 const bool zp = (zprv[j >> 5] >> (j & 31)) & 1u;
                 const real v = p.alpha * (zp ? vr[q] - p.v_thr : vr[q]) + I;
                 const real aa = p.rho * ar[q] + (zp ? real(1) : real(0));
@@ -426,22 +461,26 @@ __global__ void __launch_bounds__(SMX_WARPS * 32)
 }
 
 // Packed forward rows: row r < n_in is input row r, row n_in + j is hidden row j; Cf
-// slots each.  A slot is bits 63..52 target accumulator, bits 51..0 the weight in fixed
-// point (40 fractional bits, two's complement): one 64-bit load per slot, added with
-// acc_add.  Hidden row j holds its len_j synapses, then its readout column W_out[k][j]
-// aimed at accumulators N + 32 + k.  Slots past a row's length hold weight 0 aimed at
-// the per-lane spare N + (slot mod 32), so a warp adds a row's last 32-slot chunk whole,
-// with no per-lane test and no two lanes on one address.
+// slots each, one 64-bit load per slot.  Hidden row j holds its len_j synapses, then its
+// readout column W_out[k][j] aimed at accumulators N + 32 + k.  Slots past a row's
+// length hold weight 0 aimed at the per-lane spare N + (slot mod 32), so a warp adds a
+// row's last 32-slot chunk whole, with no per-lane test and no two lanes on one address.
+// Wide slots (FP64): bits 63..52 target accumulator, bits 51..0 the weight in fixed point
+// (40 fractional bits, two's complement).  Narrow slots (FP32): bits 63..32 the target
+// accumulator's byte offset, bits 31..0 the weight on the target's grid (see acc_add);
+// they need every accumulator's |weight| sum first (colsum_slot over all slots), then
+// pack_slot_narrow.
+
+// Target accumulator and fixed-point weight of packed slot i (weight 0: padding).
 template <typename real>
-__device__ __forceinline__ void pack_slot(const real* __restrict__ w_in, const int32_t* __restrict__ ind_in,
-                                          const int32_t* __restrict__ len_in, int C_in, int n_in,
-                                          const real* __restrict__ w_rec, const int32_t* __restrict__ ind_rec,
-                                          const int32_t* __restrict__ len_rec, int C_rec, const real* __restrict__ W_out,
-                                          int K, int N, int Cf, unsigned long long* __restrict__ pk,
-                                          unsigned long long* __restrict__ colsum, const long long i) {
+__device__ __forceinline__ void pack_src(const real* __restrict__ w_in, const int32_t* __restrict__ ind_in,
+                                         const int32_t* __restrict__ len_in, int C_in, int n_in,
+                                         const real* __restrict__ w_rec, const int32_t* __restrict__ ind_rec,
+                                         const int32_t* __restrict__ len_rec, int C_rec, const real* __restrict__ W_out,
+                                         int K, int N, int Cf, const long long i, unsigned& tgt, long long& f) {
     const int r = (int)(i / Cf), s = (int)(i % Cf);
-    unsigned tgt = (unsigned)(N + (s & 31));
-    long long f = 0;
+    tgt = (unsigned)(N + (s & 31));
+    f = 0;
     if (r < n_in) {
         if (s < len_in[r]) {
             const size_t e = (size_t)r * C_in + s;
@@ -459,19 +498,64 @@ __device__ __forceinline__ void pack_slot(const real* __restrict__ w_in, const i
             f = to_fixed(W_out[(size_t)(s - L) * N + j]);
         }
     }
+}
+
+#define SNN_PACK_ARGS                                                                                          \
+    const real *__restrict__ w_in, const int32_t *__restrict__ ind_in, const int32_t *__restrict__ len_in,    \
+        int C_in, int n_in, const real *__restrict__ w_rec, const int32_t *__restrict__ ind_rec,              \
+        const int32_t *__restrict__ len_rec, int C_rec, const real *__restrict__ W_out, int K, int N, int Cf
+#define SNN_PACK_PASS w_in, ind_in, len_in, C_in, n_in, w_rec, ind_rec, len_rec, C_rec, W_out, K, N, Cf
+
+// Wide slot i, and its |weight| into its accumulator's sum.
+template <typename real>
+__device__ __forceinline__ void pack_slot(SNN_PACK_ARGS, unsigned long long* __restrict__ pk,
+                                          unsigned long long* __restrict__ colsum, const long long i) {
+    unsigned tgt;
+    long long f;
+    pack_src<real>(SNN_PACK_PASS, i, tgt, f);
     pk[i] = ((unsigned long long)tgt << 52) | ((unsigned long long)f & ((1ull << 52) - 1));
     if (f) atomicAdd(&colsum[tgt], (unsigned long long)(f < 0 ? -f : f));
 }
+// The |weight| of slot i into its accumulator's sum (first pass of the narrow packing).
+template <typename real>
+__device__ __forceinline__ void colsum_slot(SNN_PACK_ARGS, unsigned long long* __restrict__ colsum,
+                                            const long long i) {
+    unsigned tgt;
+    long long f;
+    pack_src<real>(SNN_PACK_PASS, i, tgt, f);
+    if (f) atomicAdd(&colsum[tgt], (unsigned long long)(f < 0 ? -f : f));
+}
+// Narrow slot i from the complete sums: the weight rounded (half up) to the target's grid.
+template <typename real>
+__device__ __forceinline__ void pack_slot_narrow(SNN_PACK_ARGS, unsigned long long* __restrict__ pk,
+                                                 const unsigned long long* __restrict__ colsum, const long long i) {
+    unsigned tgt;
+    long long f;
+    pack_src<real>(SNN_PACK_PASS, i, tgt, f);
+    const int sh = narrow_shift(colsum[tgt]);
+    const long long v = sh ? (f + (1ll << (sh - 1))) >> sh : f;
+    pk[i] = ((unsigned long long)(tgt * 4u) << 32) | (unsigned)(int)v;
+}
 
 template <typename real>
-__global__ void k_pack(const real* __restrict__ w_in, const int32_t* __restrict__ ind_in,
-                       const int32_t* __restrict__ len_in, int C_in, int n_in, const real* __restrict__ w_rec,
-                       const int32_t* __restrict__ ind_rec, const int32_t* __restrict__ len_rec, int C_rec,
-                       const real* __restrict__ W_out, int K, int N, int Cf, unsigned long long* __restrict__ pk,
-                       long long n, unsigned long long* __restrict__ colsum) {
+__global__ void k_pack(SNN_PACK_ARGS, unsigned long long* __restrict__ pk, long long n,
+                       unsigned long long* __restrict__ colsum) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    pack_slot<real>(w_in, ind_in, len_in, C_in, n_in, w_rec, ind_rec, len_rec, C_rec, W_out, K, N, Cf, pk, colsum, i);
+    pack_slot<real>(SNN_PACK_PASS, pk, colsum, i);
+}
+template <typename real>
+__global__ void k_colsum(SNN_PACK_ARGS, long long n, unsigned long long* __restrict__ colsum) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    colsum_slot<real>(SNN_PACK_PASS, colsum, i);
+}
+template <typename real>
+__global__ void k_pack_narrow(SNN_PACK_ARGS, unsigned long long* __restrict__ pk, long long n,
+                              const unsigned long long* __restrict__ colsum) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pack_slot_narrow<real>(SNN_PACK_PASS, pk, colsum, i);
 }
 
 // Filtered readout error D_k^t = d_k^{t+1} + alpha D_k^{t+1} (D^{T-1} = 0), i.e.

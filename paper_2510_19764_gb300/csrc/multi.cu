@@ -6,7 +6,8 @@
 // (bookkeeping, snn_step_neurons over the whole trial, snn_eprop_update GRAD and APPLY,
 // snn_rewire_deepr on both projections), split into phases whose work is cut into items:
 //   PREP    1 item       trial id / label / time warp of the iteration, state reset
-//   PRE     n items      input spikes of the trial, packed forward rows
+//   PRE     n items      input spikes of the trial, |weight| sums of the accumulators
+//   PACK    n items      packed forward rows (narrow slots, on each accumulator's grid)
 //   FWD     1 + n items  the whole trial (forward_trial), and beside it the gather order
 //                        of every row (needed only by GATHER)
 //   SCAN    1 item       softmax of the readout, filtered readout error, bias gradient,
@@ -42,8 +43,8 @@
 namespace snn {
 
 enum : int {
-    MP_PREP = 0, MP_PRE = 1, MP_FWD = 2, MP_SCAN = 3, MP_BWD = 4, MP_GATHER = 5, MP_ADAM = 6,
-    MP_ELIM = 7, MP_DIST = 8, MP_FORM = 9, MP_N = 10,
+    MP_PREP = 0, MP_PRE = 1, MP_PACK = 2, MP_FWD = 3, MP_SCAN = 4, MP_BWD = 5, MP_GATHER = 6, MP_ADAM = 7,
+    MP_ELIM = 8, MP_DIST = 9, MP_FORM = 10, MP_N = 11,
 };
 
 constexpr int MT = 256;                          // threads per CTA
@@ -98,7 +99,7 @@ struct MInst {
     double lr, beta1, beta2, eps, l1, temperature;
     MRag rg[2];
     int n_items[MP_N];
-    int n_input, n_pack, n_sort0;                // MP_PRE: input, pack; MP_FWD: sort items of input rows first
+    int n_input, n_pack, n_sort0;                // MP_PRE: input, sums; MP_PACK; MP_FWD: sort items of input rows first
     int n_rows0;                                 // MP_ELIM / MP_FORM: items of the input projection
     int orig;                                    // the instance's index in the caller's array
 };
@@ -223,10 +224,23 @@ __device__ void m_pre(const MInst& I, int k, unsigned char* smem) {
         for (int r = 0; r < M_PACK_PER_ITEM / MT; ++r) {
             const long long s = (long long)k * M_PACK_PER_ITEM + (long long)r * MT + tid;
             if (s < n)
-                pack_slot<float>(ri.w, ri.ind, ri.len, ri.C, I.n_in, rr.w, rr.ind, rr.len, rr.C, I.W_out, I.K, I.N,
-                                 I.Cf, I.pk, I.colsum, s);
+                colsum_slot<float>(ri.w, ri.ind, ri.len, ri.C, I.n_in, rr.w, rr.ind, rr.len, rr.C, I.W_out, I.K, I.N,
+                                   I.Cf, I.colsum, s);
         }
         return;
+    }
+}
+
+// Packed forward rows, slots [k M_PACK_PER_ITEM, (k + 1) M_PACK_PER_ITEM), from the
+// complete |weight| sums of the PRE phase.
+__device__ void m_pack(const MInst& I, int k) {
+    const long long n = (long long)(I.n_in + I.N) * I.Cf;
+    const MRag &ri = I.rg[0], &rr = I.rg[1];
+    for (int r = 0; r < M_PACK_PER_ITEM / MT; ++r) {
+        const long long s = (long long)k * M_PACK_PER_ITEM + (long long)r * MT + threadIdx.x;
+        if (s < n)
+            pack_slot_narrow<float>(ri.w, ri.ind, ri.len, ri.C, I.n_in, rr.w, rr.ind, rr.len, rr.C, I.W_out, I.K,
+                                    I.N, I.Cf, I.pk, I.colsum, s);
     }
 }
 
@@ -517,6 +531,7 @@ __global__ void __launch_bounds__(MT, 1) k_multi(MArgs A) {
         switch (phase) {
             case MP_PREP: m_prep(I); break;
             case MP_PRE: m_pre(I, k, smem); break;
+            case MP_PACK: m_pack(I, k); break;
             case MP_FWD:
                 if (k == 0) m_fwd(I, smem);
                 else m_sort(I, k - 1, smem);
@@ -697,6 +712,7 @@ static snn_status multi_fill(const snn_multi_instance& s, MInst& I, size_t& smem
     I.n_rows0 = rows0;
     I.n_items[MP_PREP] = 1;
     I.n_items[MP_PRE] = I.n_input + I.n_pack;
+    I.n_items[MP_PACK] = I.n_pack;
     I.n_items[MP_FWD] = 1 + rows0 + rows1;
     I.n_items[MP_SCAN] = 1;
     I.n_items[MP_BWD] = ceil_div(d.N, M_BWD_PER_ITEM);
@@ -708,8 +724,8 @@ static snn_status multi_fill(const snn_multi_instance& s, MInst& I, size_t& smem
     I.n_items[MP_DIST] = 2;
     I.n_items[MP_FORM] = rows0 + rows1;
     // shared memory of the largest phase
-    const size_t fwd = (size_t)(d.N + 64) * 8 + (size_t)(d.n_in + d.N + 1) * 4 + (size_t)(d.n_in + d.N) * 4 * 2 + 8 +
-                       (size_t)(I.Win + 2 * I.Wh) * 4;
+    const size_t fwd = (size_t)(d.N + 64) * 4 + (size_t)(d.n_in + d.N + 1) * 4 + (size_t)(d.n_in + d.N) * 4 * 2 + 8 +
+                       (size_t)(I.Win + 2 * I.Wh) * 4;   // narrow accumulators: one word each
     const size_t sort = (size_t)MW * I.Cmax * 4;
     const size_t gat = (size_t)((b.T + 31) / 32 * 32) * 4;
     const size_t scan = (size_t)MW * 32 * d.K * 4;

@@ -191,8 +191,8 @@ class MultiRunner:
         self.graph = None
         self.graph_iters = 0
 
-    PHASES = ("prep", "inputs+pack", "forward+sort", "readout_scan", "adjoint", "gather", "adam", "deepr_elim",
-              "deepr_dist", "deepr_form")
+    PHASES = ("prep", "inputs+sums", "pack", "forward+sort", "readout_scan", "adjoint", "gather", "adam",
+              "deepr_elim", "deepr_dist", "deepr_form")
 
     def iterate(self, stream=None, flags: int = 0):
         abi.snn_multi_run(self.handle, flags, self.wait_limit_ns, stream or torch.cuda.current_stream())
@@ -233,7 +233,7 @@ class MultiRunner:
 
 class PhaseTrace:
     """Global-timer stamps of one persistent run: per instance its start and the end of
-    each phase (device int64 [n][11])."""
+    each phase (device int64 [n][12])."""
 
     def __init__(self, n: int):
         self.times = torch.zeros((n, len(MultiRunner.PHASES) + 1), dtype=torch.int64, device="cuda")
