@@ -342,7 +342,7 @@ snn_status snn_create_classifier(const snn_classifier_desc* desc, snn_classifier
  * accumulation); an autotuner picks it per (N, row length, spike rate). */
 snn_status snn_classifier_set_schedule(snn_classifier* c, int32_t warps_per_trial);
 /* How the warps of a trial share the spiking rows of a step (results do not depend on
- * it): SNN_ROWS_PAIRS (default) a warp per row, two rows in flight per warp, 128 slots
+ * it): SNN_ROWS_PAIRS (default) a warp per row, two rows in flight per warp, 160 slots
  * of each per round trip; SNN_ROWS_PER_WARP one row at a time; SNN_ROWS_PER_BLOCK all
  * warps on each row, a 32-slot chunk each; SNN_ROWS_WIDE two rows, 256 slots of each per
  * round trip (long rows); SNN_ROWS_QUAD four rows, 128 slots each.  The last two keep 16

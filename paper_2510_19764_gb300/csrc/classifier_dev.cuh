@@ -170,10 +170,12 @@ __device__ __forceinline__ void input_group(const InputParams& p, const long lon
 //      advances the leaky readout y^t = alpha y^{t-1} + W_out z^{t-1} + b (one lane per
 //      output, sequential in t) and records y^t into the d record (softmax comes later).
 constexpr int FWD_ROWS = 2;   // spiking rows a warp propagates at a time (default schedule)
+constexpr int FWD_CHUNKS = 5; // 32-slot chunks of each row loaded together (default schedule):
+                              // a hidden row's synapses plus its readout column often pass 128
 
 // Phase A row schedules (all add the same integers, so the sums do not depend on them).
 // Row per warp: warp w takes rows w, w + nwarps, ... of the spike list, FR rows at a time,
-// their blocks of CH 32-slot chunks loaded together (FR = 2, CH = 4: SNN_ROWS_PAIRS;
+// their blocks of CH 32-slot chunks loaded together (FR = 2, CH = 5: SNN_ROWS_PAIRS;
 // 1, 4: SNN_ROWS_PER_WARP; 2, 8: SNN_ROWS_WIDE for long rows; 4, 4: SNN_ROWS_QUAD).  The
 // wide forms hold 16 loads per lane in flight (fewer round trips per step, more
 // registers: they suit the persistent kernel, whose CTAs have room for them).
@@ -321,14 +323,15 @@ __device__ __forceinline__ void forward_trial(const FwdParams<real>& p, const in
                 break;
             case SNN_ROWS_WIDE:
                 if (WIDE) propagate_rows_warp<NARROW, 2, nwarps, 8>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
-                else propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<NARROW, FWD_ROWS, nwarps, FWD_CHUNKS>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
                 break;
             case SNN_ROWS_QUAD:
                 if (WIDE) propagate_rows_warp<NARROW, 4, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
-                else propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                else propagate_rows_warp<NARROW, FWD_ROWS, nwarps, FWD_CHUNKS>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
                 break;
             default:
-                propagate_rows_warp<NARROW, FWD_ROWS, nwarps>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R, warp, lane);
+                propagate_rows_warp<NARROW, FWD_ROWS, nwarps, FWD_CHUNKS>(acc, NA, lprv, n_rows, lens, p.pk, p.Cf, R,
+                                                                         warp, lane);
                 break;
         }
         __syncthreads();
