@@ -29,17 +29,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# library kernels per training batch: forward call 4 (k_input, k_pack, k_forward,
-# k_softmax_d), gradient 9 (k_readout_scan, k_backward_x2, k_reduce_gb, k_sort_rows x2,
-# k_gather, k_reduce_ragged x2, k_reduce_out), Adam 4 (k_adam_ragged x2, k_adam_dense
-# x2), DEEP R 10 (eliminate, round0, accept0, distribute, form per projection; plus one
-# 16-byte memset each)
-LAUNCHES_PER_BATCH = 27
+# library kernels per training batch: forward call 5 (k_input, k_colsum, k_pack_narrow,
+# k_forward, k_softmax_d), gradient 9 (k_readout_scan, k_backward_bulk, k_reduce_gb,
+# k_sort_rows x2, k_gather, k_reduce_ragged x2, k_reduce_out), Adam 4 (k_adam_ragged x2,
+# k_adam_dense x2), DEEP R 10 (eliminate, round0, accept0, distribute, form per
+# projection; plus one 16-byte memset each)
+LAUNCHES_PER_BATCH = 28
 # DRAM bytes (read + write) of one k_forward launch at 512 trials from one ncu capture of
 # the current kernel build (None until it has been captured; see profiles/)
-FORWARD_TRAFFIC = 4 * 505.89e6
-FORWARD_TRAFFIC_SOURCE = ("k_forward DRAM read+write per launch from one ncu capture of the current build at 128 "
-                          "trials (505.9 MB), scaled by 4 (the psi record grows with the trials)")
+FORWARD_TRAFFIC = None
+FORWARD_TRAFFIC_SOURCE = ""
 METRIC = "e-prop+DEEP R training samples/s"
 UNIT = "samples/s"
 WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}
