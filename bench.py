@@ -37,8 +37,10 @@ sys.path.insert(0, ROOT)
 LAUNCHES_PER_BATCH = 28
 # DRAM bytes (read + write) of one k_forward launch at 512 trials from one ncu capture of
 # the current kernel build (None until it has been captured; see profiles/)
-FORWARD_TRAFFIC = None
-FORWARD_TRAFFIC_SOURCE = ""
+FORWARD_TRAFFIC = 4 * 506.57e6
+FORWARD_TRAFFIC_SOURCE = ("k_forward DRAM read+write per launch from one ncu capture of the current build at 128 "
+                          "trials (14.4 MB read + 492.2 MB written = 506.6 MB), scaled by 4 (the psi record grows "
+                          "with the trials)")
 METRIC = "e-prop+DEEP R training samples/s"
 UNIT = "samples/s"
 WORKLOAD = {"n_in": 700, "N": 1024, "K": 20, "T": 1000, "B": 512, "p": 0.1, "n_bins": 10, "n_classes": 20}
