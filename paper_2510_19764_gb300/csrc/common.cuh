@@ -169,10 +169,21 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
-// position (0-based) of the n-th (0-based) set bit of x; x must have > n set bits
+// position (0-based) of the n-th (0-based) set bit of x; x must have > n set bits.  A
+// binary search by population counts: keep the low half of the window if it holds the
+// bit, else move to the high half; five fixed steps, no data-dependent loop.
 __device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
-    for (int k = 0; k < n; ++k) x &= x - 1u;
-    return __ffs(x) - 1;
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const uint32_t low = x & ((1u << w) - 1u);
+        const int c = __popc(low);
+        const bool up = n >= c;
+        n -= up ? c : 0;
+        pos += up ? w : 0;
+        x = up ? x >> w : low;
+    }
+    return pos;
 }
 
 __host__ __device__ __forceinline__ int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }

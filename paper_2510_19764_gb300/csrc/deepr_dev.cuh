@@ -170,6 +170,8 @@ __device__ __forceinline__ uint32_t conn_word(const uint32_t* crow, int wi, int 
     return word;
 }
 
+constexpr int FORM_BATCH = 8;   // activations whose chunk words a warp loads together
+
 // One warp: the activations of row i (taken[i] of them); F: NC + 1 ints of shared memory
 // for the row's chunk counts, NC = ceil(Qw / 32).
 template <typename real>
@@ -242,21 +244,43 @@ __device__ __forceinline__ void form_row_warp(int32_t* __restrict__ len, int32_t
             }
             if (lane == k) xk = x;
         }
-        int target = -1;
-        if (lane < nt && xk < carry) {
-            int lo = 0, hi = NC - 1;                     // last chunk whose prefix is <= x_k
+        // lane k: the chunk holding x_k and x_k's rank among that chunk's free targets
+        int lo = 0, rem = 0;
+        const bool valid = lane < nt && xk < carry;
+        if (valid) {
+            int hi = NC - 1;                             // last chunk whose prefix is <= x_k
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (F[mid] <= xk) lo = mid;
                 else hi = mid - 1;
             }
-            int rem = xk - F[lo];
-            for (int h = 0; h < 32 && target < 0; ++h) {
-                const int wi = lo * 32 + h;
-                const uint32_t fr = ~conn_word(crow, wi, Qw, i, forb, tail_mask);
+            rem = xk - F[lo];
+        }
+        // the whole warp resolves activation k in its chunk (lane h holds word h), the
+        // chunk words of up to FORM_BATCH activations loaded together
+        int target = -1;
+        for (int k0 = 0; k0 < nt; k0 += FORM_BATCH) {
+            uint32_t wv[FORM_BATCH];
+#pragma unroll
+            for (int u = 0; u < FORM_BATCH; ++u) {
+                const int ck = __shfl_sync(0xffffffffu, lo, (k0 + u) & 31);
+                wv[u] = k0 + u < nt ? conn_word(crow, ck * 32 + lane, Qw, i, forb, tail_mask) : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < FORM_BATCH; ++u) {
+                const int k = k0 + u;
+                if (k >= nt) break;                      // warp-uniform
+                const int ck = __shfl_sync(0xffffffffu, lo, k);
+                const int rk = __shfl_sync(0xffffffffu, rem, k);
+                const bool vk = __shfl_sync(0xffffffffu, valid ? 1 : 0, k) != 0;
+                const uint32_t fr = ~wv[u];
                 const int pc = __popc(fr);
-                if (rem < pc) target = wi * 32 + nth_set_bit(fr, rem);
-                else rem -= pc;
+                const int incl = warp_incl_scan(pc);
+                const uint32_t hm = __ballot_sync(0xffffffffu, vk && rk >= incl - pc && rk < incl);
+                int tg = -1;
+                if (hm && lane == __ffs(hm) - 1) tg = (ck * 32 + lane) * 32 + nth_set_bit(fr, rk - (incl - pc));
+                tg = __shfl_sync(0xffffffffu, tg, hm ? __ffs(hm) - 1 : 0);
+                if (lane == k && hm) target = tg;
             }
         }
         const bool bad = __any_sync(0xffffffffu, lane < nt && target < 0);
