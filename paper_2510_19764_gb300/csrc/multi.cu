@@ -12,9 +12,9 @@
 //                        of every row (needed only by GATHER)
 //   SCAN    1 item       softmax of the readout, filtered readout error, bias gradient,
 //                        Adam's running products
-//   BWD     N/512 items  the adjoint scan, 512 hidden neurons per item
+//   BWD     N/1024 items the adjoint scan, 1024 hidden neurons per item (two per thread)
 //   GATHER  Win+Wh items e-prop gradients of one spike-bit word (32 presynaptic rows)
-//   ADAM    n items      L1 + Adam (+ DEEP R noise) on 4096 elements per item
+//   ADAM    n items      L1 + Adam (+ DEEP R noise) on 8192 elements per item
 //   ELIM    n items      DEEP R elimination, 32 rows per item
 //   DIST    2 items      DEEP R redistribution of each projection (one CTA)
 //   FORM    n items      DEEP R formation, 32 rows per item
@@ -47,7 +47,8 @@ enum : int {
     MP_ELIM = 8, MP_DIST = 9, MP_FORM = 10, MP_N = 11,
 };
 
-constexpr int MT = 256;                          // threads per CTA
+constexpr int MT = 512;                          // threads per CTA (one CTA per SM: a trial's forward
+                                                 // gets 16 warps; 256 threads: 1.18x longer iterations)
 constexpr int MW = MT / 32;                      // warps per CTA
 constexpr int M_INPUT_PER_ITEM = 8 * MT;         // input groups (8 channels each) per item
 constexpr int M_PACK_PER_ITEM = 32 * MT;         // packed slots per item
