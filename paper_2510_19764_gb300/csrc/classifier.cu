@@ -2,8 +2,9 @@
 //
 // Forward: one CTA owns one trial and runs every requested step inside one launch.
 // Per step it propagates the previous step's input and hidden spikes through the two
-// ragged matrices into shared-memory fixed-point accumulators (sums independent of the
-// order of the atomic additions), draws the new input spikes from Philox, updates the
+// ragged matrices into shared-memory integer accumulators (sums independent of the
+// order of the atomic additions; FP64 on the 2^-40 fixed-point grid, FP32 on a grid per
+// accumulator set by its incoming |weight| sum), draws the new input spikes from Philox, updates the
 // neurons and the leaky readout, and records spikes (bits), psi and y; a second kernel
 // turns the recorded y into d = softmax(y) - onehot(label) for all steps in parallel.
 //
