@@ -4,8 +4,9 @@
 // Per step it propagates the previous step's input and hidden spikes through the two
 // ragged matrices into shared-memory integer accumulators (sums independent of the
 // order of the atomic additions; FP64 on the 2^-40 fixed-point grid, FP32 on a grid per
-// accumulator set by its incoming |weight| sum), draws the new input spikes from Philox, updates the
-// neurons and the leaky readout, and records spikes (bits), psi and y; a second kernel
+// accumulator set by its incoming |weight| sum), updates the neurons and the leaky
+// readout, and records spikes (bits), psi and y; the input spikes of every step are drawn
+// from Philox ahead of the step loop (k_input, all steps in parallel); a second kernel
 // turns the recorded y into d = softmax(y) - onehot(label) for all steps in parallel.
 //
 // Gradient: e-prop's traces are linear in the presynaptic filtered spike train zbar_i
