@@ -439,7 +439,7 @@ snn_status snn_eprop_update(snn_classifier* c, const snn_batch* b, int32_t phase
  * The results are bit-identical to those calls (same device functions). */
 typedef struct {
     snn_classifier* cls;
-    snn_batch batch;                /* B = 1, T <= min(max_T, 8192); state, records and workspace
+    snn_batch batch;                /* B = 1, T <= min(max_T, 4096); state, records and workspace
                                        (no trial_T) in caller memory */
     const int32_t* label_table;     /* device [n_label] */
     int32_t n_label;

@@ -633,8 +633,8 @@ snn_status snn_create_classifier(const snn_classifier_desc* d, snn_classifier** 
     c->alpha = std::exp(-d->dt / d->tau_m);
     c->rho = d->tau_a > 0 ? std::exp(-d->dt / d->tau_a) : 0.0;
     long long BT = (long long)d->max_B * d->max_T;
-    // K-splits of the gather: each CTA stages at most 8192 (trial, step) spike words
-    c->KS = (int)((BT + 8191) / 8192);
+    // K-splits of the gather: each CTA stages at most GATHER_SPAN (trial, step) spike words
+    c->KS = (int)((BT + GATHER_SPAN - 1) / GATHER_SPAN);
     const int c_rec = d->w_rec->d.C + d->K;
     c->Cf = ((d->w_in->d.C > c_rec ? d->w_in->d.C : c_rec) + 31) / 32 * 32;
     size_t rsz = d->dtype == SNN_F32 ? 4 : 8;

@@ -343,7 +343,7 @@ __device__ void m_bwd(const MInst& I, int k, unsigned char* smem) {
 }
 
 // One spike-bit word (input words first, then hidden words): its 32 rows in groups of
-// MW warps, each over all 128-slot groups; one K-split (B = 1, T <= 8192), gradients
+// MW warps, each over all 128-slot groups; one K-split (B = 1, T <= GATHER_SPAN), gradients
 // written in place.
 __device__ void m_gather(const MInst& I, int col, unsigned char* smem) {
     const MRag &ri = I.rg[0], &rr = I.rg[1];
@@ -605,7 +605,7 @@ static snn_status multi_fill(const snn_multi_instance& s, MInst& I, size_t& smem
     SNN_REQUIRE(d.dtype == SNN_F32, "snn_multi_create: FP32 classifiers only");
     SNN_REQUIRE(d.N % 2 == 0, "snn_multi_create: N must be even");
     SNN_REQUIRE(b.B == 1 && b.T > 0 && b.T <= d.max_T && b.T <= GATHER_SPAN,
-                "snn_multi_create: each instance trains one trial (B = 1) of 1 <= T <= min(max_T, 8192) steps");
+                "snn_multi_create: each instance trains one trial (B = 1) of 1 <= T <= min(max_T, %d) steps", GATHER_SPAN);
     SNN_REQUIRE(b.labels && b.bin_len && b.trial_ids && b.v && b.a && b.y && b.ysum && b.x_bits && b.z_bits &&
                     b.x_rec && b.z_rec && b.psi_rec && b.d_rec && b.delta && b.Dout && !b.trial_T,
                 "snn_multi_create: the batch needs state, records and workspace (and no trial_T)");
